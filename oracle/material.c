@@ -1,0 +1,166 @@
+/*
+ * Oracle (test infrastructure only): constitutive models and return maps.
+ *
+ * The paper merges "singular value decomposition, plasticity projection,
+ * stress computation" into the particle kernels (Sec. 4.1) and simulates
+ * sand, snow and water (Sec. 6); it prints none of the formulas.  The
+ * formulas below are the cited literature's:
+ *   fixed-corotated:  tau = 2 mu (F - R) F^T + lambda J (J - 1) I,
+ *                     R = U V^T (Stomakhin et al. 2012)
+ *   snow:             mu, lambda scaled by exp(xi (1 - Jp)); after the
+ *                     F update the singular values are clamped to
+ *                     [1 - theta_c, 1 + theta_s] and Jp absorbs the removed
+ *                     volume (Stomakhin et al. 2013)
+ *   fluid:            tau = -p J I, p = K (J^-gamma - 1)
+ *                     (Tampubolon et al. 2017)
+ *   sand:             tau = U (2 mu eps + lambda tr(eps) I) U^T with the
+ *                     Hencky strain eps = ln(sigma), and the Drucker-Prager
+ *                     return map of Klar et al. 2016 (cases I-III).
+ * Readings of points the sources leave open (log of non-positive singular
+ * values, tie cases) are listed in the design doc.
+ */
+#include <math.h>
+#include <string.h>
+#include "oracle.h"
+
+#define AT(M, r, c) (M)[3 * (r) + (c)]
+#define ORC_PI 3.14159265358979323846
+
+void orc_lame(double E, double nu, double* mu, double* la)
+{
+    *mu = E / (2.0 * (1.0 + nu));
+    *la = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+}
+
+static double det3(const double M[9])
+{
+    return AT(M, 0, 0) * (AT(M, 1, 1) * AT(M, 2, 2) - AT(M, 1, 2) * AT(M, 2, 1))
+         - AT(M, 0, 1) * (AT(M, 1, 0) * AT(M, 2, 2) - AT(M, 1, 2) * AT(M, 2, 0))
+         + AT(M, 0, 2) * (AT(M, 1, 0) * AT(M, 2, 1) - AT(M, 1, 1) * AT(M, 2, 0));
+}
+
+/* out = A B^T */
+static void mul_abt(const double A[9], const double B[9], double out[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k)
+                s += AT(A, i, k) * AT(B, j, k);
+            AT(out, i, j) = s;
+        }
+}
+
+/* out = U diag(d) W^T */
+static void udwt(const double U[9], const double d[3], const double W[9], double out[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k)
+                s += AT(U, i, k) * d[k] * AT(W, j, k);
+            AT(out, i, j) = s;
+        }
+}
+
+static void fixed_corotated(double mu, double la, const double F[9], double tau[9])
+{
+    double U[9], sig[3], V[9], R[9], D[9];
+    orc_svd3(F, U, sig, V);
+    mul_abt(U, V, R);                    /* R = U V^T */
+    double J = det3(F);
+    for (int i = 0; i < 9; ++i)
+        D[i] = F[i] - R[i];
+    mul_abt(D, F, tau);                  /* (F - R) F^T */
+    for (int i = 0; i < 9; ++i)
+        tau[i] *= 2.0 * mu;
+    for (int i = 0; i < 3; ++i)
+        AT(tau, i, i) += la * J * (J - 1.0);
+}
+
+/* Hencky strain of the singular values; a non-positive (inverted) value is
+ * read as the floor 1e-4 before the logarithm. */
+static void hencky(const double sig[3], double eps[3])
+{
+    for (int i = 0; i < 3; ++i)
+        eps[i] = log(sig[i] > 1e-4 ? sig[i] : 1e-4);
+}
+
+void orc_kirchhoff(const orc_material* mat, const double F[9], double Jp, double tau[9])
+{
+    double mu, la;
+    memset(tau, 0, 9 * sizeof(double));
+    switch (mat->kind) {
+    case ORC_ELASTIC:
+        orc_lame(mat->E, mat->nu, &mu, &la);
+        fixed_corotated(mu, la, F, tau);
+        break;
+    case ORC_SNOW: {
+        orc_lame(mat->E, mat->nu, &mu, &la);
+        double h = exp(mat->hardening * (1.0 - Jp));
+        fixed_corotated(mu * h, la * h, F, tau);
+        break;
+    }
+    case ORC_FLUID: {
+        double J = Jp;
+        double p = mat->E * (pow(J, -mat->gamma) - 1.0);
+        for (int i = 0; i < 3; ++i)
+            AT(tau, i, i) = -p * J;
+        break;
+    }
+    case ORC_SAND: {
+        orc_lame(mat->E, mat->nu, &mu, &la);
+        double U[9], sig[3], V[9], eps[3], d[3];
+        orc_svd3(F, U, sig, V);
+        hencky(sig, eps);
+        double tr = eps[0] + eps[1] + eps[2];
+        for (int i = 0; i < 3; ++i)
+            d[i] = 2.0 * mu * eps[i] + la * tr;
+        udwt(U, d, U, tau);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+void orc_plasticity(const orc_material* mat, double F[9], double* Jp)
+{
+    if (mat->kind == ORC_SNOW) {
+        double U[9], sig[3], V[9], cl[3];
+        orc_svd3(F, U, sig, V);
+        double lo = 1.0 - mat->theta_c, hi = 1.0 + mat->theta_s;
+        for (int i = 0; i < 3; ++i)
+            cl[i] = sig[i] < lo ? lo : (sig[i] > hi ? hi : sig[i]);
+        *Jp *= (sig[0] * sig[1] * sig[2]) / (cl[0] * cl[1] * cl[2]);
+        udwt(U, cl, V, F);
+    } else if (mat->kind == ORC_SAND) {
+        double mu, la;
+        orc_lame(mat->E, mat->nu, &mu, &la);
+        double U[9], sig[3], V[9], eps[3], s[3];
+        orc_svd3(F, U, sig, V);
+        hencky(sig, eps);
+        double tr = eps[0] + eps[1] + eps[2];
+        double sphi = sin(mat->friction_deg * ORC_PI / 180.0);
+        double alpha = sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi);
+        if (tr >= 0.0) {
+            /* case II: expansion, project to the cone tip */
+            s[0] = s[1] = s[2] = 1.0;
+            udwt(U, s, V, F);
+            return;
+        }
+        double dev[3], nd = 0;
+        for (int i = 0; i < 3; ++i) {
+            dev[i] = eps[i] - tr / 3.0;
+            nd += dev[i] * dev[i];
+        }
+        nd = sqrt(nd);
+        double dgamma = nd + (3.0 * la + 2.0 * mu) / (2.0 * mu) * tr * alpha;
+        if (dgamma <= 0.0)
+            return; /* case I: inside the yield cone, F unchanged */
+        /* case III: radial return onto the cone surface */
+        for (int i = 0; i < 3; ++i)
+            s[i] = exp(eps[i] - dgamma * dev[i] / nd);
+        udwt(U, s, V, F);
+    }
+}

@@ -1,0 +1,431 @@
+"""Pins for the FP64 oracle: each check compares it with something other than
+itself -- a closed form, an invariant of the method, a library routine
+(numpy's SVD), or brute force on tiny inputs.  A dropped term, a wrong sign,
+a wrong index or a transposed operand in the oracle fails at least one test.
+"""
+import numpy as np
+import pytest
+
+RNG = np.random.default_rng(12345)
+
+
+def N_quad(u):
+    """Quadratic B-spline kernel, piecewise definition (independent of the
+    base/fraction form the oracle uses)."""
+    u = np.abs(u)
+    return np.where(u < 0.5, 0.75 - u * u, np.where(u < 1.5, 0.5 * (1.5 - u) ** 2, 0.0))
+
+
+# ----------------------------------------------------------------- weights
+
+@pytest.mark.parametrize("f", list(RNG.uniform(0.5, 1.5, 16)) + [0.5, 1.0, 1.4999999])
+def test_bspline_moments_and_kernel(orc, f):
+    w = orc.bspline_weights(f)
+    off = np.arange(3) - f           # (x_i - x_p)/dx for the three nodes
+    assert abs(w.sum() - 1.0) < 1e-14                  # partition of unity
+    assert abs((w * off).sum()) < 1e-14                # zero first moment
+    assert abs((w * off * off).sum() - 0.25) < 1e-14   # second moment = 1/4 (dx^2/4)
+    np.testing.assert_allclose(w, N_quad(off), rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------- SVD
+
+def _rand_rot(rng):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def _svd_cases():
+    rng = np.random.default_rng(7)
+    cases = [np.eye(3), np.diag([2.0, 0.5, 1.0]), np.diag([1.0, 1.0, -1.0]),
+             np.zeros((3, 3)), np.diag([3.0, 0.0, 0.0])]
+    for _ in range(40):
+        cases.append(rng.normal(size=(3, 3)))
+    for _ in range(10):
+        cases.append(np.eye(3) + 1e-3 * rng.normal(size=(3, 3)))
+    for _ in range(10):                       # repeated singular values
+        R1, R2 = _rand_rot(rng), _rand_rot(rng)
+        cases.append(R1 @ np.diag([1.2, 1.2, 0.7]) @ R2.T)
+    for _ in range(5):                        # inverted
+        R1, R2 = _rand_rot(rng), _rand_rot(rng)
+        cases.append(R1 @ np.diag([1.3, 0.9, -0.2]) @ R2.T)
+    return cases
+
+
+@pytest.mark.parametrize("F", _svd_cases())
+def test_svd_against_numpy(orc, F):
+    U, s, V = orc.svd3(F)
+    np.testing.assert_allclose(U @ np.diag(s) @ V.T, F, atol=1e-12 * max(1.0, np.abs(F).max()))
+    np.testing.assert_allclose(U.T @ U, np.eye(3), atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(3), atol=1e-12)
+    assert abs(np.linalg.det(U) - 1) < 1e-12 and abs(np.linalg.det(V) - 1) < 1e-12
+    ref = np.linalg.svd(F, compute_uv=False)          # library routine, descending
+    np.testing.assert_allclose(np.abs(s), ref, atol=1e-12 * max(1.0, ref[0]))
+    assert s[0] >= s[1] >= abs(s[2]) - 1e-12
+    d = np.linalg.det(F)
+    if abs(d) > 1e-9:
+        assert np.sign(s[2]) == np.sign(d)
+
+
+# ------------------------------------------------------------------ stress
+
+def _psi_fixed_corotated(F, mu, la):
+    s = np.linalg.svd(F, compute_uv=False)
+    if np.linalg.det(F) < 0:
+        s[2] = -s[2]
+    J = np.linalg.det(F)
+    return mu * ((s - 1) ** 2).sum() + 0.5 * la * (J - 1) ** 2
+
+
+def _psi_hencky(F, mu, la):
+    s = np.linalg.svd(F, compute_uv=False)
+    e = np.log(s)
+    return mu * (e * e).sum() + 0.5 * la * e.sum() ** 2
+
+
+def _fd_first_pk(psi, F, h=1e-6):
+    P = np.zeros((3, 3))
+    for i in range(3):
+        for j in range(3):
+            E = np.zeros((3, 3))
+            E[i, j] = h
+            P[i, j] = (psi(F + E) - psi(F - E)) / (2 * h)
+    return P
+
+
+def test_fixed_corotated_is_energy_derivative(orc):
+    """tau = P F^T with P the derivative of the fixed-corotated energy
+    psi = mu sum (s_i - 1)^2 + la/2 (J - 1)^2 (Stomakhin et al. 2012)."""
+    rng = np.random.default_rng(3)
+    E, nu = 1e4, 0.2
+    mu, la = orc.lame(E, nu)
+    mat = orc.material(orc.ELASTIC, E=E, nu=nu)
+    for _ in range(10):
+        F = np.eye(3) + 0.3 * rng.normal(size=(3, 3))
+        if np.linalg.det(F) < 0.2:
+            continue
+        P = _fd_first_pk(lambda G: _psi_fixed_corotated(G, mu, la), F)
+        np.testing.assert_allclose(orc.kirchhoff(mat, F), P @ F.T, rtol=0, atol=1e-4 * E)
+
+
+def test_fixed_corotated_special_cases(orc):
+    E, nu = 1e4, 0.2
+    mu, la = orc.lame(E, nu)
+    assert abs(mu - E / 2.4) < 1e-9 and abs(la - E * 0.2 / (1.2 * 0.6)) < 1e-9
+    mat = orc.material(orc.ELASTIC, E=E, nu=nu)
+    R = _rand_rot(np.random.default_rng(1))
+    np.testing.assert_allclose(orc.kirchhoff(mat, R), 0, atol=1e-9)      # rotation: no stress
+    for s in (0.8, 1.0, 1.25):                                             # uniform dilation
+        tau = orc.kirchhoff(mat, s * np.eye(3))
+        expect = 2 * mu * (s - 1) * s + la * s ** 3 * (s ** 3 - 1)
+        np.testing.assert_allclose(tau, expect * np.eye(3), atol=1e-9 * E)
+    eps = 1e-6 * np.array([[1.0, 0.3, -0.2], [0.3, -0.5, 0.1], [-0.2, 0.1, 0.7]])
+    lin = 2 * mu * eps + la * np.trace(eps) * np.eye(3)                    # small-strain limit
+    np.testing.assert_allclose(orc.kirchhoff(mat, np.eye(3) + eps), lin, rtol=0, atol=1e-8 * E)
+    F = np.eye(3) + 0.2 * np.random.default_rng(5).normal(size=(3, 3))
+    tau, Q = orc.kirchhoff(mat, F), _rand_rot(np.random.default_rng(6))
+    np.testing.assert_allclose(orc.kirchhoff(mat, Q @ F), Q @ tau @ Q.T, atol=1e-9 * E)   # objectivity
+    np.testing.assert_allclose(tau, tau.T, atol=1e-9 * E)
+
+
+def test_snow_hardening_and_fluid_and_sand_stress(orc):
+    F = np.eye(3) + 0.05 * np.random.default_rng(8).normal(size=(3, 3))
+    el = orc.material(orc.ELASTIC, E=1.4e5, nu=0.2)
+    sn = orc.material(orc.SNOW, E=1.4e5, nu=0.2, hardening=10.0)
+    for Jp in (1.0, 0.97, 1.02):
+        np.testing.assert_allclose(orc.kirchhoff(sn, F, Jp), np.exp(10.0 * (1 - Jp)) * orc.kirchhoff(el, F),
+                                   rtol=1e-12, atol=1e-9)
+    fl = orc.material(orc.FLUID, E=1e4, gamma=7.0)
+    np.testing.assert_allclose(orc.kirchhoff(fl, np.eye(3), 1.0), 0, atol=1e-12)
+    for J in (0.9, 1.1):
+        p = 1e4 * (J ** -7 - 1)
+        np.testing.assert_allclose(orc.kirchhoff(fl, np.eye(3), J), -p * J * np.eye(3), rtol=1e-12)
+    # sand: Hencky St. Venant-Kirchhoff, tau = P F^T of psi = mu |eps|^2 + la/2 tr(eps)^2
+    sa = orc.material(orc.SAND, E=3.5e5, nu=0.3)
+    mu, la = orc.lame(3.5e5, 0.3)
+    rng = np.random.default_rng(9)
+    for _ in range(6):
+        G = np.eye(3) + 0.2 * rng.normal(size=(3, 3))
+        if np.linalg.det(G) < 0.3:
+            continue
+        P = _fd_first_pk(lambda H: _psi_hencky(H, mu, la), G, h=1e-7)
+        np.testing.assert_allclose(orc.kirchhoff(sa, G), P @ G.T, rtol=0, atol=2e-4 * 3.5e5 * 1e-2)
+
+
+# -------------------------------------------------------------- plasticity
+
+def test_snow_clamp(orc):
+    sn = orc.material(orc.SNOW, E=1.4e5, nu=0.2, theta_c=2.5e-2, theta_s=7.5e-3)
+    rng = np.random.default_rng(11)
+    R1, R2 = _rand_rot(rng), _rand_rot(rng)
+    F_in = R1 @ np.diag([1.005, 0.99, 0.98]) @ R2.T          # inside [0.975, 1.0075]
+    F2, J2 = orc.plasticity(sn, F_in, 1.0)
+    np.testing.assert_allclose(F2, F_in, atol=1e-13)
+    assert abs(J2 - 1.0) < 1e-13
+    F_out = R1 @ np.diag([1.05, 1.0, 0.9]) @ R2.T
+    F3, J3 = orc.plasticity(sn, F_out, 0.95)
+    np.testing.assert_allclose(np.linalg.svd(F3, compute_uv=False), [1.0075, 1.0, 0.975], atol=1e-12)
+    # total deformation det(F_E) Jp is conserved by the return map
+    assert abs(np.linalg.det(F3) * J3 - np.linalg.det(F_out) * 0.95) < 1e-12
+    np.testing.assert_allclose(F3, R1 @ np.diag([1.0075, 1.0, 0.975]) @ R2.T, atol=1e-12)
+
+
+def test_drucker_prager_cases(orc):
+    E, nu, phi = 3.5e5, 0.3, 30.0
+    sa = orc.material(orc.SAND, E=E, nu=nu, friction_deg=phi)
+    mu, la = orc.lame(E, nu)
+    sphi = np.sin(np.radians(phi))
+    alpha = np.sqrt(2 / 3) * 2 * sphi / (3 - sphi)
+    rng = np.random.default_rng(13)
+    R1, R2 = _rand_rot(rng), _rand_rot(rng)
+    # case II: volume expansion -> cone tip, sigma = 1
+    F, _ = orc.plasticity(sa, R1 @ np.diag([1.05, 1.01, 0.99]) @ R2.T)
+    np.testing.assert_allclose(F, R1 @ R2.T, atol=1e-12)
+    # case I: compression with little shear stays
+    Fi = R1 @ np.diag([0.999, 0.998, 0.997]) @ R2.T
+    F, _ = orc.plasticity(sa, Fi)
+    np.testing.assert_allclose(F, Fi, atol=1e-13)
+    # case III: sheared compression is returned onto the cone surface
+    Fo = R1 @ np.diag([1.03, 0.99, 0.95]) @ R2.T
+    eps = np.log([1.03, 0.99, 0.95])
+    assert eps.sum() < 0
+    F, _ = orc.plasticity(sa, Fo)
+    s = np.linalg.svd(F, compute_uv=False)
+    e2 = np.log(s)
+    dev2 = e2 - e2.mean()
+    assert abs(e2.sum() - eps.sum()) < 1e-12                       # trace preserved
+    yield_fn = np.linalg.norm(dev2) + (3 * la + 2 * mu) / (2 * mu) * e2.sum() * alpha
+    assert abs(yield_fn) < 1e-12                                   # on the cone
+    dev = eps - eps.mean()
+    np.testing.assert_allclose(dev2 / np.linalg.norm(dev2), np.sort(dev)[::-1] / np.linalg.norm(dev), atol=1e-9)
+
+
+# --------------------------------------------------------------- transfers
+
+def _random_state(orc, rng, n, lo, hi, dx, F_noise=0.05, C_scale=1.0, v_scale=1.0):
+    x = rng.uniform(lo, hi, size=(n, 3))
+    v = v_scale * rng.normal(size=(n, 3))
+    C = C_scale * rng.normal(size=(n, 3, 3))
+    F = np.eye(3) + F_noise * rng.normal(size=(n, 3, 3))
+    vol = rng.uniform(0.5, 1.5, n) * dx ** 3 / 8
+    return orc.State(x, v, C, F, None, vol, 0)
+
+
+def test_p2g_conservation(orc):
+    rng = np.random.default_rng(21)
+    dx = 1 / 64
+    cfg = orc.config(64, dx)
+    mat = orc.material(orc.ELASTIC, E=1e4, nu=0.2, rho=3.0)
+    s = _random_state(orc, rng, 300, 0.3, 0.7, dx)
+    dt = 1e-4
+    g, st = orc.p2g(cfg, mat, s, dt)
+    assert st == 0
+    mp = 3.0 * s.vol
+    assert abs(g.m.sum() - mp.sum()) <= 1e-13 * mp.sum()
+    P = g.p.reshape(-1, 3).sum(0)
+    np.testing.assert_allclose(P, (mp[:, None] * s.v).sum(0), rtol=1e-12, atol=1e-13)
+    # angular momentum: sum_i x_i x p_i = sum_p x_p x m v + m (dx^2/4) eps_abc C_cb
+    xi = g.node_positions(dx).reshape(-1, 3)
+    L_grid = np.cross(xi, g.p.reshape(-1, 3)).sum(0)
+    C = s.C
+    spin = np.stack([C[:, 2, 1] - C[:, 1, 2], C[:, 0, 2] - C[:, 2, 0], C[:, 1, 0] - C[:, 0, 1]], axis=1)
+    L_part = (np.cross(s.x, mp[:, None] * s.v) + mp[:, None] * dx * dx / 4 * spin).sum(0)
+    np.testing.assert_allclose(L_grid, L_part, rtol=1e-10, atol=1e-14)
+
+
+def test_p2g_brute_force_tiny(orc):
+    """Tiny case against a naive loop over every node of an 8^3 grid with the
+    piecewise kernel, the stress from the closed form of a uniform dilation."""
+    dx = 1 / 8
+    cfg = orc.config(8, dx)
+    E, nu = 2e3, 0.25
+    mat = orc.material(orc.ELASTIC, E=E, nu=nu, rho=2.0)
+    mu, la = orc.lame(E, nu)
+    rng = np.random.default_rng(4)
+    n = 6
+    x = rng.uniform(0.35, 0.65, size=(n, 3))
+    v = rng.normal(size=(n, 3))
+    C = rng.normal(size=(n, 3, 3))
+    sc = rng.uniform(0.9, 1.1, n)
+    F = sc[:, None, None] * np.eye(3)[None]
+    vol = np.full(n, 1e-3)
+    s = orc.State(x, v, C, F, None, vol, 0)
+    dt = 1e-3
+    g, st = orc.p2g(cfg, mat, s, dt, orc.DenseGrid([0, 0, 0], [8, 8, 8]))
+    assert st == 0
+    m_ref = np.zeros((8, 8, 8))
+    p_ref = np.zeros((8, 8, 8, 3))
+    for q in range(n):
+        J = sc[q] ** 3
+        tau = (2 * mu * (sc[q] - 1) * sc[q] + la * J * (J - 1)) * np.eye(3)
+        mq = 2.0 * vol[q]
+        A = mq * C[q] - 4 * dt * vol[q] / dx ** 2 * tau
+        for k in range(8):
+            for j in range(8):
+                for i in range(8):
+                    xi = np.array([i, j, k]) * dx
+                    w = N_quad(x[q, 0] / dx - i) * N_quad(x[q, 1] / dx - j) * N_quad(x[q, 2] / dx - k)
+                    m_ref[k, j, i] += w * mq
+                    p_ref[k, j, i] += w * (mq * v[q] + A @ (xi - x[q]))
+    np.testing.assert_allclose(g.mass(), m_ref, atol=1e-15)
+    np.testing.assert_allclose(g.mom(), p_ref, atol=1e-12)
+
+
+def test_p2g_node_matches_dense(orc):
+    rng = np.random.default_rng(22)
+    dx = 1 / 32
+    cfg = orc.config(32, dx)
+    mat = orc.material(orc.ELASTIC)
+    s = _random_state(orc, rng, 200, 0.3, 0.7, dx)
+    g, _ = orc.p2g(cfg, mat, s, 1e-4)
+    m = g.mass()
+    idx = np.argwhere(m > 0)
+    for kk in idx[rng.choice(len(idx), 10, replace=False)]:
+        node = np.array([kk[2], kk[1], kk[0]]) + g.lo
+        out = orc.p2g_node(cfg, mat, s, 1e-4, node)
+        assert abs(out[0] - m[tuple(kk)]) < 1e-15
+        np.testing.assert_allclose(out[1:], g.mom()[tuple(kk)], atol=1e-13)
+
+
+def test_grid_update_boundaries(orc):
+    dx = 1 / 16
+    dt = 1e-2
+    g = orc.DenseGrid([0, 0, 0], [16, 16, 16])
+    m, p = g.mass(), g.mom()
+    m[8, 8, 8] = 2.0; p[8, 8, 8] = [2.0, 4.0, -6.0]          # interior
+    m[8, 1, 8] = 1.0; p[8, 1, 8] = [1.0, -3.0, 0.5]          # y wall layer (low), moving into the wall
+    m[8, 14, 8] = 1.0; p[8, 14, 8] = [1.0, 3.0, 0.5]         # y wall layer (high), moving into the wall
+    m[8, 12, 2] = 1.0; p[8, 12, 2] = [0.5, 0.5, 0.5]         # x low wall, moving away
+    p[5, 5, 5] = [1.0, 1.0, 1.0]                             # massless node carries no velocity
+    gs = orc.DenseGrid(g.lo, g.dim); gs.m[:] = g.m; gs.p[:] = g.p
+    gr = 9.8
+    orc.grid_update(orc.config(16, dx, orc.SLIP, 3), dt, g)
+    V = g.mom()
+    np.testing.assert_allclose(V[8, 8, 8], [1.0, 2.0 - gr * dt, -3.0], atol=1e-14)
+    np.testing.assert_allclose(V[8, 1, 8], [1.0, 0.0, 0.5], atol=1e-14)
+    np.testing.assert_allclose(V[8, 14, 8], [1.0, 0.0, 0.5], atol=1e-14)
+    np.testing.assert_allclose(V[8, 12, 2], [0.5, 0.5 - gr * dt, 0.5], atol=1e-14)
+    np.testing.assert_allclose(V[5, 5, 5], 0, atol=0)
+    orc.grid_update(orc.config(16, dx, orc.STICKY, 3), dt, gs)
+    V = gs.mom()
+    np.testing.assert_allclose(V[8, 8, 8], [1.0, 2.0 - gr * dt, -3.0], atol=1e-14)
+    for c in ([8, 1, 8], [8, 14, 8], [8, 12, 2]):
+        np.testing.assert_allclose(V[tuple(c)], 0, atol=0)
+
+
+def test_g2p_affine_reproduction(orc):
+    """Grid velocity a + B x_i is reproduced exactly: v_p = a + B x_p, C_p = B."""
+    rng = np.random.default_rng(31)
+    dx = 1 / 32
+    cfg = orc.config(32, dx)
+    mat = orc.material(orc.ELASTIC)
+    n = 50
+    F0 = np.eye(3) + 0.1 * rng.normal(size=(n, 3, 3))
+    s = orc.State(rng.uniform(0.3, 0.7, (n, 3)), F=F0)
+    a = rng.normal(size=3)
+    B = rng.normal(size=(3, 3))
+    lo, dim = orc.grid_bounds(s.x, dx)
+    g = orc.DenseGrid(lo, dim)
+    g.p[:] = (a + g.node_positions(dx).reshape(-1, 3) @ B.T).reshape(-1)
+    x0 = s.x.copy()
+    dt = 1e-3
+    assert orc.g2p(cfg, mat, s, dt, g) == 0
+    vp = a + x0 @ B.T
+    np.testing.assert_allclose(s.v, vp, atol=1e-12)
+    np.testing.assert_allclose(s.C, np.broadcast_to(B, (n, 3, 3)), atol=1e-10)
+    np.testing.assert_allclose(s.x, x0 + dt * vp, atol=1e-14)
+    np.testing.assert_allclose(s.F, np.einsum("ab,pbc->pac", np.eye(3) + dt * B, F0), atol=1e-12)
+    # fluid: J <- (1 + dt tr C) J, F untouched
+    sf = orc.State(x0, Jp=np.full(n, 0.9))
+    fl = orc.material(orc.FLUID, E=1e4)
+    orc.g2p(cfg, fl, sf, dt, g)
+    np.testing.assert_allclose(sf.Jp, 0.9 * (1 + dt * np.trace(B)), rtol=1e-12)
+    np.testing.assert_allclose(sf.F, np.broadcast_to(np.eye(3), (n, 3, 3)), atol=0)
+
+
+def test_free_fall_closed_form(orc):
+    """F = I, C = 0, uniform v0, no wall reached: each substep adds dt g, so
+    x_n = x0 + n dt v0 + g dt^2 n (n + 1) / 2 (symplectic Euler)."""
+    rng = np.random.default_rng(41)
+    dx = 1 / 64
+    cfg = orc.config(64, dx, orc.STICKY)
+    mat = orc.material(orc.ELASTIC, E=1e4, nu=0.2)
+    n = 400
+    x0 = rng.uniform(0.4, 0.6, (n, 3))
+    v0 = np.array([0.3, 0.1, -0.2])
+    s = orc.State(x0, np.tile(v0, (n, 1)), vol=1e-6)
+    dt, steps = 1e-3, 25
+    for _ in range(steps):
+        assert orc.substep(cfg, mat, s, dt) == 0
+    g = np.array([0, -9.8, 0])
+    expect = x0 + steps * dt * v0 + g * dt * dt * steps * (steps + 1) / 2
+    np.testing.assert_allclose(s.x, expect, atol=1e-12)
+    np.testing.assert_allclose(s.v, np.tile(v0 + steps * dt * g, (n, 1)), atol=1e-11)
+    np.testing.assert_allclose(s.C, 0, atol=1e-9)
+    np.testing.assert_allclose(s.F, np.broadcast_to(np.eye(3), (n, 3, 3)), atol=1e-12)
+
+
+def test_substep_is_phase_composition(orc):
+    rng = np.random.default_rng(51)
+    dx = 1 / 32
+    cfg = orc.config(32, dx, orc.SLIP)
+    mats = [orc.material(orc.ELASTIC), orc.material(orc.SNOW, E=1.4e5, rho=400.0),
+            orc.material(orc.FLUID, E=1e4, rho=1000.0), orc.material(orc.SAND, E=3.5e5, nu=0.3, rho=2200.0)]
+    s = _random_state(orc, rng, 120, 0.3, 0.7, dx, F_noise=0.01, C_scale=0.1, v_scale=0.1)
+    s.mat[:] = rng.integers(0, 4, s.n)
+    s.Jp[:] = 1.0
+    a, b = s.copy(), s.copy()
+    dt = 1e-4
+    orc.substep(cfg, mats, a, dt)
+    g, _ = orc.p2g(cfg, mats, b, dt)
+    orc.grid_update(cfg, dt, g)
+    orc.g2p(cfg, mats, b, dt, g)
+    for f in ("x", "v", "C", "F", "Jp"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+# -------------------------------------------------------- keys, sort, pblocks
+
+def _morton(c, bits):
+    code = 0
+    for i in range(bits):
+        for a in range(3):
+            code |= ((int(c[a]) >> i) & 1) << (3 * i + a)
+    return code
+
+
+def test_keys_sort_pblocks_brute_force(orc):
+    rng = np.random.default_rng(61)
+    L, inv_dx = 3, 32.0          # 32^3 nodes, 8^3 blocks
+    x = rng.uniform(0.05, 0.95, (500, 3)).astype(np.float32)
+    x[:50] = x[50:100]           # duplicate positions -> equal keys
+    keys, st = orc.particle_keys(x, inv_dx, L)
+    assert st == 0
+    ref = []
+    for p in range(len(x)):
+        b = [int(np.floor(np.float32(np.float32(x[p, a]) * np.float32(inv_dx)) - np.float32(0.5))) for a in range(3)]
+        ref.append((_morton([c >> 2 for c in b], L) << 6) | _morton([c & 3 for c in b], 2))
+    np.testing.assert_array_equal(keys, np.array(ref, dtype=np.uint32))
+    perm = orc.stable_sort(keys)
+    expect = sorted(range(len(x)), key=lambda i: (ref[i], i))
+    np.testing.assert_array_equal(perm, expect)
+    blocks = orc.pblocks(keys, L)
+    want = set()
+    for k in ref:
+        code = k >> 6
+        b = [sum(((code >> (3 * i + a)) & 1) << i for i in range(L)) for a in range(3)]
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dxx in (-1, 0, 1):
+                    c = (b[0] + dxx, b[1] + dy, b[2] + dz)
+                    if min(c) >= 0 and max(c) < (1 << L):
+                        want.add(_morton(c, L))
+    np.testing.assert_array_equal(blocks, np.array(sorted(want), dtype=np.int32))
+
+
+def test_keys_domain_error(orc):
+    keys, st = orc.particle_keys(np.array([[0.001, 0.5, 0.5]], dtype=np.float32), 64.0, 4)
+    assert st == 4 and keys[0] == 0xFFFFFFFF
