@@ -1,0 +1,330 @@
+"""Throughput of the MLS-MPM substep on the snow-blocks scene.
+
+Workload (the 1.33M-particle snow scene of the paper's Sec. 6.5, stood in
+for by synthetic snow blocks): 6 random boxes at 8 particles per cell,
+1,340,960 particles, 256^3 grid of 4^3 blocks, Stomakhin snow (E = 1.4e5,
+nu = 0.2, theta_c = 2.5e-2, theta_s = 7.5e-3, hardening 10, rho = 400),
+frictionless walls, dt = 5e-5, frames of 1/60 s (333 1/3 substeps).
+
+A "step" is one substep: [rebuild-mapping + sort when the free-zone test
+asks for it] -> P2G -> grid update -> G2P.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs its own
+replica of the scene (the path has no data exchange: "replicas only"), and
+rank 0 reports the aggregate over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLS-MPM particle-substeps/s & ms/frame on 1 GB300; batched vs per-scene launches"
+UNIT = "particle-substeps/s"
+RES = 256
+DX = 1.0 / RES
+DT = 5e-5
+FRAME = 1.0 / 60.0
+SUBSTEPS_PER_FRAME = FRAME / DT            # 333.33
+SNOW = dict(E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0)
+VOL = DX ** 3 / 8
+# Algorithmic bytes per particle per launch (FP32 SoA):
+#   P2G reads x 12, v 12, C 36, F 36, Jp 4, vol 4, material 1            = 105 B
+#   G2P reads x 12, F 36, Jp 4, material 1; writes x, v, C, F, Jp 100     = 153 B
+# grid update per node of a physical block: read 16, write 16, clear 16 = 48 B
+BYTES_P2G = 105
+BYTES_G2P = 153
+BYTES_GRID_NODE = 48
+
+
+def workload_config(n):
+    return {"workload": "snow blocks: 6 random boxes, %d particles at 8/cell, 256^3 grid of 4^3 blocks, "
+                        "Stomakhin snow, slip walls, dt=5e-5" % n,
+            "particles": n, "grid": [RES, RES, RES], "dt": DT, "material": "snow (E=1.4e5, nu=0.2, rho=400)",
+            "substeps_per_frame": round(SUBSTEPS_PER_FRAME, 3),
+            "l2": "inputs larger than L2: particle state %.0f MB + grid, no flush" % (n * 105 / 1e6)}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ oracle timing
+
+def oracle_throughput(x, seconds=15.0, max_particles=None, steps=None):
+    """Time the FP64 oracle, single-threaded, on a compact subset of the scene
+    (the particles nearest the first box's centre).  Returns (value, sample)."""
+    import oracle as orc
+    orc.build()
+    n = len(x) if max_particles is None else min(len(x), max_particles)
+    if n < len(x):
+        lo = x.min(0)
+        # nearest-to-a-corner-box subset keeps the oracle's dense box small
+        d = np.abs(x - (lo + 0.05)).max(1)
+        idx = np.argsort(d, kind="stable")[:n]
+        xs = x[idx]
+    else:
+        xs = x
+    s = orc.State(xs.astype(np.float64), vol=VOL)
+    cfg = orc.config(RES, DX, orc.SLIP)
+    m = orc.material(orc.SNOW, **SNOW)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        orc.substep(cfg, m, s, DT)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and el >= seconds):
+            break
+    return n * done / el, "%d oracle substeps (FP64, 1 thread) on %d of the scene's particles, %.1f s" % (done, n, el)
+
+
+# --------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2111_00699_gb300 import scenes
+    x, _ = scenes.snow_blocks()
+    total = args.steps + args.warmup
+    # size each step so the whole run stays within ~2.5 minutes at ~0.7 M particle-substeps/s
+    per_step = int(max(1000, min(len(x), 0.7e6 * 150.0 / max(total, 1))))
+    import oracle as orc
+    orc.build()
+    if args.warmup:
+        oracle_throughput(x, max_particles=per_step, steps=args.warmup)
+    value, sample = oracle_throughput(x, max_particles=per_step, steps=max(args.steps, 1))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(len(x)), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- main arm
+
+def _traffic_for(kernel, src_hash):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_sha1") != src_hash:
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=333)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-frames", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2111_00699_gb300 import build, mpm, scenes
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    x, _ = scenes.snow_blocks()
+    n = len(x)
+    mat = mpm.material(mpm.SNOW, **SNOW)
+    stream = torch.cuda.Stream()
+    xs = torch.from_numpy(x).cuda()
+
+    def fresh_sim():
+        sim = mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream)
+        sim.add_particles(xs)
+        return sim
+
+    # ---- device-resident throughput (the `value`) ----
+    sim = fresh_sim()
+    with torch.cuda.stream(stream):
+        sim.run(args.warmup, DT)
+    sim.sync()
+    launches0 = sim.stats()["kernel_launches"]
+    rebuilds0 = sim.stats()["rebuilds"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        sim.run(args.steps, DT)
+        ev1.record(stream)
+        ev1.synchronize()
+    sim.sync()
+    barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = sim.stats()
+    launches = st["kernel_launches"] - launches0
+    rebuilds = st["rebuilds"] - rebuilds0
+    n_pblocks = st["n_pblocks"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n * args.steps / (ms / 1e3)
+
+    # ---- per-phase timing with CUDA events on the simulator's stream ----
+    prof_steps = min(args.steps, 1000)
+    sim.profile_enable(True)
+    sim.profile_read()
+    sim.run(prof_steps, DT)
+    phases = sim.profile_read()
+    sim.profile_enable(False)
+    sim.sync()
+    n_now = sim.n
+    pb_now = sim.stats()["n_pblocks"]
+    sim.close()
+    avg = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in phases.items()}
+    algo = {"p2g": BYTES_P2G * n_now, "g2p": BYTES_G2P * n_now, "grid": BYTES_GRID_NODE * 64 * pb_now}
+    dom = max(("p2g", "grid", "g2p"), key=lambda k: phases[k][0])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "of measured" if hbm else "of fallback"
+    hbm = hbm or 6800.0
+    achieved = algo[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
+    src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", "substep.cu"), "rb").read()).hexdigest()
+    kernel_name = {"p2g": "k_p2g", "g2p": "k_g2p", "grid": "k_grid"}[dom]
+    roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": peak_note,
+                "algorithmic_bytes_per_launch": algo[dom], "avg_launch_ms": avg[dom],
+                "traffic": _traffic_for(kernel_name, src_hash),
+                "phases_ms_per_launch": {k: round(v, 5) for k, v in avg.items()},
+                "phase_launches": {k: v[1] for k, v in phases.items()}}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if args.e2e_frames > 0:
+        sim = fresh_sim()
+        host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
+                for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
+        sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
+                            Jp=host["Jp"])
+        per_frame = int(round(SUBSTEPS_PER_FRAME))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_frames):
+            sim.write_state(x=host["x"], v=host["v"], C=host["C"], F=host["F"], Jp=host["Jp"])
+            sim.run(per_frame, DT)
+            sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
+                                Jp=host["Jp"])
+        el = time.perf_counter() - t0
+        sim.close()
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        state_bytes = n * 4 * (3 + 3 + 9 + 9 + 1)
+        e2e = {"value": world * n * per_frame * args.e2e_frames / el, "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes / per_frame, "d2h_bytes_per_step": state_bytes / per_frame,
+               "protocol": "per frame: mpm_write_state of the full state from pinned host memory, %d mpm_substep "
+                           "calls, mpm_read_state of the full state into pinned host memory; bytes are per "
+                           "substep" % per_frame, "frames": args.e2e_frames}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, sample = oracle_throughput(x, seconds=15.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_frame": ms_per_step * SUBSTEPS_PER_FRAME,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
+            "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * libmpm -- one explicit MLS-MPM substep on a GB300 (sm_103a), behind a C ABI.
+ *
+ * Method: "Principles towards Real-Time Simulation of Material Point Method
+ * on Modern GPUs" (Fei, Huang, Gao).  One time step is the five phases of
+ * Sec. 4: rebuild-mapping (particle codes, block hash with the 3x3x3
+ * neighbour blocks, Sec. 4 and Sec. 4.2.1), particle sort to cell
+ * granularity (Sec. 4.2.2), particle-to-grid transfer with the stress
+ * computation merged in (Sec. 4.1), grid update with the boundary condition
+ * merged in (Sec. 4.1), and grid-to-particle transfer.  The first two phases
+ * run only when some particle is about to leave the blocks mapped at the
+ * last rebuild (the "free zone" of Sec. 4.2.1).  Transfers are MLS-MPM with
+ * quadratic B-splines (Sec. 6, [Hu et al. 2018]).
+ *
+ * Conventions for every call:
+ *   - Every entry point returns mpm_status (or a plain value where stated);
+ *     no C++ exception and no abort crosses this boundary.
+ *   - Pointers are plain host or device addresses; a call that takes
+ *     `on_device` reads/writes device memory when it is non-zero and host
+ *     memory when it is zero.  The library never keeps a caller pointer
+ *     beyond the call: inputs are copied in, outputs copied out.
+ *   - Work is enqueued on the CUDA stream given to mpm_create.  Calls marked
+ *     "syncs" wait for that stream; the others return before the GPU is done.
+ *   - Device-side failures (a particle leaving the domain, a non-finite
+ *     value) set a sticky error word; the next syncing call returns it and
+ *     mpm_last_error() describes it.
+ *   - All particle arrays crossing the ABI are in insertion order (the
+ *     order of mpm_add_particles calls), row-major FP32:
+ *     x, v: n x 3;  C, F: n x 3 x 3 with element (a, b) at 9 p + 3 a + b;
+ *     Jp: n (snow plastic volume ratio, or J for fluid particles).
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_ctx mpm_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_EINVAL = 1,     /* bad argument (null pointer, bad size, bad material) */
+    MPM_ENOMEM = 2,     /* the allocator returned NULL */
+    MPM_ECAPACITY = 3,  /* a fixed capacity (max_particles) would be exceeded */
+    MPM_EDOMAIN = 4,    /* a particle's 3x3x3 stencil left the grid, or outran the mapped blocks */
+    MPM_ENONFINITE = 5, /* a particle position became NaN or infinite */
+    MPM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+    MPM_ECUDA = 7,      /* a CUDA runtime call failed; see mpm_last_error */
+    MPM_ENOTSUP = 8     /* the request is valid but not supported by this build */
+} mpm_status;
+
+typedef enum { MPM_ELASTIC = 0, MPM_FLUID = 1, MPM_SNOW = 2, MPM_SAND = 3 } mpm_kind;
+typedef enum { MPM_STICKY = 0, MPM_SLIP = 1 } mpm_boundary;
+
+/* One material.  E is Young's modulus (for MPM_FLUID: the bulk modulus K).
+ * Fixed-corotated elastic [Stomakhin 2012]; snow = fixed-corotated on F_E
+ * with exp(hardening (1 - Jp)) and singular values clamped to
+ * [1 - theta_c, 1 + theta_s] [Stomakhin 2013]; fluid p = K (J^-gamma - 1)
+ * [Tampubolon 2017]; sand = Hencky-strain St. Venant-Kirchhoff with the
+ * Drucker-Prager return map for friction angle friction_deg [Klar 2016]. */
+typedef struct {
+    int32_t kind;          /* mpm_kind */
+    float E, nu, rho;
+    float gamma;           /* fluid exponent */
+    float theta_c, theta_s, hardening;
+    float friction_deg;
+} mpm_material;
+
+/* Grid and scene.  Nodes i = 0..res[a]-1 sit at i * dx.  Nodes with
+ * i < wall or i >= res - wall are wall nodes: sticky walls zero their
+ * velocity, slip walls zero the component pointing into the wall.
+ * Particle keys need 3L + 6 <= 32 bits with 4 * 2^L >= max(res):
+ * res up to 1024 per axis. */
+typedef struct {
+    int32_t res[3];
+    float dx;
+    int32_t boundary;      /* mpm_boundary */
+    int32_t wall;          /* wall layer thickness in nodes (3 is usual) */
+    float gravity[3];
+    int64_t max_particles; /* 0: grow without bound (4x when half full) */
+    int32_t use_g2p2g;     /* reserved: fused G2P2G transfer; 0 = separate phases */
+    int32_t reserved[7];
+} mpm_config;
+
+/* Device memory provider.  alloc returns device memory usable on `stream`
+ * or NULL; free releases it.  Pass NULL to mpm_create to use
+ * cudaMallocAsync / cudaFreeAsync on the context's stream. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* user);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+    void* user;
+} mpm_allocator;
+
+/* Create a simulation context (Sec. 4: the grid of 4x4x4 blocks and the
+ * empty particle set).  mats[0..n_mats-1] (n_mats <= 8) are copied.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream). */
+mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mats,
+                      const mpm_allocator* allocator, void* cuda_stream, mpm_ctx** out);
+
+/* Append n particles at rest-state F = I, C = 0, Jp = 1.  x: n x 3 positions;
+ * v: n x 3 velocities or NULL for zero; vol0: n rest volumes or NULL for
+ * dx^3 / 8 each; material: index into the context's materials.  Capacity
+ * grows to 4x the needed size when more than half full (Sec. 3.1, GPU
+ * container).  Marks the mapping for a rebuild.  Syncs. */
+mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
+                             const float* vol0, int material, int on_device);
+
+/* Advance by one substep of size dt: [rebuild-mapping and sort, when some
+ * particle neared the edge of its mapped blocks two substeps ago] ->
+ * P2G (stress merged in) -> grid update (boundary merged in, next buffer
+ * cleared) -> G2P (F update and return mapping merged in).  Asynchronous;
+ * a rebuild costs one host wait for the new block count. */
+mpm_status mpm_substep(mpm_ctx* ctx, float dt);
+
+/* Copy the particle state out in insertion order; any pointer may be NULL
+ * to skip that field.  Syncs; returns the sticky device error, if any. */
+mpm_status mpm_read_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, float* Jp,
+                          int on_device);
+
+/* Overwrite the particle state (insertion order); NULL fields are kept.
+ * Marks the mapping for a rebuild.  Syncs. */
+mpm_status mpm_write_state(mpm_ctx* ctx, const float* x, const float* v, const float* C,
+                           const float* F, const float* Jp, int on_device);
+
+/* Wait for the stream and return the sticky device error, if any. */
+mpm_status mpm_sync(mpm_ctx* ctx);
+
+/* Run rebuild-mapping and the full sort now (Sec. 4.2.1, Sec. 4.2.2). Syncs. */
+mpm_status mpm_rebuild(mpm_ctx* ctx);
+
+int64_t mpm_num_particles(const mpm_ctx* ctx);
+const char* mpm_last_error(const mpm_ctx* ctx); /* never NULL; owned by ctx */
+void mpm_destroy(mpm_ctx* ctx);                  /* NULL is a no-op; syncs */
+
+/* ---- introspection (tests, benchmarks) ------------------------------- */
+
+typedef struct {
+    int64_t substeps;      /* substeps run */
+    int64_t rebuilds;      /* rebuild-mapping runs */
+    int64_t n_pblocks;     /* physical blocks at the last rebuild */
+    int64_t grid_capacity; /* blocks the grid buffers can hold */
+    int64_t particle_capacity;
+    int64_t kernel_launches; /* kernels this context has launched */
+} mpm_stats;
+
+mpm_status mpm_get_stats(const mpm_ctx* ctx, mpm_stats* out);
+
+/* Sort keys of the particles in storage order after the last rebuild
+ * (Sec. 4.2.2: Morton(block) << 6 | Morton(cell), ascending) and the
+ * insertion index of each stored particle.  keys, ids: n entries each;
+ * either may be NULL.  Syncs. */
+mpm_status mpm_read_order(mpm_ctx* ctx, uint32_t* keys, int32_t* ids, int on_device);
+
+/* Physical blocks of the last rebuild (Sec. 4: gblocks and their 3x3x3
+ * neighbours) as Morton slots in block-index order (ascending).  Writes
+ * min(count, cap) entries to slots (may be NULL) and the count.  Syncs. */
+mpm_status mpm_read_blocks(mpm_ctx* ctx, int32_t* slots, int64_t cap, int64_t* count);
+
+/* Run the P2G phase for the current state with step dt into a fresh grid
+ * and copy the result out as a dense res0 x res1 x res2 array of
+ * (m, p_x, p_y, p_z) float quadruples, node (i, j, k) at
+ * 4 * (i + res0 * (j + res1 * k)).  Does not advance the simulation.
+ * Rebuilds first if needed.  Syncs. */
+mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device);
+
+/* Per-phase timing with CUDA events on the context's stream.  Phase ids:
+ * 0 rebuild, 1 P2G, 2 grid update, 3 G2P.  mpm_profile_read syncs and
+ * writes total milliseconds and launch counts per phase since the last
+ * read (n_phases <= 4 entries each). */
+#define MPM_PHASES 4
+mpm_status mpm_profile_enable(mpm_ctx* ctx, int on);
+mpm_status mpm_profile_read(mpm_ctx* ctx, double* ms, int64_t* launches, int n_phases);
+
+/* ---- stand-alone kernels ---------------------------------------------- */
+
+/* Stable LSD radix sort of (key, value) pairs on the device (the histogram
+ * sort of Sec. 4.2.2 with 8-bit digits over the low key_bits bits).
+ * keys_in/vals_in: n entries (read only); keys_out/vals_out: n entries.
+ * Scratch: call with scratch == NULL to get the byte count in
+ * *scratch_bytes; then pass a device buffer of at least that size (the
+ * preallocated scratch of Sec. 6.3.1).  Asynchronous on cuda_stream. */
+mpm_status mpm_radix_sort_pairs(const uint32_t* keys_in, const int32_t* vals_in,
+                                uint32_t* keys_out, int32_t* vals_out, int64_t n, int key_bits,
+                                void* scratch, size_t* scratch_bytes, void* cuda_stream);
+
+/* Batched SVD / stress evaluation of the constitutive model (Sec. 4.1:
+ * SVD, plasticity projection and stress computation), for testing the
+ * device routines in isolation.  F: n x 9, Jp: n; outputs U, V: n x 9,
+ * sig: n x 3, tau: n x 9 (any output may be NULL).  Device pointers.
+ * Syncs. */
+mpm_status mpm_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n);
+mpm_status mpm_debug_stress(const mpm_material* mat, const float* F, const float* Jp,
+                            float* tau, int64_t n);
+/* Apply the end-of-G2P return map to n trial F (in place) and Jp. */
+mpm_status mpm_debug_plasticity(const mpm_material* mat, float* F, float* Jp, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM_H */

@@ -1,0 +1,782 @@
+// Host side of libmpm: the context, memory management and the C ABI.
+//
+// Principles followed (Sec. 3.1): no reallocation once running except the
+// 4x-when-half-full growth of the particle and grid containers; the fewest
+// kernels per substep (P2G, grid update, G2P); no host/device sync in a
+// substep except one wait for the new block count when a rebuild runs.
+//
+// Rebuild trigger without a per-substep sync: G2P of substep s writes a flag
+// word when some particle's stencil, widened by one cell per side, reaches
+// an unmapped block.  Particles move less than one cell per substep (the CFL
+// condition), so that flag only has to be acted on before the P2G of
+// substep s + 2.  mpm_substep(s) therefore waits on the flag of substep
+// s - 2, which the GPU has finished while it runs substep s - 1: the host
+// never stalls the stream.  A particle that outruns the mapping anyway
+// (faster than one cell per substep) is reported as MPM_EDOMAIN, never
+// written out of bounds.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_math.cuh"
+#include "internal.h"
+
+using namespace mpm;
+
+namespace {
+
+constexpr int kRing = 4;
+
+struct ProfRec {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mpm_ctx {
+    mpm_config cfg{};
+    SimParams sp{};
+    mpm_allocator alloc{};
+    bool have_alloc = false;
+    cudaStream_t stream = nullptr;
+
+    // particles (double-buffered so the sort can permute out of place)
+    int64_t n = 0, cap = 0;
+    void* pbuf[2] = {nullptr, nullptr};
+    size_t pbuf_bytes = 0;
+    PartView pv[2]{};
+    int cur = 0;
+
+    // block table (direct-mapped by Morton code) and physical blocks
+    int64_t n_slots = 0;
+    int32_t* flags = nullptr;
+    int32_t* ranks = nullptr;
+    int32_t* table = nullptr;
+    int32_t* pslot = nullptr;
+    void* scan_scr = nullptr;
+    size_t scan_scr_bytes = 0;
+    int32_t n_pblocks = 0;
+    int64_t grid_cap = 0;
+    float4* grid[2] = {nullptr, nullptr};
+    int gcur = 0;
+
+    // sort
+    int64_t sort_cap = 0;
+    uint32_t* keys = nullptr;
+    int32_t* vals = nullptr;
+    uint32_t* skeys = nullptr;
+    int32_t* svals = nullptr;
+    void* sort_scr = nullptr;
+    size_t sort_scr_bytes = 0;
+    bool keys_valid = false;
+
+    // staging for host copies and layout changes
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+
+    // status: dstat[0] sticky error bits, dstat[1 + slot] per-substep flags,
+    // dstat[1 + kRing] block count of the last rebuild
+    uint32_t* dstat = nullptr;
+    uint32_t* hstat = nullptr;  // pinned mirror
+    cudaEvent_t ev[kRing] = {};
+    int64_t step = 0, last_rebuild = -1;
+    bool need_rebuild = true;
+
+    int64_t rebuilds = 0, launches = 0;
+    std::string err;
+
+    bool prof = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[MPM_PHASES] = {0, 0, 0, 0};
+    int64_t prof_launch[MPM_PHASES] = {0, 0, 0, 0};
+};
+
+namespace {
+
+mpm_status fail(mpm_ctx* c, mpm_status st, const char* msg)
+{
+    if (c)
+        c->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                              \
+            return MPM_ECUDA;                                                                           \
+        }                                                                                               \
+    } while (0)
+
+void* dalloc(mpm_ctx* ctx, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 256;
+    if (ctx->have_alloc)
+        return ctx->alloc.alloc(bytes, (void*)ctx->stream, ctx->alloc.user);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess)
+        return nullptr;
+    return p;
+}
+
+void dfree(mpm_ctx* ctx, void* p, size_t bytes)
+{
+    if (!p)
+        return;
+    if (bytes == 0)
+        bytes = 256;
+    if (ctx->have_alloc)
+        ctx->alloc.free(p, bytes, (void*)ctx->stream, ctx->alloc.user);
+    else
+        cudaFreeAsync(p, ctx->stream);
+}
+
+template <class T>
+mpm_status realloc_buf(mpm_ctx* ctx, T*& p, size_t& have, size_t want)
+{
+    if (want <= have && p)
+        return MPM_OK;
+    dfree(ctx, (void*)p, have);
+    p = (T*)dalloc(ctx, want);
+    have = p ? want : 0;
+    return p ? MPM_OK : fail(ctx, MPM_ENOMEM, "device allocation failed");
+}
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+size_t part_bytes(int64_t cap) { return (size_t)cap * (kChannels * 4 + 1 + 4) + 512; }
+
+PartView make_view(void* base, int64_t cap)
+{
+    PartView v;
+    v.soa = (float*)base;
+    v.cap = cap;
+    char* p = (char*)base + (size_t)cap * kChannels * 4;
+    v.id = (int32_t*)p;
+    v.mat = (uint8_t*)(p + (size_t)cap * 4);
+    return v;
+}
+
+// Phase timing helpers (events on the context's stream).
+void prof_begin(mpm_ctx* ctx, cudaEvent_t& a)
+{
+    if (!ctx->prof)
+        return;
+    if (ctx->ev_pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        a = e;
+    } else {
+        a = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+    }
+    cudaEventRecord(a, ctx->stream);
+}
+
+void prof_drain(mpm_ctx* ctx, size_t keep)
+{
+    while (ctx->prof_recs.size() > keep) {
+        ProfRec r = ctx->prof_recs.front();
+        ctx->prof_recs.erase(ctx->prof_recs.begin());
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        ctx->prof_ms[r.phase] += ms;
+        ctx->prof_launch[r.phase] += 1;
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+}
+
+void prof_end(mpm_ctx* ctx, int phase, cudaEvent_t a)
+{
+    if (!ctx->prof)
+        return;
+    cudaEvent_t b;
+    prof_begin(ctx, b);
+    ctx->prof_recs.push_back({phase, a, b});
+    if (ctx->prof_recs.size() > 4096)
+        prof_drain(ctx, 2048);
+}
+
+mpm_status device_error(mpm_ctx* ctx)
+{
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&ctx->hstat[kRing], ctx->dstat, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    e = ctx->hstat[kRing];
+    if (e & ST_ENONFINITE)
+        return fail(ctx, MPM_ENONFINITE, "a particle position became non-finite");
+    if (e & ST_EDOMAIN)
+        return fail(ctx, MPM_EDOMAIN, "a particle stencil left the grid");
+    if (e & ST_MISSED)
+        return fail(ctx, MPM_EDOMAIN, "a particle outran its mapped blocks (moved more than one cell per substep)");
+    return MPM_OK;
+}
+
+mpm_status ensure_particle_capacity(mpm_ctx* ctx, int64_t need)
+{
+    if (ctx->cfg.max_particles > 0 && need > ctx->cfg.max_particles)
+        return fail(ctx, MPM_ECAPACITY, "max_particles exceeded");
+    if (ctx->pbuf[0] && (need <= ctx->cap / 2 ||
+                         (ctx->cfg.max_particles > 0 && ctx->cap >= ctx->cfg.max_particles && need <= ctx->cap)))
+        return MPM_OK;
+    // Sec. 3.1: grow to 4x the requested size once more than half full.
+    int64_t ncap = round_up(4 * need, 256);
+    if (ctx->cfg.max_particles > 0 && ncap > ctx->cfg.max_particles)
+        ncap = round_up(ctx->cfg.max_particles, 256);
+    if (ncap > (int64_t)0x7fffff00)
+        return fail(ctx, MPM_ECAPACITY, "particle count exceeds 2^31");
+    size_t nb = part_bytes(ncap);
+    void* nbuf[2] = {dalloc(ctx, nb), dalloc(ctx, nb)};
+    if (!nbuf[0] || !nbuf[1]) {
+        dfree(ctx, nbuf[0], nb);
+        dfree(ctx, nbuf[1], nb);
+        return fail(ctx, MPM_ENOMEM, "particle allocation failed");
+    }
+    PartView nv = make_view(nbuf[0], ncap);
+    if (ctx->n > 0) {
+        const PartView& ov = ctx->pv[ctx->cur];
+        for (int c = 0; c < kChannels; ++c)
+            CK(cudaMemcpyAsync(nv.ch(c), ov.ch(c), (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(nv.id, ov.id, (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(nv.mat, ov.mat, (size_t)ctx->n, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    dfree(ctx, ctx->pbuf[0], ctx->pbuf_bytes);
+    dfree(ctx, ctx->pbuf[1], ctx->pbuf_bytes);
+    ctx->pbuf[0] = nbuf[0];
+    ctx->pbuf[1] = nbuf[1];
+    ctx->pbuf_bytes = nb;
+    ctx->pv[0] = nv;
+    ctx->pv[1] = make_view(nbuf[1], ncap);
+    ctx->cur = 0;
+    ctx->cap = ncap;
+    // sort buffers follow the particle capacity
+    size_t kb = (size_t)ncap * 4, have;
+    have = ctx->sort_cap * 4;
+    mpm_status st;
+    size_t h1 = have, h2 = have, h3 = have, h4 = have;
+    if ((st = realloc_buf(ctx, ctx->keys, h1, kb)) != MPM_OK) return st;
+    if ((st = realloc_buf(ctx, ctx->vals, h2, kb)) != MPM_OK) return st;
+    if ((st = realloc_buf(ctx, ctx->skeys, h3, kb)) != MPM_OK) return st;
+    if ((st = realloc_buf(ctx, ctx->svals, h4, kb)) != MPM_OK) return st;
+    ctx->sort_cap = ncap;
+    if ((st = realloc_buf(ctx, ctx->sort_scr, ctx->sort_scr_bytes, radix_sort_scratch_bytes(ncap))) != MPM_OK)
+        return st;
+    ctx->keys_valid = false;
+    return MPM_OK;
+}
+
+mpm_status ensure_stage(mpm_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->stage_bytes && ctx->stage)
+        return MPM_OK;
+    size_t want = bytes < 2 * ctx->stage_bytes ? 2 * ctx->stage_bytes : bytes;
+    return realloc_buf(ctx, ctx->stage, ctx->stage_bytes, want);
+}
+
+GridView grid_view(mpm_ctx* ctx)
+{
+    GridView g;
+    g.cur = ctx->grid[ctx->gcur];
+    g.nxt = ctx->grid[1 - ctx->gcur];
+    g.table = ctx->table;
+    g.pslot = ctx->pslot;
+    g.n_pblocks = ctx->n_pblocks;
+    return g;
+}
+
+// Rebuild-mapping + full sort (Sec. 4.2.1, Sec. 4.2.2).
+mpm_status rebuild(mpm_ctx* ctx)
+{
+    cudaEvent_t pa = nullptr;
+    prof_begin(ctx, pa);
+    cudaStream_t s = ctx->stream;
+    int64_t n = ctx->n;
+    const SimParams& sp = ctx->sp;
+    if (n > 0) {
+        launch_keys(sp, ctx->pv[ctx->cur], n, ctx->keys, ctx->vals, ctx->dstat, s);
+        ctx->launches += 1;
+        CK(radix_sort_pairs(ctx->keys, ctx->vals, ctx->skeys, ctx->svals, n, 3 * sp.L + 6, ctx->sort_scr, s,
+                            &ctx->launches));
+    }
+    CK(cudaMemsetAsync(ctx->flags, 0, (size_t)ctx->n_slots * 4, s));
+    launch_mark_pblocks(ctx->skeys, n, sp.L, ctx->flags, s);
+    CK(exclusive_scan(ctx->flags, ctx->ranks, ctx->n_slots, ctx->scan_scr, s, &ctx->launches));
+    launch_build_table(ctx->flags, ctx->ranks, ctx->n_slots, ctx->table, ctx->pslot,
+                       (int32_t*)&ctx->dstat[1 + kRing], s);
+    ctx->launches += 2;
+    if (n > 0) {
+        launch_permute(ctx->pv[ctx->cur], ctx->pv[1 - ctx->cur], ctx->svals, n, s);
+        ctx->launches += 1;
+        ctx->cur = 1 - ctx->cur;
+    }
+    CK(cudaMemcpyAsync(&ctx->hstat[kRing + 1], &ctx->dstat[1 + kRing], 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    int32_t npb = (int32_t)ctx->hstat[kRing + 1];
+    ctx->n_pblocks = npb;
+    if ((int64_t)npb > ctx->grid_cap / 2 || !ctx->grid[0]) {
+        int64_t gcap = 4 * (int64_t)npb;
+        if (gcap > ctx->n_slots)
+            gcap = ctx->n_slots;
+        if (gcap < 64)
+            gcap = 64;
+        size_t have0 = (size_t)ctx->grid_cap * 1024, have1 = have0;
+        mpm_status st;
+        if ((st = realloc_buf(ctx, ctx->grid[0], have0, (size_t)gcap * 1024)) != MPM_OK) return st;
+        if ((st = realloc_buf(ctx, ctx->grid[1], have1, (size_t)gcap * 1024)) != MPM_OK) return st;
+        ctx->grid_cap = gcap;
+    }
+    if (npb > 0) {
+        CK(cudaMemsetAsync(ctx->grid[0], 0, (size_t)npb * 1024, s));
+        CK(cudaMemsetAsync(ctx->grid[1], 0, (size_t)npb * 1024, s));
+    }
+    ctx->gcur = 0;
+    ctx->keys_valid = true;
+    ctx->need_rebuild = false;
+    ctx->last_rebuild = ctx->step;
+    ctx->rebuilds += 1;
+    prof_end(ctx, 0, pa);
+    return MPM_OK;
+}
+
+bool valid_material(const mpm_material& m)
+{
+    if (m.kind < MPM_ELASTIC || m.kind > MPM_SAND)
+        return false;
+    if (!(m.rho > 0.f) || !(m.E > 0.f))
+        return false;
+    if (m.kind != MPM_FLUID && !(m.nu > -1.f && m.nu < 0.5f))
+        return false;
+    if (m.kind == MPM_SNOW && !(m.theta_c >= 0.f && m.theta_c < 1.f && m.theta_s >= 0.f))
+        return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mats, const mpm_allocator* allocator,
+                      void* cuda_stream, mpm_ctx** out)
+{
+    if (!cfg || !out || !mats || n_mats < 1 || n_mats > kMaxMaterials)
+        return MPM_EINVAL;
+    *out = nullptr;
+    if (!(cfg->dx > 0.f) || cfg->wall < 0 || (cfg->boundary != MPM_STICKY && cfg->boundary != MPM_SLIP))
+        return MPM_EINVAL;
+    int maxres = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (cfg->res[a] < 8 || cfg->res[a] > 1024)
+            return MPM_EINVAL;
+        maxres = cfg->res[a] > maxres ? cfg->res[a] : maxres;
+    }
+    if (cfg->use_g2p2g != 0)
+        return MPM_ENOTSUP;
+    for (int i = 0; i < n_mats; ++i)
+        if (!valid_material(mats[i]))
+            return MPM_EINVAL;
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return MPM_EINVAL;
+    mpm_ctx* ctx = new (std::nothrow) mpm_ctx();
+    if (!ctx)
+        return MPM_ENOMEM;
+    ctx->cfg = *cfg;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (allocator) {
+        ctx->alloc = *allocator;
+        ctx->have_alloc = true;
+    }
+    SimParams& sp = ctx->sp;
+    for (int a = 0; a < 3; ++a) {
+        sp.res[a] = cfg->res[a];
+        sp.g[a] = cfg->gravity[a];
+    }
+    sp.dx = cfg->dx;
+    sp.inv_dx = 1.0f / cfg->dx;
+    sp.boundary = cfg->boundary;
+    sp.wall = cfg->wall;
+    int L = 0;
+    while ((4 << L) < maxres)
+        ++L;
+    sp.L = L;
+    sp.n_mats = n_mats;
+    for (int i = 0; i < n_mats; ++i)
+        sp.mat[i] = make_mat_params(mats[i]);
+    ctx->n_slots = (int64_t)1 << (3 * L);
+
+    mpm_status st = MPM_OK;
+    size_t b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
+    size_t sb = (size_t)ctx->n_slots * 4;
+    if ((st = realloc_buf(ctx, ctx->flags, b0, sb)) != MPM_OK ||
+        (st = realloc_buf(ctx, ctx->ranks, b1, sb)) != MPM_OK ||
+        (st = realloc_buf(ctx, ctx->table, b2, sb)) != MPM_OK ||
+        (st = realloc_buf(ctx, ctx->pslot, b3, sb)) != MPM_OK ||
+        (st = realloc_buf(ctx, ctx->dstat, b4, 256)) != MPM_OK ||
+        (st = realloc_buf(ctx, ctx->scan_scr, ctx->scan_scr_bytes, scan_scratch_bytes(ctx->n_slots))) != MPM_OK) {
+        mpm_destroy(ctx);
+        return st;
+    }
+    if (cudaMallocHost(&ctx->hstat, 256) != cudaSuccess) {
+        ctx->hstat = nullptr;
+        mpm_destroy(ctx);
+        return MPM_ENOMEM;
+    }
+    memset(ctx->hstat, 0, 256);
+    for (int i = 0; i < kRing; ++i)
+        if (cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            mpm_destroy(ctx);
+            return MPM_ECUDA;
+        }
+    if (cudaMemsetAsync(ctx->dstat, 0, 256, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->table, 0xff, sb, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        mpm_destroy(ctx);
+        return MPM_ECUDA;
+    }
+    *out = ctx;
+    return MPM_OK;
+}
+
+void mpm_destroy(mpm_ctx* ctx)
+{
+    if (!ctx)
+        return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->ev_pool)
+        cudaEventDestroy(e);
+    size_t sb = (size_t)ctx->n_slots * 4;
+    dfree(ctx, ctx->pbuf[0], ctx->pbuf_bytes);
+    dfree(ctx, ctx->pbuf[1], ctx->pbuf_bytes);
+    dfree(ctx, ctx->flags, sb);
+    dfree(ctx, ctx->ranks, sb);
+    dfree(ctx, ctx->table, sb);
+    dfree(ctx, ctx->pslot, sb);
+    dfree(ctx, ctx->scan_scr, ctx->scan_scr_bytes);
+    dfree(ctx, ctx->grid[0], (size_t)ctx->grid_cap * 1024);
+    dfree(ctx, ctx->grid[1], (size_t)ctx->grid_cap * 1024);
+    size_t kb = (size_t)ctx->sort_cap * 4;
+    dfree(ctx, ctx->keys, kb);
+    dfree(ctx, ctx->vals, kb);
+    dfree(ctx, ctx->skeys, kb);
+    dfree(ctx, ctx->svals, kb);
+    dfree(ctx, ctx->sort_scr, ctx->sort_scr_bytes);
+    dfree(ctx, ctx->stage, ctx->stage_bytes);
+    dfree(ctx, ctx->dstat, 256);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->hstat)
+        cudaFreeHost(ctx->hstat);
+    for (int i = 0; i < kRing; ++i)
+        if (ctx->ev[i])
+            cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+}
+
+mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v, const float* vol0,
+                             int material, int on_device)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    if (n < 0 || (n > 0 && !x) || material < 0 || material >= ctx->sp.n_mats)
+        return fail(ctx, MPM_EINVAL, "mpm_add_particles: bad argument");
+    if (n == 0)
+        return MPM_OK;
+    mpm_status st = ensure_particle_capacity(ctx, ctx->n + n);
+    if (st != MPM_OK)
+        return st;
+    const float *dx = x, *dv = v, *dvol = vol0;
+    if (!on_device) {
+        size_t bytes = (size_t)n * 4 * 7 + 1024;
+        if ((st = ensure_stage(ctx, bytes)) != MPM_OK)
+            return st;
+        float* sx = (float*)ctx->stage;
+        float* sv = sx + 3 * n;
+        float* svol = sv + 3 * n;
+        CK(cudaMemcpyAsync(sx, x, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream));
+        dx = sx;
+        if (v) {
+            CK(cudaMemcpyAsync(sv, v, (size_t)n * 12, cudaMemcpyHostToDevice, ctx->stream));
+            dv = sv;
+        }
+        if (vol0) {
+            CK(cudaMemcpyAsync(svol, vol0, (size_t)n * 4, cudaMemcpyHostToDevice, ctx->stream));
+            dvol = svol;
+        }
+    }
+    float dx3 = ctx->sp.dx * ctx->sp.dx * ctx->sp.dx;
+    launch_append(ctx->pv[ctx->cur], ctx->n, n, dx, dv, dvol, dx3 / 8.0f, material, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    ctx->n += n;
+    ctx->need_rebuild = true;
+    ctx->keys_valid = false;
+    return MPM_OK;
+}
+
+mpm_status mpm_substep(mpm_ctx* ctx, float dt)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    if (!(dt > 0.f))
+        return fail(ctx, MPM_EINVAL, "mpm_substep: dt must be positive");
+    if (ctx->n == 0) {
+        ctx->step += 1;
+        return MPM_OK;
+    }
+    // flag of substep step - 2 (see the file comment)
+    if (!ctx->need_rebuild && ctx->step >= 2 && ctx->step - 2 >= ctx->last_rebuild) {
+        int slot = (int)((ctx->step - 2) % kRing);
+        CK(cudaEventSynchronize(ctx->ev[slot]));
+        if (ctx->hstat[slot] & (ST_REBUILD_SOFT | ST_REBUILD_HARD))
+            ctx->need_rebuild = true;
+    }
+    if (ctx->need_rebuild) {
+        mpm_status st = rebuild(ctx);
+        if (st != MPM_OK)
+            return st;
+    }
+    cudaStream_t s = ctx->stream;
+    int slot = (int)(ctx->step % kRing);
+    CK(cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s));
+    GridView gv = grid_view(ctx);
+    const PartView& pv = ctx->pv[ctx->cur];
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    prof_begin(ctx, e0);
+    launch_p2g(ctx->sp, pv, gv, ctx->n, dt, ctx->dstat, s);
+    prof_end(ctx, 1, e0);
+    prof_begin(ctx, e1);
+    launch_grid_update(ctx->sp, gv, dt, s);
+    prof_end(ctx, 2, e1);
+    prof_begin(ctx, e2);
+    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, s);
+    prof_end(ctx, 3, e2);
+    ctx->launches += 3;
+    CK(cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev[slot], s));
+    CK(cudaGetLastError());
+    ctx->gcur = 1 - ctx->gcur;
+    ctx->step += 1;
+    return MPM_OK;
+}
+
+mpm_status mpm_sync(mpm_ctx* ctx)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    return device_error(ctx);
+}
+
+mpm_status mpm_rebuild(mpm_ctx* ctx)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    mpm_status st = rebuild(ctx);
+    if (st != MPM_OK)
+        return st;
+    return device_error(ctx);
+}
+
+mpm_status mpm_read_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, float* Jp, int on_device)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    float* outs[5] = {x, v, C, F, Jp};
+    static const int W[5] = {3, 3, 9, 9, 1};
+    int64_t n = ctx->n;
+    for (int f = 0; f < 5 && n > 0; ++f) {
+        if (!outs[f])
+            continue;
+        size_t bytes = (size_t)n * W[f] * 4;
+        if (on_device) {
+            launch_gather_out(ctx->pv[ctx->cur], n, f, outs[f], ctx->stream);
+        } else {
+            mpm_status st = ensure_stage(ctx, bytes);
+            if (st != MPM_OK)
+                return st;
+            launch_gather_out(ctx->pv[ctx->cur], n, f, (float*)ctx->stage, ctx->stream);
+            CK(cudaMemcpyAsync(outs[f], ctx->stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        ctx->launches += 1;
+    }
+    CK(cudaGetLastError());
+    return device_error(ctx);
+}
+
+mpm_status mpm_write_state(mpm_ctx* ctx, const float* x, const float* v, const float* C, const float* F,
+                           const float* Jp, int on_device)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    const float* ins[5] = {x, v, C, F, Jp};
+    static const int W[5] = {3, 3, 9, 9, 1};
+    int64_t n = ctx->n;
+    for (int f = 0; f < 5 && n > 0; ++f) {
+        if (!ins[f])
+            continue;
+        size_t bytes = (size_t)n * W[f] * 4;
+        if (on_device) {
+            launch_scatter_in(ctx->pv[ctx->cur], n, f, ins[f], ctx->stream);
+        } else {
+            mpm_status st = ensure_stage(ctx, bytes);
+            if (st != MPM_OK)
+                return st;
+            CK(cudaMemcpyAsync(ctx->stage, ins[f], bytes, cudaMemcpyHostToDevice, ctx->stream));
+            launch_scatter_in(ctx->pv[ctx->cur], n, f, (const float*)ctx->stage, ctx->stream);
+            // the stage buffer is reused by the next field: order the copies
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+        ctx->launches += 1;
+    }
+    if (x) {
+        ctx->need_rebuild = true;
+        ctx->keys_valid = false;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    return MPM_OK;
+}
+
+int64_t mpm_num_particles(const mpm_ctx* ctx) { return ctx ? ctx->n : 0; }
+
+const char* mpm_last_error(const mpm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mpm_status mpm_get_stats(const mpm_ctx* ctx, mpm_stats* out)
+{
+    if (!ctx || !out)
+        return MPM_EINVAL;
+    out->substeps = ctx->step;
+    out->rebuilds = ctx->rebuilds;
+    out->n_pblocks = ctx->n_pblocks;
+    out->grid_capacity = ctx->grid_cap;
+    out->particle_capacity = ctx->cap;
+    out->kernel_launches = ctx->launches;
+    return MPM_OK;
+}
+
+mpm_status mpm_read_order(mpm_ctx* ctx, uint32_t* keys, int32_t* ids, int on_device)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    if (!ctx->keys_valid)
+        return fail(ctx, MPM_EINVAL, "mpm_read_order: no rebuild since the particles last changed");
+    size_t bytes = (size_t)ctx->n * 4;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (keys && bytes)
+        CK(cudaMemcpyAsync(keys, ctx->skeys, bytes, k, ctx->stream));
+    if (ids && bytes)
+        CK(cudaMemcpyAsync(ids, ctx->pv[ctx->cur].id, bytes, k, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MPM_OK;
+}
+
+mpm_status mpm_read_blocks(mpm_ctx* ctx, int32_t* slots, int64_t cap, int64_t* count)
+{
+    if (!ctx || !count || cap < 0)
+        return MPM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    *count = ctx->n_pblocks;
+    int64_t m = cap < ctx->n_pblocks ? cap : ctx->n_pblocks;
+    if (slots && m > 0)
+        CK(cudaMemcpy(slots, ctx->pslot, (size_t)m * 4, cudaMemcpyDeviceToHost));
+    return MPM_OK;
+}
+
+mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
+{
+    if (!ctx || !grid_out)
+        return MPM_EINVAL;
+    if (ctx->need_rebuild || ctx->n == 0) {
+        mpm_status st = rebuild(ctx);
+        if (st != MPM_OK)
+            return st;
+    }
+    cudaStream_t s = ctx->stream;
+    int64_t nodes = (int64_t)ctx->sp.res[0] * ctx->sp.res[1] * ctx->sp.res[2];
+    size_t bytes = (size_t)nodes * 16;
+    float* dense = grid_out;
+    if (!on_device) {
+        mpm_status st = ensure_stage(ctx, bytes);
+        if (st != MPM_OK)
+            return st;
+        dense = (float*)ctx->stage;
+    }
+    CK(cudaMemsetAsync(dense, 0, bytes, s));
+    GridView gv = grid_view(ctx);
+    launch_p2g(ctx->sp, ctx->pv[ctx->cur], gv, ctx->n, dt, ctx->dstat, s);
+    launch_grid_to_dense(ctx->sp, gv.cur, ctx->pslot, ctx->n_pblocks, dense, s);
+    ctx->launches += 2;
+    if (ctx->n_pblocks > 0)
+        CK(cudaMemsetAsync(gv.cur, 0, (size_t)ctx->n_pblocks * 1024, s));
+    if (!on_device)
+        CK(cudaMemcpyAsync(grid_out, dense, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaGetLastError());
+    return device_error(ctx);
+}
+
+mpm_status mpm_profile_enable(mpm_ctx* ctx, int on)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    ctx->prof = on != 0;
+    return MPM_OK;
+}
+
+mpm_status mpm_profile_read(mpm_ctx* ctx, double* ms, int64_t* launches, int n_phases)
+{
+    if (!ctx || n_phases < 0 || n_phases > MPM_PHASES)
+        return MPM_EINVAL;
+    prof_drain(ctx, 0);
+    for (int i = 0; i < n_phases; ++i) {
+        if (ms)
+            ms[i] = ctx->prof_ms[i];
+        if (launches)
+            launches[i] = ctx->prof_launch[i];
+    }
+    for (int i = 0; i < MPM_PHASES; ++i) {
+        ctx->prof_ms[i] = 0;
+        ctx->prof_launch[i] = 0;
+    }
+    return MPM_OK;
+}
+
+mpm_status mpm_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n)
+{
+    if (!F || n < 0)
+        return MPM_EINVAL;
+    launch_debug_svd(F, U, sig, V, n, 0);
+    return cudaDeviceSynchronize() == cudaSuccess && cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ECUDA;
+}
+
+mpm_status mpm_debug_stress(const mpm_material* mat, const float* F, const float* Jp, float* tau, int64_t n)
+{
+    if (!mat || !F || !tau || n < 0 || !valid_material(*mat))
+        return MPM_EINVAL;
+    launch_debug_stress(make_mat_params(*mat), F, Jp, tau, n, 0);
+    return cudaDeviceSynchronize() == cudaSuccess && cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ECUDA;
+}
+
+mpm_status mpm_debug_plasticity(const mpm_material* mat, float* F, float* Jp, int64_t n)
+{
+    if (!mat || !F || n < 0 || !valid_material(*mat))
+        return MPM_EINVAL;
+    launch_debug_plasticity(make_mat_params(*mat), F, Jp, n, 0);
+    return cudaDeviceSynchronize() == cudaSuccess && cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ECUDA;
+}
+
+}  // extern "C"

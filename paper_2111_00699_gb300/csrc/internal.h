@@ -1,0 +1,102 @@
+// Internal types shared by the libmpm translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpm.h"
+
+namespace mpm {
+
+constexpr int kMaxMaterials = 8;
+
+// Particle SoA channels: one float array of `cap` entries per channel.
+enum Channel : int {
+    CH_X = 0,    // x, y, z
+    CH_V = 3,    // velocity
+    CH_C = 6,    // affine velocity C (row-major 3x3)
+    CH_F = 15,   // deformation gradient F (row-major 3x3)
+    CH_JP = 24,  // snow Jp / fluid J
+    CH_VOL = 25, // rest volume
+    kChannels = 26
+};
+
+// Device status word bits.
+enum : uint32_t {
+    ST_REBUILD_SOFT = 1u,  // a particle's next stencil may reach an unmapped block
+    ST_REBUILD_HARD = 2u,  // a particle's stencil reached an unmapped block
+    ST_EDOMAIN = 4u,       // a stencil left the grid
+    ST_ENONFINITE = 8u,    // a position became non-finite
+    ST_MISSED = 16u,       // P2G/G2P found an unmapped block (CFL violated)
+};
+
+struct MatParams {
+    int kind;
+    float mu, la, rho;
+    float K, gamma;          // fluid
+    float lo, hi, xi;        // snow clamp bounds, hardening
+    float alpha, dp_coef;    // sand: cone slope, (3 la + 2 mu) / (2 mu)
+};
+
+struct SimParams {
+    int res[3];
+    float dx, inv_dx;
+    int boundary, wall;
+    float g[3];
+    int L;                   // Morton bits per axis of the block table
+    int n_mats;
+    MatParams mat[kMaxMaterials];
+};
+
+struct PartView {
+    float* soa;     // kChannels x cap floats
+    int64_t cap;
+    uint8_t* mat;
+    int32_t* id;
+    __host__ __device__ float* ch(int c) const { return soa + (int64_t)c * cap; }
+};
+
+struct GridView {
+    float4* cur;          // (p or v, m) per node, 64 nodes per physical block
+    float4* nxt;          // buffer for the next substep (cleared by the grid update)
+    const int32_t* table; // Morton slot -> physical block index, or -1
+    const int32_t* pslot; // physical block index -> Morton slot
+    int32_t n_pblocks;
+};
+
+// ---- launchers implemented in the .cu files -------------------------------
+
+// sort.cu
+size_t radix_sort_scratch_bytes(int64_t n);
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t radix_sort_pairs(const uint32_t* kin, const int32_t* vin, uint32_t* kout, int32_t* vout,
+                             int64_t n, int key_bits, void* scratch, cudaStream_t s, int64_t* launches);
+cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, void* scratch, cudaStream_t s,
+                           int64_t* launches);
+
+// rebuild.cu
+void launch_keys(const SimParams& sp, const PartView& pv, int64_t n, uint32_t* keys, int32_t* vals,
+                 uint32_t* err, cudaStream_t s);
+void launch_mark_pblocks(const uint32_t* skeys, int64_t n, int L, int32_t* flags, cudaStream_t s);
+void launch_build_table(const int32_t* flags, const int32_t* ranks, int64_t n_slots, int32_t* table,
+                        int32_t* pslot, int32_t* n_pblocks, cudaStream_t s);
+void launch_permute(const PartView& src, const PartView& dst, const int32_t* perm, int64_t n, cudaStream_t s);
+void launch_append(const PartView& pv, int64_t n0, int64_t n, const float* x, const float* v,
+                   const float* vol, float default_vol, int material, cudaStream_t s);
+void launch_gather_out(const PartView& pv, int64_t n, int field, float* out, cudaStream_t s);
+void launch_scatter_in(const PartView& pv, int64_t n, int field, const float* in, cudaStream_t s);
+void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t* pslot, int32_t n_pblocks,
+                          float* dense, cudaStream_t s);
+
+// substep.cu
+void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
+                uint32_t* err, cudaStream_t s);
+void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s);
+void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
+                uint32_t* flags, uint32_t* err, cudaStream_t s);
+MatParams make_mat_params(const mpm_material& m);
+void launch_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n, cudaStream_t s);
+void launch_debug_stress(const MatParams& mp, const float* F, const float* Jp, float* tau, int64_t n,
+                         cudaStream_t s);
+void launch_debug_plasticity(const MatParams& mp, float* F, float* Jp, int64_t n, cudaStream_t s);
+
+}  // namespace mpm

@@ -1,0 +1,236 @@
+// Rebuild-mapping (Sec. 4 and Sec. 4.2.1) and particle bookkeeping kernels.
+//
+// The block "hash" is direct-mapped: a table with one int32 per block of
+// the whole domain, indexed by the block's Morton code.  On a GB300 (288 GB
+// HBM, 129 MB L2) that table is 1 MB for a 256^3 grid and stays in L2, so a
+// lookup is one cached load with no probing.  Physical-block indices are the
+// ranks of the Morton codes of the marked blocks (a scan over the table),
+// which makes the mapping deterministic.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device_math.cuh"
+#include "internal.h"
+
+namespace mpm {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n + per - 1) / per); }
+
+// Particle code (Sec. 4): base node per axis with the -dx/2 shift of the
+// particle blocks; key = Morton(block) << 6 | Morton(cell within block).
+__global__ void k_keys(SimParams sp, PartView pv, int64_t n, uint32_t* __restrict__ keys,
+                       int32_t* __restrict__ vals, uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    int b[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float x = pv.ch(CH_X + a)[p];
+        b[a] = base_of(x, sp.inv_dx);
+        ok = ok && isfinite(x) && b[a] >= 0 && b[a] + 2 < sp.res[a] && (b[a] >> 2) < (1 << sp.L);
+    }
+    uint32_t key = 0xffffffffu;
+    if (ok) {
+        uint32_t blk = morton3((uint32_t)b[0] >> 2, (uint32_t)b[1] >> 2, (uint32_t)b[2] >> 2);
+        uint32_t cell = morton3((uint32_t)b[0] & 3u, (uint32_t)b[1] & 3u, (uint32_t)b[2] & 3u);
+        key = (blk << 6) | cell;
+    } else {
+        atomicOr(err, ST_EDOMAIN);
+    }
+    keys[p] = key;
+    vals[p] = (int32_t)p;
+}
+
+// Mark the 3x3x3 neighbourhood of every gblock (the first particle of each
+// run of equal block codes in the sorted keys does the marking).
+__global__ void k_mark(const uint32_t* __restrict__ skeys, int64_t n, int L, int32_t* __restrict__ flags)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    uint32_t k = skeys[i];
+    if (k == 0xffffffffu)
+        return;
+    uint32_t code = k >> 6;
+    if (i > 0 && (skeys[i - 1] >> 6) == code)
+        return;
+    int bx = (int)compact3(code), by = (int)compact3(code >> 1), bz = (int)compact3(code >> 2);
+    int side = 1 << L;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = bx + dx, y = by + dy, z = bz + dz;
+                if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side)
+                    continue;
+                flags[morton3((uint32_t)x, (uint32_t)y, (uint32_t)z)] = 1;
+            }
+}
+
+__global__ void k_table(const int32_t* __restrict__ flags, const int32_t* __restrict__ ranks, int64_t n_slots,
+                        int32_t* __restrict__ table, int32_t* __restrict__ pslot, int32_t* __restrict__ n_pblocks)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slots)
+        return;
+    int f = flags[s];
+    int r = ranks[s];
+    table[s] = f ? r : -1;
+    if (f)
+        pslot[r] = (int32_t)s;
+    if (s == n_slots - 1)
+        *n_pblocks = r + f;
+}
+
+// dst[i] = src[perm[i]] for every channel, the material and the id.
+__global__ void k_permute(PartView src, PartView dst, const int32_t* __restrict__ perm, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t j = perm[i];
+#pragma unroll 2
+    for (int c = 0; c < kChannels; ++c)
+        dst.ch(c)[i] = src.ch(c)[j];
+    dst.mat[i] = src.mat[j];
+    dst.id[i] = src.id[j];
+}
+
+__global__ void k_append(PartView pv, int64_t n0, int64_t n, const float* __restrict__ x,
+                         const float* __restrict__ v, const float* __restrict__ vol, float default_vol, int material)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t p = n0 + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        pv.ch(CH_X + a)[p] = x[3 * i + a];
+        pv.ch(CH_V + a)[p] = v ? v[3 * i + a] : 0.0f;
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        pv.ch(CH_C + e)[p] = 0.0f;
+        pv.ch(CH_F + e)[p] = (e % 4 == 0) ? 1.0f : 0.0f;
+    }
+    pv.ch(CH_JP)[p] = 1.0f;
+    pv.ch(CH_VOL)[p] = vol ? vol[i] : default_vol;
+    pv.mat[p] = (uint8_t)material;
+    pv.id[p] = (int32_t)p;
+}
+
+// out[id[i] * width + e] = channel(first + e)[i]: storage order -> insertion order.
+__global__ void k_gather_out(PartView pv, int64_t n, int first, int width, float* __restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t q = pv.id[i];
+    for (int e = 0; e < width; ++e)
+        out[q * width + e] = pv.ch(first + e)[i];
+}
+
+__global__ void k_scatter_in(PartView pv, int64_t n, int first, int width, const float* __restrict__ in)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t q = pv.id[i];
+    for (int e = 0; e < width; ++e)
+        pv.ch(first + e)[i] = in[q * width + e];
+}
+
+__global__ void k_grid_to_dense(SimParams sp, const float4* __restrict__ grid, const int32_t* __restrict__ pslot,
+                                int32_t n_pblocks, float* __restrict__ dense)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_pblocks * 64)
+        return;
+    int pb = (int)(idx >> 6), l = (int)(idx & 63);
+    uint32_t s = (uint32_t)pslot[pb];
+    int i = 4 * (int)compact3(s) + (l & 3);
+    int j = 4 * (int)compact3(s >> 1) + ((l >> 2) & 3);
+    int k = 4 * (int)compact3(s >> 2) + (l >> 4);
+    if (i >= sp.res[0] || j >= sp.res[1] || k >= sp.res[2])
+        return;
+    float4 g = grid[idx];
+    int64_t o = 4 * ((int64_t)i + (int64_t)sp.res[0] * ((int64_t)j + (int64_t)sp.res[1] * k));
+    dense[o + 0] = g.w;
+    dense[o + 1] = g.x;
+    dense[o + 2] = g.y;
+    dense[o + 3] = g.z;
+}
+
+}  // namespace
+
+void launch_keys(const SimParams& sp, const PartView& pv, int64_t n, uint32_t* keys, int32_t* vals, uint32_t* err,
+                 cudaStream_t s)
+{
+    if (n > 0)
+        k_keys<<<blocks_for(n), kBlock, 0, s>>>(sp, pv, n, keys, vals, err);
+}
+
+void launch_mark_pblocks(const uint32_t* skeys, int64_t n, int L, int32_t* flags, cudaStream_t s)
+{
+    if (n > 0)
+        k_mark<<<blocks_for(n), kBlock, 0, s>>>(skeys, n, L, flags);
+}
+
+void launch_build_table(const int32_t* flags, const int32_t* ranks, int64_t n_slots, int32_t* table,
+                        int32_t* pslot, int32_t* n_pblocks, cudaStream_t s)
+{
+    k_table<<<blocks_for(n_slots), kBlock, 0, s>>>(flags, ranks, n_slots, table, pslot, n_pblocks);
+}
+
+void launch_permute(const PartView& src, const PartView& dst, const int32_t* perm, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        k_permute<<<blocks_for(n), kBlock, 0, s>>>(src, dst, perm, n);
+}
+
+void launch_append(const PartView& pv, int64_t n0, int64_t n, const float* x, const float* v, const float* vol,
+                   float default_vol, int material, cudaStream_t s)
+{
+    if (n > 0)
+        k_append<<<blocks_for(n), kBlock, 0, s>>>(pv, n0, n, x, v, vol, default_vol, material);
+}
+
+// field: 0 x, 1 v, 2 C, 3 F, 4 Jp
+static void field_range(int field, int& first, int& width)
+{
+    static const int F0[5] = {CH_X, CH_V, CH_C, CH_F, CH_JP};
+    static const int W[5] = {3, 3, 9, 9, 1};
+    first = F0[field];
+    width = W[field];
+}
+
+void launch_gather_out(const PartView& pv, int64_t n, int field, float* out, cudaStream_t s)
+{
+    int first, width;
+    field_range(field, first, width);
+    if (n > 0)
+        k_gather_out<<<blocks_for(n), kBlock, 0, s>>>(pv, n, first, width, out);
+}
+
+void launch_scatter_in(const PartView& pv, int64_t n, int field, const float* in, cudaStream_t s)
+{
+    int first, width;
+    field_range(field, first, width);
+    if (n > 0)
+        k_scatter_in<<<blocks_for(n), kBlock, 0, s>>>(pv, n, first, width, in);
+}
+
+void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t* pslot, int32_t n_pblocks,
+                          float* dense, cudaStream_t s)
+{
+    if (n_pblocks > 0)
+        k_grid_to_dense<<<blocks_for((int64_t)n_pblocks * 64), kBlock, 0, s>>>(sp, grid, pslot, n_pblocks, dense);
+}
+
+}  // namespace mpm

@@ -1,0 +1,436 @@
+// The three essential phases of one MLS-MPM substep (Sec. 4): P2G with the
+// stress computation merged in (Sec. 4.1), the grid update with the boundary
+// condition and the clearing of the next buffer merged in (Sec. 4.1), and
+// G2P with the F update, the return mapping and the free-zone test merged in.
+//
+// Layout: particles are SoA float channels (coalesced per warp); grid nodes
+// are float4 (p_x, p_y, p_z, m) -- after the update (v_x, v_y, v_z, m) -- in
+// physical blocks of 4x4x4 = 64 nodes, node (i, j, k) of a block at
+// (i & 3) + 4 (j & 3) + 16 (k & 3).  A node's block index comes from the
+// direct-mapped Morton table.  P2G adds into the grid with native global
+// float4 atomics (Sec. 4.3: native atomics only, no shared-memory float
+// atomics, no __syncthreads).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "device_math.cuh"
+#include "internal.h"
+
+namespace mpm {
+
+namespace {
+
+constexpr int kTransferThreads = 128;  // 4 warps per CUDA block (Sec. 6.2)
+
+// The physical blocks a 3-node stencil starting at base b touches: per axis
+// the block b >> 2 and, when (b & 3) >= 2, also the next one.  pb[dz][dy][dx]
+// (flattened dx + 2 dy + 4 dz) receives the block indices; returns false if
+// one of them is not mapped.
+__device__ __forceinline__ bool stencil_blocks(const GridView& gv, const int* b, int* pb)
+{
+    uint32_t sx[2], sy[2], sz[2];
+    int B0 = b[0] >> 2, B1 = b[1] >> 2, B2 = b[2] >> 2;
+    sx[0] = spread3((uint32_t)B0);
+    sx[1] = spread3((uint32_t)B0 + 1u);
+    sy[0] = spread3((uint32_t)B1) << 1;
+    sy[1] = spread3((uint32_t)B1 + 1u) << 1;
+    sz[0] = spread3((uint32_t)B2) << 2;
+    sz[1] = spread3((uint32_t)B2 + 1u) << 2;
+    int cx = (b[0] & 3) >= 2, cy = (b[1] & 3) >= 2, cz = (b[2] & 3) >= 2;
+    bool ok = true;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                int v = 0;
+                if ((dx <= cx) && (dy <= cy) && (dz <= cz)) {
+                    v = __ldg(&gv.table[sx[dx] | sy[dy] | sz[dz]]);
+                    ok = ok && v >= 0;
+                }
+                pb[dx + 2 * dy + 4 * dz] = v;
+            }
+    return ok;
+}
+
+// The 3x3x3 stencil at base b lies inside the grid.
+__device__ __forceinline__ bool in_grid(const SimParams& sp, const int* b, const float* x)
+{
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        ok = ok && isfinite(x[a]) && b[a] >= 0 && b[a] + 2 < sp.res[a];
+    return ok;
+}
+
+__global__ void __launch_bounds__(kTransferThreads) k_p2g(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                          float dt, uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float x[3], f[3], w[3][3];
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = pv.ch(CH_X + a)[p];
+        b[a] = base_of(x[a], sp.inv_dx);
+        f[a] = __fmul_rn(x[a], sp.inv_dx) - (float)b[a];
+        bspline(f[a], w[a]);
+    }
+    if (!in_grid(sp, b, x)) {
+        atomicOr(err, ST_EDOMAIN);
+        return;
+    }
+    int pb[8];
+    if (!stencil_blocks(gv, b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+    const MatParams m = sp.mat[pv.mat[p]];
+    float F[9], tau[9];
+    float Jp = pv.ch(CH_JP)[p];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        F[e] = (m.kind != MPM_FLUID) ? pv.ch(CH_F + e)[p] : ((e % 4 == 0) ? 1.0f : 0.0f);
+    kirchhoff(m, F, Jp, tau);
+    float vol = pv.ch(CH_VOL)[p];
+    float mp = m.rho * vol;
+    float kst = 4.0f * dt * vol * sp.inv_dx * sp.inv_dx;
+    // A = (m C - k tau) dx so that A (node - f) = (m C - k tau)(x_i - x_p)
+    float A[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        A[e] = (mp * pv.ch(CH_C + e)[p] - kst * tau[e]) * sp.dx;
+    float mv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        mv[a] = mp * pv.ch(CH_V + a)[p];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int nz = (b[2] & 3) + k;
+        float dz = (float)k - f[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int ny = (b[1] & 3) + j;
+            float dy = (float)j - f[1];
+            float wyz = w[1][j] * w[2][k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                int nx = (b[0] & 3) + i;
+                float dxo = (float)i - f[0];
+                float wt = w[0][i] * wyz;
+                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
+                float4 val;
+                val.x = wt * (mv[0] + A[0] * dxo + A[1] * dy + A[2] * dz);
+                val.y = wt * (mv[1] + A[3] * dxo + A[4] * dy + A[5] * dz);
+                val.z = wt * (mv[2] + A[6] * dxo + A[7] * dy + A[8] * dz);
+                val.w = wt * mp;
+                atomicAdd(&gv.cur[(int64_t)blk * 64 + local], val);
+            }
+        }
+    }
+}
+
+__global__ void k_grid(SimParams sp, GridView gv, float dt)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)gv.n_pblocks * 64)
+        return;
+    float4 g = gv.cur[idx];
+    gv.nxt[idx] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float v[3] = {0.0f, 0.0f, 0.0f};
+    if (g.w > 0.0f) {
+        float im = 1.0f / g.w;
+        v[0] = g.x * im + dt * sp.g[0];
+        v[1] = g.y * im + dt * sp.g[1];
+        v[2] = g.z * im + dt * sp.g[2];
+        uint32_t s = (uint32_t)gv.pslot[idx >> 6];
+        int l = (int)(idx & 63);
+        int c[3] = {4 * (int)compact3(s) + (l & 3), 4 * (int)compact3(s >> 1) + ((l >> 2) & 3),
+                    4 * (int)compact3(s >> 2) + (l >> 4)};
+        if (sp.boundary == MPM_STICKY) {
+            bool wall = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                wall = wall || c[a] < sp.wall || c[a] >= sp.res[a] - sp.wall;
+            if (wall)
+                v[0] = v[1] = v[2] = 0.0f;
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (c[a] < sp.wall && v[a] < 0.0f)
+                    v[a] = 0.0f;
+                if (c[a] >= sp.res[a] - sp.wall && v[a] > 0.0f)
+                    v[a] = 0.0f;
+            }
+        }
+    }
+    gv.cur[idx] = make_float4(v[0], v[1], v[2], g.w);
+}
+
+// True if every node in [lo, hi] (per axis, clipped to the grid) lies in a
+// mapped block.
+__device__ __forceinline__ bool range_mapped(const SimParams& sp, const GridView& gv, const int* lo, const int* hi)
+{
+    int B0[3], B1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int l = max(lo[a], 0), h = min(hi[a], sp.res[a] - 1);
+        B0[a] = l >> 2;
+        B1[a] = h >> 2;
+    }
+    bool ok = true;
+    for (int z = B0[2]; z <= B1[2]; ++z)
+        for (int y = B0[1]; y <= B1[1]; ++y)
+            for (int x = B0[0]; x <= B1[0]; ++x)
+                ok = ok && __ldg(&gv.table[morton3((uint32_t)x, (uint32_t)y, (uint32_t)z)]) >= 0;
+    return ok;
+}
+
+__global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                          float dt, uint32_t* __restrict__ flags,
+                                                          uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float x[3], f[3], w[3][3];
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = pv.ch(CH_X + a)[p];
+        b[a] = base_of(x[a], sp.inv_dx);
+        f[a] = __fmul_rn(x[a], sp.inv_dx) - (float)b[a];
+        bspline(f[a], w[a]);
+    }
+    if (!in_grid(sp, b, x)) {
+        atomicOr(err, ST_EDOMAIN);
+        return;
+    }
+    int pb[8];
+    if (!stencil_blocks(gv, b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+    float vp[3] = {0.0f, 0.0f, 0.0f};
+    float Bm[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        Bm[e] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int nz = (b[2] & 3) + k;
+        float dz = (float)k - f[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int ny = (b[1] & 3) + j;
+            float dy = (float)j - f[1];
+            float wyz = w[1][j] * w[2][k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                int nx = (b[0] & 3) + i;
+                float dxo = (float)i - f[0];
+                float wt = w[0][i] * wyz;
+                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
+                float4 g = gv.cur[(int64_t)blk * 64 + local];
+                float gx = wt * g.x, gy = wt * g.y, gz = wt * g.z;
+                vp[0] += gx;
+                vp[1] += gy;
+                vp[2] += gz;
+                Bm[0] += gx * dxo; Bm[1] += gx * dy; Bm[2] += gx * dz;
+                Bm[3] += gy * dxo; Bm[4] += gy * dy; Bm[5] += gy * dz;
+                Bm[6] += gz * dxo; Bm[7] += gz * dy; Bm[8] += gz * dz;
+            }
+        }
+    }
+    // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
+    float C[9];
+    float c4 = 4.0f * sp.inv_dx;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        C[e] = c4 * Bm[e];
+        pv.ch(CH_C + e)[p] = C[e];
+    }
+    float xn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xn[a] = x[a] + dt * vp[a];
+        pv.ch(CH_X + a)[p] = xn[a];
+        pv.ch(CH_V + a)[p] = vp[a];
+    }
+    const MatParams m = sp.mat[pv.mat[p]];
+    float Jp = pv.ch(CH_JP)[p];
+    if (m.kind == MPM_FLUID) {
+        Jp *= 1.0f + dt * (C[0] + C[4] + C[8]);
+        pv.ch(CH_JP)[p] = Jp;
+    } else {
+        float F[9], Fn[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            F[e] = pv.ch(CH_F + e)[p];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Fn[3 * r + c] = F[3 * r + c] + dt * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
+        float Jn = Jp;
+        plasticity(m, Fn, Jn);
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            pv.ch(CH_F + e)[p] = Fn[e];
+        if (m.kind == MPM_SNOW)
+            pv.ch(CH_JP)[p] = Jn;
+    }
+    // Free-zone test (Sec. 4.2.1): while every particle's stencil stays in
+    // mapped blocks no rebuild is needed.  A particle that changed cell
+    // checks the stencil one cell wider on each side (one more substep of
+    // travel); failing that asks for a rebuild before the substep after next.
+    int bn[3];
+    bool moved = false, bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        bad = bad || !isfinite(xn[a]);
+        bn[a] = base_of(xn[a], sp.inv_dx);
+        moved = moved || bn[a] != b[a];
+    }
+    if (bad) {
+        atomicOr(err, ST_ENONFINITE);
+        return;
+    }
+    if (moved) {
+        bool dom = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            dom = dom && bn[a] >= 0 && bn[a] + 2 < sp.res[a] && ((bn[a] + 2) >> 2) < (1 << sp.L);
+        if (!dom) {
+            atomicOr(err, ST_EDOMAIN);
+            return;
+        }
+        int lo[3] = {bn[0] - 1, bn[1] - 1, bn[2] - 1}, hi[3] = {bn[0] + 3, bn[1] + 3, bn[2] + 3};
+        if (!range_mapped(sp, gv, lo, hi)) {
+            int lo2[3] = {bn[0], bn[1], bn[2]}, hi2[3] = {bn[0] + 2, bn[1] + 2, bn[2] + 2};
+            atomicOr(flags, range_mapped(sp, gv, lo2, hi2) ? ST_REBUILD_SOFT : (ST_REBUILD_SOFT | ST_REBUILD_HARD));
+        }
+    }
+}
+
+__global__ void k_debug_svd(const float* __restrict__ F, float* U, float* sig, float* V, int64_t n)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float f[9], u[9], s[3], v[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        f[e] = F[9 * p + e];
+    svd3(f, u, s, v);
+    for (int e = 0; e < 9; ++e) {
+        if (U) U[9 * p + e] = u[e];
+        if (V) V[9 * p + e] = v[e];
+    }
+    if (sig)
+        for (int e = 0; e < 3; ++e)
+            sig[3 * p + e] = s[e];
+}
+
+__global__ void k_debug_stress(MatParams m, const float* __restrict__ F, const float* __restrict__ Jp,
+                               float* __restrict__ tau, int64_t n)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float f[9], t[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        f[e] = F[9 * p + e];
+    kirchhoff(m, f, Jp ? Jp[p] : 1.0f, t);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        tau[9 * p + e] = t[e];
+}
+
+__global__ void k_debug_plasticity(MatParams m, float* __restrict__ F, float* __restrict__ Jp, int64_t n)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float f[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        f[e] = F[9 * p + e];
+    float j = Jp ? Jp[p] : 1.0f;
+    plasticity(m, f, j);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        F[9 * p + e] = f[e];
+    if (Jp)
+        Jp[p] = j;
+}
+
+inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace
+
+MatParams make_mat_params(const mpm_material& m)
+{
+    MatParams q{};
+    q.kind = m.kind;
+    q.rho = m.rho;
+    double E = m.E, nu = m.nu;
+    q.mu = (float)(E / (2.0 * (1.0 + nu)));
+    q.la = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    q.K = m.E;
+    q.gamma = m.gamma;
+    q.lo = 1.0f - m.theta_c;
+    q.hi = 1.0f + m.theta_s;
+    q.xi = m.hardening;
+    double sphi = sin((double)m.friction_deg * 3.14159265358979323846 / 180.0);
+    q.alpha = (float)(sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
+    q.dp_coef = (float)((3.0 * q.la + 2.0 * q.mu) / (2.0 * q.mu));
+    return q;
+}
+
+void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* err,
+                cudaStream_t s)
+{
+    if (n > 0)
+        k_p2g<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+}
+
+void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s)
+{
+    if (gv.n_pblocks > 0)
+        k_grid<<<blocks_for((int64_t)gv.n_pblocks * 64, 256), 256, 0, s>>>(sp, gv, dt);
+}
+
+void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* flags,
+                uint32_t* err, cudaStream_t s)
+{
+    if (n > 0)
+        k_g2p<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+}
+
+void launch_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        k_debug_svd<<<blocks_for(n, 128), 128, 0, s>>>(F, U, sig, V, n);
+}
+
+void launch_debug_stress(const MatParams& mp, const float* F, const float* Jp, float* tau, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        k_debug_stress<<<blocks_for(n, 128), 128, 0, s>>>(mp, F, Jp, tau, n);
+}
+
+void launch_debug_plasticity(const MatParams& mp, float* F, float* Jp, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        k_debug_plasticity<<<blocks_for(n, 128), 128, 0, s>>>(mp, F, Jp, n);
+}
+
+}  // namespace mpm

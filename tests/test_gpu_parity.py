@@ -1,0 +1,390 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated per check):
+  * keys, permutation, physical-block list: bit-exact;
+  * grid mass and momentum after P2G: |gpu - oracle|_inf <= 1e-5 |oracle|_inf
+    (per field);
+  * x after 10 substeps: |dx|_inf <= 1e-4 (domain length 1); v after 10
+    substeps: |dv|_inf <= 1e-4 |v|_inf;
+  * total grid mass vs total particle mass: 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_2111_00699_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2111_00699_gb300 import build, mpm
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    orc.build()
+    return mpm
+
+
+def linf(a, b):
+    return float(np.abs(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64)).max())
+
+
+def mats_pair(M, kind, **kw):
+    return M.material(kind, **kw), orc.material(kind, **kw)
+
+
+def oracle_state_from(sim_state, vol, mat_ids=None):
+    st = {k: v.detach().cpu().numpy().astype(np.float64) for k, v in sim_state.items()}
+    return orc.State(st["x"], st["v"], st["C"], st["F"], st["Jp"], vol, 0 if mat_ids is None else mat_ids)
+
+
+def L_of(res):
+    L = 0
+    while (4 << L) < res:
+        L += 1
+    return L
+
+
+# ---------------------------------------------------------------- device math
+
+def _rand_rot(rng, n):
+    q, r = np.linalg.qr(rng.normal(size=(n, 3, 3)))
+    q = q * np.sign(np.diagonal(r, axis1=1, axis2=2))[:, None, :]
+    d = np.linalg.det(q)
+    q[d < 0, :, 0] *= -1
+    return q
+
+
+def test_svd_matches_numpy(M):
+    rng = np.random.default_rng(0)
+    n = 4096
+    F = np.concatenate([np.eye(3) + 0.1 * rng.normal(size=(n // 2, 3, 3)),
+                        rng.normal(size=(n // 4, 3, 3)),
+                        np.einsum("nab,nb,ncb->nac", _rand_rot(rng, n // 4),
+                                  np.tile([1.2, 1.2, 0.7], (n // 4, 1)), _rand_rot(rng, n // 4))])
+    F[-8:] = np.diag([1.0, 1.0, -1.0]) @ F[-8:]               # inverted
+    Ft = torch.tensor(F, dtype=torch.float32, device="cuda")
+    U, S, V = (t.double().cpu().numpy() for t in M.debug_svd(Ft))
+    F32 = Ft.double().cpu().numpy()
+    scale = np.abs(F32).reshape(n, -1).max(1)
+    rec = np.einsum("nab,nb,ncb->nac", U, S, V)
+    assert (np.abs(rec - F32).reshape(n, -1).max(1) / scale).max() < 2e-5
+    I = np.eye(3)
+    assert np.abs(np.einsum("nba,nbc->nac", U, U) - I).max() < 2e-5
+    assert np.abs(np.einsum("nba,nbc->nac", V, V) - I).max() < 2e-5
+    assert np.abs(np.linalg.det(U) - 1).max() < 2e-5 and np.abs(np.linalg.det(V) - 1).max() < 2e-5
+    ref = np.linalg.svd(F32, compute_uv=False)
+    assert (np.abs(np.abs(S) - ref).max(1) / ref[:, 0]).max() < 2e-5
+    assert np.all(S[:, 0] >= S[:, 1] - 1e-5 * ref[:, 0]) and np.all(S[:, 1] >= np.abs(S[:, 2]) - 1e-5 * ref[:, 0])
+    d = np.linalg.det(F32)
+    big = np.abs(d) > 1e-3
+    assert np.all(np.sign(S[big, 2]) == np.sign(d[big]))
+
+
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+def test_stress_matches_oracle(M, kind):
+    rng = np.random.default_rng(1)
+    n = 2048
+    kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2), snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, hardening=10.0),
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0), sand=dict(kind=M.SAND, E=3.5e5, nu=0.3))[kind]
+    k = kw.pop("kind")
+    gm, om = M.material(k, **kw), orc.material(k, **kw)
+    F = (np.eye(3) + 0.05 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    Jp = rng.uniform(0.95, 1.05, n).astype(np.float32)
+    tau = M.debug_stress(gm, torch.from_numpy(F).cuda(), torch.from_numpy(Jp).cuda()).double().cpu().numpy()
+    ref = np.stack([orc.kirchhoff(om, F[i].astype(np.float64), float(Jp[i])) for i in range(n)])
+    assert linf(tau, ref) <= 1e-4 * np.abs(ref).max()
+
+
+def test_plasticity_matches_oracle(M):
+    rng = np.random.default_rng(2)
+    n = 1024
+    for kind, kw in ((M.SNOW, dict(E=1.4e5, nu=0.2, theta_c=2.5e-2, theta_s=7.5e-3)),
+                     (M.SAND, dict(E=3.5e5, nu=0.3, friction_deg=30.0))):
+        gm, om = M.material(kind, **kw), orc.material(kind, **kw)
+        F = (np.eye(3) + 0.04 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+        Jp = rng.uniform(0.9, 1.1, n).astype(np.float32)
+        Fg, Jg = M.debug_plasticity(gm, torch.from_numpy(F).cuda(), torch.from_numpy(Jp).cuda())
+        Fg, Jg = Fg.double().cpu().numpy(), Jg.double().cpu().numpy()
+        for i in range(n):
+            Fo, Jo = orc.plasticity(om, F[i].astype(np.float64), float(Jp[i]))
+            assert linf(Fg[i], Fo) <= 2e-5, (kind, i)
+            assert abs(Jg[i] - Jo) <= 2e-5 * abs(Jo), (kind, i)
+
+
+# ---------------------------------------------------------------------- sort
+
+@pytest.mark.parametrize("n,bits", [(1, 8), (2047, 18), (2048, 24), (2049, 24), (100_003, 32), (1 << 20, 24)])
+def test_radix_sort_bit_exact(M, n, bits):
+    rng = np.random.default_rng(n + bits)
+    mod = 1 << bits
+    distinct = max(2, n // 4)                      # force runs of equal keys
+    raw = rng.integers(0, min(mod, distinct), size=n, dtype=np.uint64)
+    keys = ((raw * np.uint64(2654435761)) % np.uint64(mod)).astype(np.uint32)
+    vals = np.arange(n, dtype=np.int32)
+    ks, vs = M.radix_sort_pairs(torch.from_numpy(keys.view(np.int32)).cuda(), torch.from_numpy(vals).cuda(), bits)
+    perm = orc.stable_sort(keys)
+    np.testing.assert_array_equal(vs.cpu().numpy(), perm)
+    np.testing.assert_array_equal(ks.cpu().numpy().view(np.uint32), keys[perm])
+
+
+def _check_order_and_blocks(sim, x, res):
+    L = L_of(res)
+    keys, st = orc.particle_keys(x, float(res), L)
+    assert st == 0
+    perm = orc.stable_sort(keys)
+    gk, gid = sim.read_order()
+    np.testing.assert_array_equal(gk, keys[perm])
+    np.testing.assert_array_equal(gid, perm)
+    np.testing.assert_array_equal(sim.read_blocks(), orc.pblocks(keys, L))
+
+
+def test_keys_order_blocks_small(M):
+    x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
+    with M.Simulator(64, 1 / 64, [M.material(M.ELASTIC)]) as sim:
+        sim.add_particles(x)
+        sim.rebuild()
+        _check_order_and_blocks(sim, x, 64)
+
+
+def test_keys_order_blocks_snow_full_size(M):
+    x, _ = scenes.snow_blocks()
+    with M.Simulator(256, 1 / 256, [M.material(M.SNOW, E=1.4e5, nu=0.2, rho=400.0)], boundary=M.SLIP) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        sim.rebuild()
+        _check_order_and_blocks(sim, x, 256)
+
+
+# ------------------------------------------------------------------ P2G grid
+
+def _perturbed_state(rng, n, v_scale=0.5, C_scale=5.0, F_scale=0.02):
+    v = (v_scale * rng.normal(size=(n, 3))).astype(np.float32)
+    C = (C_scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    F = (np.eye(3) + F_scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    return v, C, F
+
+
+def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-5):
+    rng = np.random.default_rng(7)
+    n = len(x)
+    v, C, F = _perturbed_state(rng, n)
+    sim.write_state(v=torch.from_numpy(v).cuda(), C=torch.from_numpy(C).cuda(), F=torch.from_numpy(F).cuda())
+    g = sim.debug_p2g(dt).double().cpu().numpy()            # (z, y, x, 4)
+    s = oracle_state_from(sim.read_state(), vol, mat_ids)
+    cfg = orc.config(res, 1.0 / res)
+    og, st = orc.p2g(cfg, om_list, s, dt)
+    assert st == 0
+    lo, dim = og.lo, og.dim
+    ref_m = np.zeros((res, res, res))
+    ref_p = np.zeros((res, res, res, 3))
+    ref_m[lo[2]:lo[2] + dim[2], lo[1]:lo[1] + dim[1], lo[0]:lo[0] + dim[0]] = og.mass()
+    ref_p[lo[2]:lo[2] + dim[2], lo[1]:lo[1] + dim[1], lo[0]:lo[0] + dim[0]] = og.mom()
+    assert linf(g[..., 0], ref_m) <= tol * np.abs(ref_m).max()
+    assert linf(g[..., 1:], ref_p) <= tol * np.abs(ref_p).max()
+    rho = np.array([m.rho for m in om_list])
+    mass_p = float((rho[s.mat] * s.vol).sum())
+    assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
+
+
+def test_p2g_grid_small_elastic(M):
+    x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
+    vol = 0.008 / 8192
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
+    with M.Simulator(64, 1 / 64, [gm]) as sim:
+        sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
+        _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
+
+
+@pytest.mark.parametrize("kind", ["snow", "fluid", "sand"])
+def test_p2g_grid_materials(M, kind):
+    kw = dict(snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0), fluid=dict(kind=M.FLUID, E=1e4, rho=1000.0),
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0))[kind]
+    k = kw.pop("kind")
+    gm, om = mats_pair(M, k, **kw)
+    x, _ = scenes.blocks(11, 20000, 64, 2)
+    vol = (1 / 64) ** 3 / 8
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP) as sim:
+        sim.add_particles(x)
+        if k == M.FLUID:
+            sim.write_state(Jp=torch.full((len(x),), 0.97, device="cuda"))
+        _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
+
+
+def test_p2g_grid_snow_full_size(M):
+    x, _ = scenes.snow_blocks()
+    vol = (1 / 256) ** 3 / 8
+    gm, om = mats_pair(M, M.SNOW, E=1.4e5, nu=0.2, rho=400.0)
+    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        _p2g_parity(M, sim, [gm], [om], x, vol, 5e-5, 256)
+
+
+# ------------------------------------------------------------- whole substeps
+
+def _run_both(M, sim, om_list, s, steps, dt, cfg):
+    sim.run(steps, dt)
+    for _ in range(steps):
+        assert orc.substep(cfg, om_list, s, dt) == 0
+    return {k: v.double().cpu().numpy() for k, v in sim.read_state().items()}
+
+
+def test_substeps_small_elastic(M):
+    """The small elastic case: 8,192 particles, 64^3, E=1e4, nu=0.2, rho=1,
+    dt=1e-4, sticky walls; 10 substeps within the stated tolerances, then the
+    remaining 90 of its 100 substeps."""
+    x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
+    vol = 0.008 / 8192
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
+    cfg = orc.config(64, 1 / 64, orc.STICKY)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.STICKY) as sim:
+        sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
+        s = orc.State(x.astype(np.float64), vol=vol)
+        g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        g = _run_both(M, sim, [om], s, 90, 1e-4, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        assert linf(g["v"], s.v) <= 1e-3 * np.abs(s.v).max()
+
+
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+def test_substeps_materials(M, kind):
+    kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
+              snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
+    k = kw.pop("kind")
+    gm, om = mats_pair(M, k, **kw)
+    dt = 5e-5 if k == M.SNOW else 1e-4
+    x, _ = scenes.blocks(13, 20000, 64, 2)
+    vol = (1 / 64) ** 3 / 8
+    rng = np.random.default_rng(3)
+    n = len(x)
+    v = (0.3 * rng.normal(size=(n, 3))).astype(np.float32)
+    F = (np.eye(3) + 0.01 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP) as sim:
+        sim.add_particles(x, v=v)
+        if k != M.FLUID:
+            sim.write_state(F=torch.from_numpy(F).cuda())
+        s = oracle_state_from(sim.read_state(), vol)
+        g = _run_both(M, sim, [om], s, 10, dt, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+    if k != M.FLUID:
+        assert linf(g["F"], s.F) <= 1e-4
+    assert linf(g["Jp"], s.Jp) <= 1e-4
+
+
+def test_one_substep_snow_full_size(M):
+    x, _ = scenes.snow_blocks()
+    vol = (1 / 256) ** 3 / 8
+    gm, om = mats_pair(M, M.SNOW, E=1.4e5, nu=0.2, rho=400.0)
+    cfg = orc.config(256, 1 / 256, orc.SLIP)
+    rng = np.random.default_rng(9)
+    v = (0.2 * rng.normal(size=(len(x), 3))).astype(np.float32)
+    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda(), v=torch.from_numpy(v).cuda())
+        s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+        g = _run_both(M, sim, [om], s, 1, 5e-5, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+    assert linf(g["C"], s.C) <= 1e-4 * np.abs(s.C).max()
+    assert linf(g["F"], s.F) <= 1e-5
+
+
+def test_rebuild_is_triggered_and_parity_holds(M):
+    """A fast block crosses several cells: the free-zone test must request
+    rebuilds, and the result still matches the oracle."""
+    x = scenes.cube_uniform(4, 3000, 0.3, 0.4)
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    v = np.tile(np.array([30.0, 20.0, 10.0], np.float32), (len(x), 1))
+    vol = (1 / 64) ** 3 / 8
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP) as sim:
+        sim.add_particles(x, v=v)
+        s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+        g = _run_both(M, sim, [om], s, 60, 1e-4, cfg)
+        stats = sim.stats()
+    assert stats["rebuilds"] >= 3, stats
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_ragged_sizes(M):
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
+    with M.Simulator(32, 1 / 32, [gm]) as sim:
+        sim.run(3, 1e-4)                          # no particles: a no-op
+        assert sim.n == 0
+        assert sim.read_state()["x"].shape == (0, 3)
+    cfg = orc.config(32, 1 / 32, orc.STICKY)
+    for n in (1, 31, 127, 129, 2049):
+        x = scenes.cube_uniform(n, n, 0.35, 0.65)
+        with M.Simulator(32, 1 / 32, [gm]) as sim:
+            sim.add_particles(x, vol=np.full(n, 1e-6, np.float32))
+            s = orc.State(x.astype(np.float64), vol=1e-6)
+            g = _run_both(M, sim, [om], s, 5, 1e-4, cfg)
+        assert linf(g["x"], s.x) <= 1e-4, n
+        assert linf(g["v"], s.v) <= 1e-4 * max(np.abs(s.v).max(), 1e-12), n
+
+
+def test_growth_insertion_order_and_capacity(M):
+    gm = M.material(M.ELASTIC)
+    xs = [scenes.cube_uniform(i, m, 0.3, 0.7) for i, m in enumerate((100, 1000, 5000))]
+    with M.Simulator(64, 1 / 64, [gm]) as sim:
+        sim.add_particles(xs[0])
+        sim.rebuild()
+        sim.add_particles(torch.from_numpy(xs[1]).cuda())
+        sim.rebuild()
+        sim.add_particles(xs[2])
+        caps = sim.stats()["particle_capacity"]
+        assert caps >= 4 * 6100 - 256
+        out = sim.read_state(("x",))["x"].cpu().numpy()
+        np.testing.assert_array_equal(out, np.concatenate(xs))
+        sim.rebuild()
+        np.testing.assert_array_equal(sim.read_state(("x",))["x"].cpu().numpy(), np.concatenate(xs))
+    with M.Simulator(64, 1 / 64, [gm], max_particles=500) as sim:
+        sim.add_particles(xs[0])
+        with pytest.raises(M.MpmError) as e:
+            sim.add_particles(xs[1])
+        assert e.value.status == 3                 # MPM_ECAPACITY
+
+
+def test_domain_and_nonfinite_errors(M):
+    gm = M.material(M.ELASTIC)
+    with M.Simulator(32, 1 / 32, [gm]) as sim:
+        sim.add_particles(np.array([[0.001, 0.5, 0.5], [0.5, 0.5, 0.5]], np.float32))
+        sim.substep(1e-4)
+        with pytest.raises(M.MpmError) as e:
+            sim.sync()
+        assert e.value.status == 4                 # MPM_EDOMAIN
+    with M.Simulator(32, 1 / 32, [gm]) as sim:
+        sim.add_particles(np.array([[0.5, 0.5, 0.5]], np.float32), v=np.array([[np.nan, 0, 0]], np.float32))
+        sim.run(2, 1e-4)
+        with pytest.raises(M.MpmError) as e:
+            sim.sync()
+        assert e.value.status == 5                 # MPM_ENONFINITE
+
+
+def test_host_buffers_and_side_stream(M):
+    x = scenes.cube_uniform(3, 4000, 0.4, 0.6)
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with M.Simulator(64, 1 / 64, [gm], stream=stream) as sim:
+            sim.add_particles(x, vol=np.full(len(x), 1e-6, np.float32))
+            sim.run(5, 1e-4)
+            host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
+                    for k, s in (("x", (len(x), 3)), ("v", (len(x), 3)))}
+            sim.read_state_into(x=host["x"], v=host["v"])
+    s = orc.State(x.astype(np.float64), vol=1e-6)
+    cfg = orc.config(64, 1 / 64, orc.STICKY)
+    for _ in range(5):
+        orc.substep(cfg, om, s, 1e-4)
+    assert linf(host["x"].numpy(), s.x) <= 1e-4
+    assert linf(host["v"].numpy(), s.v) <= 1e-4 * np.abs(s.v).max()
