@@ -43,11 +43,11 @@ SUBSTEPS_PER_FRAME = FRAME / DT            # 333.33
 SNOW = dict(E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0)
 VOL = DX ** 3 / 8
 # Algorithmic bytes per particle per launch (FP32 SoA):
-#   P2G reads x 12, v 12, C 36, F 36, Jp 4, vol 4, material 1            = 105 B
-#   G2P reads x 12, F 36, Jp 4, material 1; writes x, v, C, F, Jp 100     = 153 B
+#   P2G reads x 12, v 12, C 36, tau 24, vol 4, material 1                  = 89 B
+#   G2P reads x 12, F 36, Jp 4, material 1; writes x, v, C, F, Jp, tau 124 = 177 B
 # grid update per node of a physical block: read 16, write 16, clear 16 = 48 B
-BYTES_P2G = 105
-BYTES_G2P = 153
+BYTES_P2G = 89
+BYTES_G2P = 177
 BYTES_GRID_NODE = 48
 
 
@@ -56,7 +56,7 @@ def workload_config(n):
                         "Stomakhin snow, slip walls, dt=5e-5" % n,
             "particles": n, "grid": [RES, RES, RES], "dt": DT, "material": "snow (E=1.4e5, nu=0.2, rho=400)",
             "substeps_per_frame": round(SUBSTEPS_PER_FRAME, 3),
-            "l2": "inputs larger than L2: particle state %.0f MB + grid, no flush" % (n * 105 / 1e6)}
+            "l2": "inputs larger than L2: particle state %.0f MB + grid, no flush" % (n * 133 / 1e6)}
 
 
 # ---------------------------------------------------------------- clocks
@@ -158,6 +158,11 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- main arm
 
+def _lib_variant_name(v):
+    from paper_2111_00699_gb300 import _lib
+    return _lib.P2G_VARIANTS[v] if 0 <= v < len(_lib.P2G_VARIANTS) else None
+
+
 def _traffic_for(kernel, src_hash):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -177,6 +182,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-frames", type=int, default=3)
+    ap.add_argument("--p2g-variant", type=int, default=-1,
+                    help="P2G scatter variant (0 direct, 1 strided, 2 tile); -1 = autotune")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -206,15 +213,22 @@ def main():
     stream = torch.cuda.Stream()
     xs = torch.from_numpy(x).cuda()
 
-    def fresh_sim():
-        sim = mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream)
+    def fresh_sim(variant=2):
+        sim = mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream, p2g_variant=variant)
         sim.add_particles(xs)
         return sim
 
     # ---- device-resident throughput (the `value`) ----
+    from paper_2111_00699_gb300 import tune
     sim = fresh_sim()
-    with torch.cuda.stream(stream):
-        sim.run(args.warmup, DT)
+    tuned = {"best_name": _lib_variant_name(args.p2g_variant), "ms": None}
+    warm = args.warmup
+    if args.p2g_variant < 0:
+        tuned = tune.tune_p2g(sim, DT, steps=20, rounds=2)      # advances 120 substeps
+        warm = max(3, warm - 120)
+    else:
+        sim.set_p2g_variant(args.p2g_variant)
+    sim.run(warm, DT)
     sim.sync()
     launches0 = sim.stats()["kernel_launches"]
     rebuilds0 = sim.stats()["rebuilds"]
@@ -266,7 +280,8 @@ def main():
     hbm = hbm or 6800.0
     achieved = algo[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
     src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", "substep.cu"), "rb").read()).hexdigest()
-    kernel_name = {"p2g": "k_p2g", "g2p": "k_g2p", "grid": "k_grid"}[dom]
+    p2g_name = "k_p2g_" + (tuned.get("best_name") or "tile")
+    kernel_name = {"p2g": p2g_name, "g2p": "k_g2p", "grid": "k_grid"}[dom]
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_note,
                 "algorithmic_bytes_per_launch": algo[dom], "avg_launch_ms": avg[dom],
@@ -277,7 +292,7 @@ def main():
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if args.e2e_frames > 0:
-        sim = fresh_sim()
+        sim = fresh_sim(tuned.get("best", max(args.p2g_variant, 0)))
         host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
                 for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
         sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
@@ -318,7 +333,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_frame": ms_per_step * SUBSTEPS_PER_FRAME,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
+            "clocks": clk.summary(), "p2g_variant": tuned, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu}
     print(json.dumps(line))
     if world > 1:

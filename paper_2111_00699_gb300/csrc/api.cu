@@ -384,6 +384,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
     }
     if (cfg->use_g2p2g != 0)
         return MPM_ENOTSUP;
+    if (cfg->p2g_variant < 0 || cfg->p2g_variant >= kP2GVariants)
+        return MPM_EINVAL;
     for (int i = 0; i < n_mats; ++i)
         if (!valid_material(mats[i]))
             return MPM_EINVAL;
@@ -558,7 +560,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     const PartView& pv = ctx->pv[ctx->cur];
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     prof_begin(ctx, e0);
-    launch_p2g(ctx->sp, pv, gv, ctx->n, dt, ctx->dstat, s);
+    launch_p2g(ctx->sp, pv, gv, ctx->n, dt, ctx->dstat, ctx->cfg.p2g_variant, s);
     prof_end(ctx, 1, e0);
     prof_begin(ctx, e1);
     launch_grid_update(ctx->sp, gv, dt, s);
@@ -643,6 +645,10 @@ mpm_status mpm_write_state(mpm_ctx* ctx, const float* x, const float* v, const f
         }
         ctx->launches += 1;
     }
+    if (F || Jp) {
+        launch_prepare_stress(ctx->sp, ctx->pv[ctx->cur], n, ctx->stream);
+        ctx->launches += 1;
+    }
     if (x) {
         ctx->need_rebuild = true;
         ctx->keys_valid = false;
@@ -718,7 +724,7 @@ mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
     }
     CK(cudaMemsetAsync(dense, 0, bytes, s));
     GridView gv = grid_view(ctx);
-    launch_p2g(ctx->sp, ctx->pv[ctx->cur], gv, ctx->n, dt, ctx->dstat, s);
+    launch_p2g(ctx->sp, ctx->pv[ctx->cur], gv, ctx->n, dt, ctx->dstat, ctx->cfg.p2g_variant, s);
     launch_grid_to_dense(ctx->sp, gv.cur, ctx->pslot, ctx->n_pblocks, dense, s);
     ctx->launches += 2;
     if (ctx->n_pblocks > 0)
@@ -727,6 +733,14 @@ mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
         CK(cudaMemcpyAsync(grid_out, dense, bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaGetLastError());
     return device_error(ctx);
+}
+
+mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant)
+{
+    if (!ctx || variant < 0 || variant >= kP2GVariants)
+        return MPM_EINVAL;
+    ctx->cfg.p2g_variant = variant;
+    return MPM_OK;
 }
 
 mpm_status mpm_profile_enable(mpm_ctx* ctx, int on)

@@ -64,8 +64,11 @@ __device__ __forceinline__ void bspline(float f, float w[3])
 __device__ __forceinline__ void jacobi_pair(float& spp, float& sqq, float& spq, float& srp, float& srq,
                                             float* V, int p, int q)
 {
+    // An off-diagonal below FP32 resolution of the diagonal is already zero to
+    // working precision; rotating it away (by up to 45 degrees when the
+    // diagonal is degenerate, as for F = I) would only add rounding.
     float mag = fabsf(spp) + fabsf(sqq);
-    if (!(fabsf(spq) > 1e-12f * mag + 1e-35f))
+    if (!(fabsf(spq) > 6e-8f * mag + 1e-35f))
         return;
     float theta = (sqq - spp) / (2.0f * spq);
     float at = fabsf(theta);
@@ -102,9 +105,21 @@ __device__ __forceinline__ void swap_neg_cols(float* V, float& la, float& lb, in
 __device__ __forceinline__ void givens_rows(float* B, float* U, int i, int j)
 {
     float a = B[3 * i + i], b = B[3 * j + i];
-    float r2 = a * a + b * b;
-    if (!(r2 > 1e-37f))
+    if (!(fabsf(b) > 6e-8f * fabsf(a))) {
+        // b is zero to working precision: the rotation is the identity, or a
+        // half turn (exact sign flips of rows i, j) when the pivot is negative.
+        if (a < 0.0f) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                B[3 * i + k] = -B[3 * i + k];
+                B[3 * j + k] = -B[3 * j + k];
+                U[3 * k + i] = -U[3 * k + i];
+                U[3 * k + j] = -U[3 * k + j];
+            }
+        }
         return;
+    }
+    float r2 = a * a + b * b;
     float ir = rsqrtf(r2);
     float c = a * ir, s = b * ir;
 #pragma unroll
@@ -175,7 +190,7 @@ __device__ __forceinline__ void udwt(const float* U, const float* d, const float
                              U[3 * i + 2] * d[2] * W[3 * j + 2];
 }
 
-// ---- constitutive models (Sec. 4.1: stress merged into P2G) -------------------
+// ---- constitutive models (Sec. 4.1: SVD, projection and stress merged) --------
 // Kirchhoff stress tau = P F^T.  Fixed-corotated, written through the SVD:
 // (F - R) F^T = U (Sigma - I) Sigma U^T, so tau = U diag(2 mu (s - 1) s) U^T
 // + lambda J (J - 1) I.  Sand: tau = U diag(2 mu eps + lambda tr eps) U^T with
@@ -254,6 +269,79 @@ __device__ __forceinline__ void plasticity(const MatParams& m, float* F, float& 
     t[1] = __expf(e1 - k * d1);
     t[2] = __expf(e2 - k * d2);
     udwt(U, t, V, F);
+}
+
+// End-of-G2P constitutive update with a single SVD (Sec. 4.1 merges "SVD,
+// plasticity projection, stress computation"): the return map on the trial
+// F (snow clamp + Jp, Drucker-Prager projection), then the Kirchhoff stress
+// of the projected state, which the next P2G needs.  Output t6 = (xx, yy, zz,
+// xy, xz, yz) of the symmetric tau = U diag(d) U^T + vol I.
+__device__ __forceinline__ void constitutive_update(const MatParams& m, float* F, float& Jp, float* t6)
+{
+    if (m.kind == MPM_FLUID) {
+        float p = m.K * (__powf(Jp, -m.gamma) - 1.0f);
+        t6[0] = t6[1] = t6[2] = -p * Jp;
+        t6[3] = t6[4] = t6[5] = 0.0f;
+        return;
+    }
+    float U[9], s[3], V[9], d[3];
+    float vol = 0.0f;
+    svd3(F, U, s, V);
+    if (m.kind == MPM_SNOW) {
+        float t[3];
+        t[0] = fminf(fmaxf(s[0], m.lo), m.hi);
+        t[1] = fminf(fmaxf(s[1], m.lo), m.hi);
+        t[2] = fminf(fmaxf(s[2], m.lo), m.hi);
+        Jp *= (s[0] * s[1] * s[2]) / (t[0] * t[1] * t[2]);
+        udwt(U, t, V, F);
+        float h = __expf(m.xi * (1.0f - Jp));
+        float mu = m.mu * h, la = m.la * h;
+        float J = t[0] * t[1] * t[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d[k] = 2.0f * mu * (t[k] - 1.0f) * t[k];
+        vol = la * J * (J - 1.0f);
+    } else if (m.kind == MPM_SAND) {
+        float e[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            e[k] = __logf(fmaxf(s[k], 1e-4f));
+        float tr = e[0] + e[1] + e[2];
+        if (tr >= 0.0f) {
+            float one[3] = {1.0f, 1.0f, 1.0f};
+            udwt(U, one, V, F);
+            e[0] = e[1] = e[2] = 0.0f;
+        } else {
+            float third = tr * (1.0f / 3.0f);
+            float d0 = e[0] - third, d1 = e[1] - third, d2 = e[2] - third;
+            float nd = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            float dg = nd + m.dp_coef * tr * m.alpha;
+            if (dg > 0.0f) {
+                float k = dg / nd;
+                e[0] -= k * d0;
+                e[1] -= k * d1;
+                e[2] -= k * d2;
+                float t[3] = {__expf(e[0]), __expf(e[1]), __expf(e[2])};
+                udwt(U, t, V, F);
+            }
+        }
+        float tr2 = e[0] + e[1] + e[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d[k] = 2.0f * m.mu * e[k] + m.la * tr2;
+    } else {
+        float J = s[0] * s[1] * s[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d[k] = 2.0f * m.mu * (s[k] - 1.0f) * s[k];
+        vol = m.la * J * (J - 1.0f);
+    }
+    t6[0] = U[0] * U[0] * d[0] + U[1] * U[1] * d[1] + U[2] * U[2] * d[2] + vol;
+    t6[1] = U[3] * U[3] * d[0] + U[4] * U[4] * d[1] + U[5] * U[5] * d[2] + vol;
+    t6[2] = U[6] * U[6] * d[0] + U[7] * U[7] * d[1] + U[8] * U[8] * d[2] + vol;
+    t6[3] = U[0] * U[3] * d[0] + U[1] * U[4] * d[1] + U[2] * U[5] * d[2];
+    t6[4] = U[0] * U[6] * d[0] + U[1] * U[7] * d[1] + U[2] * U[8] * d[2];
+    t6[5] = U[3] * U[6] * d[0] + U[4] * U[7] * d[1] + U[5] * U[8] * d[2];
 }
 
 }  // namespace mpm

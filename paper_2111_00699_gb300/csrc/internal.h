@@ -17,7 +17,16 @@ enum Channel : int {
     CH_F = 15,   // deformation gradient F (row-major 3x3)
     CH_JP = 24,  // snow Jp / fluid J
     CH_VOL = 25, // rest volume
-    kChannels = 26
+    CH_TAU = 26, // Kirchhoff stress of the current F: xx, yy, zz, xy, xz, yz
+    kChannels = 32
+};
+
+// P2G scatter variants (tuning knob mpm_config.p2g_variant).
+enum P2GVariant : int {
+    P2G_DIRECT = 0,   // thread per particle in storage order, float4 global atomics
+    P2G_STRIDED = 1,  // lanes take every 8th particle of a 256-particle tile (distinct cells), float4 atomics
+    P2G_TILE = 2,     // CTA accumulates its 256 particles into a shared-memory node tile, one flush
+    kP2GVariants = 3
 };
 
 // Device status word bits.
@@ -89,7 +98,8 @@ void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t
 
 // substep.cu
 void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
-                uint32_t* err, cudaStream_t s);
+                uint32_t* err, int variant, cudaStream_t s);
+void launch_prepare_stress(const SimParams& sp, const PartView& pv, int64_t n, cudaStream_t s);
 void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s);
 void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                 uint32_t* flags, uint32_t* err, cudaStream_t s);

@@ -121,6 +121,9 @@ __global__ void k_append(PartView pv, int64_t n0, int64_t n, const float* __rest
     }
     pv.ch(CH_JP)[p] = 1.0f;
     pv.ch(CH_VOL)[p] = vol ? vol[i] : default_vol;
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+        pv.ch(CH_TAU + e)[p] = 0.0f;   // stress of F = I, Jp = J = 1 is zero for every model
     pv.mat[p] = (uint8_t)material;
     pv.id[p] = (int32_t)p;
 }

@@ -65,74 +65,212 @@ __device__ __forceinline__ bool in_grid(const SimParams& sp, const int* b, const
     return ok;
 }
 
-__global__ void __launch_bounds__(kTransferThreads) k_p2g(SimParams sp, PartView pv, GridView gv, int64_t n,
-                                                          float dt, uint32_t* __restrict__ err)
+// Everything P2G needs of one particle: stencil base and weights, mass, the
+// momentum m v and the affine matrix A = (m C - 4 dt V / dx^2 tau) dx, so that
+// node (i, j, k) of the stencil receives w (m v + A (node - f)) and w m.
+struct P2GParticle {
+    int b[3];
+    float f[3], w[3][3];
+    float mp, mv[3], A[9];
+};
+
+__device__ __forceinline__ bool load_p2g_particle(const SimParams& sp, const PartView& pv, int64_t p, float dt,
+                                                  P2GParticle& q, uint32_t* err)
+{
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        x[a] = pv.ch(CH_X + a)[p];
+        q.b[a] = base_of(x[a], sp.inv_dx);
+        q.f[a] = __fmul_rn(x[a], sp.inv_dx) - (float)q.b[a];
+        bspline(q.f[a], q.w[a]);
+    }
+    if (!in_grid(sp, q.b, x)) {
+        atomicOr(err, ST_EDOMAIN);
+        return false;
+    }
+    const float rho = sp.mat[pv.mat[p]].rho;
+    float vol = pv.ch(CH_VOL)[p];
+    q.mp = rho * vol;
+    float kst = 4.0f * dt * vol * sp.inv_dx * sp.inv_dx;
+    float t[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+        t[e] = kst * pv.ch(CH_TAU + e)[p];
+    // symmetric tau: (xx, yy, zz, xy, xz, yz)
+    const float tm[9] = {t[0], t[3], t[4], t[3], t[1], t[5], t[4], t[5], t[2]};
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        q.A[e] = (q.mp * pv.ch(CH_C + e)[p] - tm[e]) * sp.dx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        q.mv[a] = q.mp * pv.ch(CH_V + a)[p];
+    return true;
+}
+
+__device__ __forceinline__ float4 node_contribution(const P2GParticle& q, int i, int j, int k)
+{
+    float dxo = (float)i - q.f[0], dy = (float)j - q.f[1], dz = (float)k - q.f[2];
+    float wt = q.w[0][i] * q.w[1][j] * q.w[2][k];
+    float4 val;
+    val.x = wt * (q.mv[0] + q.A[0] * dxo + q.A[1] * dy + q.A[2] * dz);
+    val.y = wt * (q.mv[1] + q.A[3] * dxo + q.A[4] * dy + q.A[5] * dz);
+    val.z = wt * (q.mv[2] + q.A[6] * dxo + q.A[7] * dy + q.A[8] * dz);
+    val.w = wt * q.mp;
+    return val;
+}
+
+// 27 float4 global atomics (native vector reductions on sm_90+).
+__device__ __forceinline__ void scatter_global(const GridView& gv, const P2GParticle& q, uint32_t* err)
+{
+    int pb[8];
+    if (!stencil_blocks(gv, q.b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int nz = (q.b[2] & 3) + k;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int ny = (q.b[1] & 3) + j;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                int nx = (q.b[0] & 3) + i;
+                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
+                atomicAdd(&gv.cur[(int64_t)blk * 64 + local], node_contribution(q, i, j, k));
+            }
+        }
+    }
+}
+
+constexpr int kTileThreads = 256;       // particles per CTA in the strided / tile variants
+constexpr int kTileNodes = 2048;        // shared-memory tile capacity (nodes), 32 KB
+
+// P2G_DIRECT: thread per particle in storage order.
+__global__ void __launch_bounds__(kTransferThreads) k_p2g_direct(SimParams sp, PartView pv, GridView gv,
+                                                                 int64_t n, float dt, uint32_t* __restrict__ err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
-    float x[3], f[3], w[3][3];
-    int b[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        x[a] = pv.ch(CH_X + a)[p];
-        b[a] = base_of(x[a], sp.inv_dx);
-        f[a] = __fmul_rn(x[a], sp.inv_dx) - (float)b[a];
-        bspline(f[a], w[a]);
-    }
-    if (!in_grid(sp, b, x)) {
-        atomicOr(err, ST_EDOMAIN);
+    P2GParticle q;
+    if (load_p2g_particle(sp, pv, p, dt, q, err))
+        scatter_global(gv, q, err);
+}
+
+// Lane L of warp w takes particle 8 L + w of the CTA's 256: after the cell
+// sort, consecutive particles share cells (8 per cell), so this puts the 32
+// lanes of a warp on ~32 different cells and their atomics on different
+// addresses.
+__device__ __forceinline__ int64_t strided_particle(int64_t base)
+{
+    return base + (int64_t)((threadIdx.x & 31) * 8 + (threadIdx.x >> 5));
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_p2g_strided(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                              float dt, uint32_t* __restrict__ err)
+{
+    int64_t p = strided_particle((int64_t)blockIdx.x * kTileThreads);
+    if (p >= n)
         return;
+    P2GParticle q;
+    if (load_p2g_particle(sp, pv, p, dt, q, err))
+        scatter_global(gv, q, err);
+}
+
+// P2G_TILE: the CTA's 256 consecutive (cell-sorted) particles accumulate
+// into a shared-memory tile spanning the bounding box of their stencils,
+// then the touched nodes are flushed with one float4 global atomic each.
+// A CTA whose box exceeds the tile falls back to direct atomics.
+__global__ void __launch_bounds__(kTileThreads) k_p2g_tile(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                           float dt, uint32_t* __restrict__ err)
+{
+    __shared__ float tile[4][kTileNodes];
+    __shared__ int box[6];
+    const int tid = threadIdx.x;
+    if (tid < 3) {
+        box[tid] = 0x7fffffff;
+        box[3 + tid] = -0x7fffffff;
     }
-    int pb[8];
-    if (!stencil_blocks(gv, b, pb)) {
-        atomicOr(err, ST_MISSED);
-        return;
-    }
-    const MatParams m = sp.mat[pv.mat[p]];
-    float F[9], tau[9];
-    float Jp = pv.ch(CH_JP)[p];
+    __syncthreads();
+    int64_t p = strided_particle((int64_t)blockIdx.x * kTileThreads);
+    P2GParticle q;
+    bool ok = p < n && load_p2g_particle(sp, pv, p, dt, q, err);
+    if (ok) {
 #pragma unroll
-    for (int e = 0; e < 9; ++e)
-        F[e] = (m.kind != MPM_FLUID) ? pv.ch(CH_F + e)[p] : ((e % 4 == 0) ? 1.0f : 0.0f);
-    kirchhoff(m, F, Jp, tau);
-    float vol = pv.ch(CH_VOL)[p];
-    float mp = m.rho * vol;
-    float kst = 4.0f * dt * vol * sp.inv_dx * sp.inv_dx;
-    // A = (m C - k tau) dx so that A (node - f) = (m C - k tau)(x_i - x_p)
-    float A[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e)
-        A[e] = (mp * pv.ch(CH_C + e)[p] - kst * tau[e]) * sp.dx;
-    float mv[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        mv[a] = mp * pv.ch(CH_V + a)[p];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int nz = (b[2] & 3) + k;
-        float dz = (float)k - f[2];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            int ny = (b[1] & 3) + j;
-            float dy = (float)j - f[1];
-            float wyz = w[1][j] * w[2][k];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                int nx = (b[0] & 3) + i;
-                float dxo = (float)i - f[0];
-                float wt = w[0][i] * wyz;
-                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
-                float4 val;
-                val.x = wt * (mv[0] + A[0] * dxo + A[1] * dy + A[2] * dz);
-                val.y = wt * (mv[1] + A[3] * dxo + A[4] * dy + A[5] * dz);
-                val.z = wt * (mv[2] + A[6] * dxo + A[7] * dy + A[8] * dz);
-                val.w = wt * mp;
-                atomicAdd(&gv.cur[(int64_t)blk * 64 + local], val);
-            }
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&box[a], q.b[a]);
+            atomicMax(&box[3 + a], q.b[a]);
         }
     }
+    __syncthreads();
+    const int lo0 = box[0], lo1 = box[1], lo2 = box[2];
+    const int d0 = box[3] - lo0 + 3, d1 = box[4] - lo1 + 3, d2 = box[5] - lo2 + 3;
+    const bool empty = box[3] < lo0;
+    const int nodes = empty ? 0 : d0 * d1 * d2;
+    if (nodes > kTileNodes) {
+        if (ok)
+            scatter_global(gv, q, err);
+        return;   // uniform across the CTA: no barrier follows
+    }
+    for (int i = tid; i < nodes; i += kTileThreads) {
+        tile[0][i] = 0.0f;
+        tile[1][i] = 0.0f;
+        tile[2][i] = 0.0f;
+        tile[3][i] = 0.0f;
+    }
+    __syncthreads();
+    if (ok) {
+        const int o0 = q.b[0] - lo0, o1 = q.b[1] - lo1, o2 = q.b[2] - lo2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    int idx = (o0 + i) + d0 * ((o1 + j) + d1 * (o2 + k));
+                    float4 v = node_contribution(q, i, j, k);
+                    atomicAdd(&tile[0][idx], v.x);
+                    atomicAdd(&tile[1][idx], v.y);
+                    atomicAdd(&tile[2][idx], v.z);
+                    atomicAdd(&tile[3][idx], v.w);
+                }
+    }
+    __syncthreads();
+    for (int i = tid; i < nodes; i += kTileThreads) {
+        float m = tile[3][i];
+        if (!(m != 0.0f))
+            continue;
+        int x = lo0 + i % d0, y = lo1 + (i / d0) % d1, z = lo2 + i / (d0 * d1);
+        int blk = __ldg(&gv.table[morton3((uint32_t)x >> 2, (uint32_t)y >> 2, (uint32_t)z >> 2)]);
+        if (blk < 0) {
+            atomicOr(err, ST_MISSED);
+            continue;
+        }
+        int local = (x & 3) + 4 * (y & 3) + 16 * (z & 3);
+        atomicAdd(&gv.cur[(int64_t)blk * 64 + local], make_float4(tile[0][i], tile[1][i], tile[2][i], m));
+    }
+}
+
+// Kirchhoff stress of the stored F and Jp, for states P2G has not seen yet
+// (after mpm_write_state).
+__global__ void k_prepare_stress(SimParams sp, PartView pv, int64_t n)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    const MatParams m = sp.mat[pv.mat[p]];
+    float F[9], tau[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        F[e] = pv.ch(CH_F + e)[p];
+    kirchhoff(m, F, pv.ch(CH_JP)[p], tau);
+    const float t6[6] = {tau[0], tau[4], tau[8], tau[1], tau[2], tau[5]};
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+        pv.ch(CH_TAU + e)[p] = t6[e];
 }
 
 __global__ void k_grid(SimParams sp, GridView gv, float dt)
@@ -265,9 +403,12 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
     }
     const MatParams m = sp.mat[pv.mat[p]];
     float Jp = pv.ch(CH_JP)[p];
+    float t6[6];
     if (m.kind == MPM_FLUID) {
         Jp *= 1.0f + dt * (C[0] + C[4] + C[8]);
         pv.ch(CH_JP)[p] = Jp;
+        float Fdummy[9];
+        constitutive_update(m, Fdummy, Jp, t6);
     } else {
         float F[9], Fn[9];
 #pragma unroll
@@ -279,13 +420,16 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
             for (int c = 0; c < 3; ++c)
                 Fn[3 * r + c] = F[3 * r + c] + dt * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
         float Jn = Jp;
-        plasticity(m, Fn, Jn);
+        constitutive_update(m, Fn, Jn, t6);
 #pragma unroll
         for (int e = 0; e < 9; ++e)
             pv.ch(CH_F + e)[p] = Fn[e];
         if (m.kind == MPM_SNOW)
             pv.ch(CH_JP)[p] = Jn;
     }
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+        pv.ch(CH_TAU + e)[p] = t6[e];
     // Free-zone test (Sec. 4.2.1): while every particle's stencil stays in
     // mapped blocks no rebuild is needed.  A particle that changed cell
     // checks the stencil one cell wider on each side (one more substep of
@@ -396,10 +540,22 @@ MatParams make_mat_params(const mpm_material& m)
 }
 
 void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* err,
-                cudaStream_t s)
+                int variant, cudaStream_t s)
+{
+    if (n <= 0)
+        return;
+    if (variant == P2G_STRIDED)
+        k_p2g_strided<<<blocks_for(n, kTileThreads), kTileThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else if (variant == P2G_TILE)
+        k_p2g_tile<<<blocks_for(n, kTileThreads), kTileThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else
+        k_p2g_direct<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+}
+
+void launch_prepare_stress(const SimParams& sp, const PartView& pv, int64_t n, cudaStream_t s)
 {
     if (n > 0)
-        k_p2g<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+        k_prepare_stress<<<blocks_for(n, 128), 128, 0, s>>>(sp, pv, n);
 }
 
 void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s)

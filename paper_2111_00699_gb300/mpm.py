@@ -49,7 +49,7 @@ class Simulator:
 
     def __init__(self, res, dx, materials, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0),
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
-                 device=None):
+                 device=None, p2g_variant: int = 2):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -67,6 +67,7 @@ class Simulator:
         cfg.gravity = (ctypes.c_float * 3)(*gravity)
         cfg.max_particles = int(max_particles)
         cfg.use_g2p2g = 0
+        cfg.p2g_variant = int(p2g_variant)
         mats = (_lib.Material * len(self.materials))(*self.materials)
         self._alloc = None
         if torch_allocator:
@@ -201,6 +202,9 @@ class Simulator:
         g = torch.empty((r[2], r[1], r[0], 4), dtype=torch.float32, device=self.device)
         _check(load().mpm_debug_p2g(self._ctx, float(dt), ctypes.c_void_p(g.data_ptr()), 1), self._ctx)
         return g
+
+    def set_p2g_variant(self, variant: int):
+        _check(load().mpm_set_p2g_variant(self._ctx, int(variant)), self._ctx)
 
     def profile_enable(self, on: bool = True):
         _check(load().mpm_profile_enable(self._ctx, 1 if on else 0), self._ctx)

@@ -189,11 +189,12 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-def test_p2g_grid_small_elastic(M):
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
     gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
-    with M.Simulator(64, 1 / 64, [gm]) as sim:
+    with M.Simulator(64, 1 / 64, [gm], p2g_variant=variant) as sim:
         sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
@@ -213,11 +214,12 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-def test_p2g_grid_snow_full_size(M):
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
     gm, om = mats_pair(M, M.SNOW, E=1.4e5, nu=0.2, rho=400.0)
-    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP) as sim:
+    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP, p2g_variant=variant) as sim:
         sim.add_particles(torch.from_numpy(x).cuda())
         _p2g_parity(M, sim, [gm], [om], x, vol, 5e-5, 256)
 
@@ -388,3 +390,35 @@ def test_host_buffers_and_side_stream(M):
         orc.substep(cfg, om, s, 1e-4)
     assert linf(host["x"].numpy(), s.x) <= 1e-4
     assert linf(host["v"].numpy(), s.v) <= 1e-4 * np.abs(s.v).max()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_p2g_sparse_cloud_tile_fallback(M, variant):
+    """Particles spread over the whole domain: each 256-particle tile's box is
+    far larger than the shared-memory tile, so the tile variant takes its
+    direct-atomics fallback; results must not change."""
+    x = scenes.cube_uniform(21, 5000, 0.1, 0.9)
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    vol = (1 / 64) ** 3 / 8
+    with M.Simulator(64, 1 / 64, [gm], p2g_variant=variant) as sim:
+        sim.add_particles(x)
+        _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
+
+
+def test_autotuner_picks_a_variant_and_keeps_parity(M):
+    from paper_2111_00699_gb300 import tune
+    x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
+    vol = 0.008 / 8192
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
+    cfg = orc.config(64, 1 / 64, orc.STICKY)
+    with M.Simulator(64, 1 / 64, [gm]) as sim:
+        sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
+        res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1)
+        assert res["best"] in (0, 1, 2) and all(v > 0 for v in res["ms"].values())
+        ran = sim.stats()["substeps"]
+        s = orc.State(x.astype(np.float64), vol=vol)
+        for _ in range(ran):
+            orc.substep(cfg, om, s, 1e-4)
+        g = {k: v.double().cpu().numpy() for k, v in sim.read_state().items()}
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
