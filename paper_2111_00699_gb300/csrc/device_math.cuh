@@ -61,6 +61,16 @@ __device__ __forceinline__ void bspline(float f, float w[3])
 // exact Jacobi angles.  Result: F = U diag(sig) V^T, det U = det V = +1,
 // sig[0] >= sig[1] >= |sig[2]|, sig[2] < 0 for inverted F.
 
+// 1/sqrt(x) to ~1 ulp: the fast-math rsqrt plus one Newton step.  The
+// orthogonality of a rotation (c^2 + s^2 = 1 with s = t c) depends only on
+// the accuracy of c = 1/sqrt(1 + t^2), and errors in it feed straight into
+// sigma - 1, i.e. into the stress.
+__device__ __forceinline__ float rsqrt_nr(float x)
+{
+    float y = rsqrtf(x);
+    return y * (1.5f - 0.5f * x * y * y);
+}
+
 __device__ __forceinline__ void jacobi_pair(float& spp, float& sqq, float& spq, float& srp, float& srq,
                                             float* V, int p, int q)
 {
@@ -73,7 +83,7 @@ __device__ __forceinline__ void jacobi_pair(float& spp, float& sqq, float& spq, 
     float theta = (sqq - spp) / (2.0f * spq);
     float at = fabsf(theta);
     float t = at > 1e15f ? 0.5f / theta : copysignf(1.0f, theta) / (at + sqrtf(theta * theta + 1.0f));
-    float c = rsqrtf(t * t + 1.0f);
+    float c = rsqrt_nr(t * t + 1.0f);
     float s = t * c;
     spp -= t * spq;
     sqq += t * spq;
@@ -120,7 +130,7 @@ __device__ __forceinline__ void givens_rows(float* B, float* U, int i, int j)
         return;
     }
     float r2 = a * a + b * b;
-    float ir = rsqrtf(r2);
+    float ir = rsqrt_nr(r2);
     float c = a * ir, s = b * ir;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
