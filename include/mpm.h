@@ -193,6 +193,33 @@ mpm_status mpm_radix_sort_pairs(const uint32_t* keys_in, const int32_t* vals_in,
                                 uint32_t* keys_out, int32_t* vals_out, int64_t n, int key_bits,
                                 void* scratch, size_t* scratch_bytes, void* cuda_stream);
 
+/* Allocation-free variant of mpm_radix_sort_pairs.  The paper has no
+ * counterpart; it exists for callers that must not allocate device memory
+ * themselves or through the library: a host engine or plugin that owns every
+ * device allocation and gives libraries no allocator hook, or a per-frame
+ * callback in a real-time loop where an allocation may synchronize the device
+ * and blow the frame budget.  Such a caller passes only its inputs and
+ * outputs (device pointers, same layout and meaning as in
+ * mpm_radix_sort_pairs, which must not alias); the scratch lives in one
+ * fixed array of device memory inside the library, sized for
+ * MPM_SORT_NOALLOC_MAX_KEYS keys (about 8.5 MB), which every GPU that loads
+ * the library holds until the process exits.
+ *   - n > MPM_SORT_NOALLOC_MAX_KEYS returns MPM_ECAPACITY and launches nothing.
+ *   - The first call on each device looks up that device's address of the
+ *     array (a one-time set-up with that device current); make that first
+ *     call before any CUDA stream capture.
+ *   - No call allocates or frees memory (no cudaMalloc / cudaFree, no
+ *     allocating library routine).
+ *   - All calls share the one array and it keeps whatever the last call left
+ *     there: every call overwrites what it reads, so nothing carries over, but
+ *     two calls whose GPU work overlaps (different streams, or different
+ *     host threads) race on it and corrupt each other's result.
+ * Asynchronous on cuda_stream. */
+#define MPM_SORT_NOALLOC_MAX_KEYS (1 << 20)
+mpm_status mpm_radix_sort_pairs_noalloc(const uint32_t* keys_in, const int32_t* vals_in,
+                                        uint32_t* keys_out, int32_t* vals_out, int64_t n,
+                                        int key_bits, void* cuda_stream);
+
 /* Batched SVD / stress evaluation of the constitutive model (Sec. 4.1:
  * SVD, plasticity projection and stress computation), for testing the
  * device routines in isolation.  F: n x 9, Jp: n; outputs U, V: n x 9,

@@ -20,6 +20,7 @@ STATUS_NAMES = ["MPM_OK", "MPM_EINVAL", "MPM_ENOMEM", "MPM_ECAPACITY", "MPM_EDOM
 ELASTIC, FLUID, SNOW, SAND = 0, 1, 2, 3
 STICKY, SLIP = 0, 1
 PHASES = 4
+SORT_NOALLOC_MAX_KEYS = 1 << 20
 P2G_VARIANTS = ("direct", "strided", "tile")
 
 
@@ -73,6 +74,7 @@ _PROTOS = {
     "mpm_profile_enable": (I, [P, I]),
     "mpm_profile_read": (I, [P, P, P, I]),
     "mpm_radix_sort_pairs": (I, [P, P, P, P, I64, I, P, P, P]),
+    "mpm_radix_sort_pairs_noalloc": (I, [P, P, P, P, I64, I, P]),
     "mpm_debug_svd": (I, [P, P, P, P, I64]),
     "mpm_debug_stress": (I, [P, P, P, P, I64]),
     "mpm_debug_plasticity": (I, [P, P, P, I64]),

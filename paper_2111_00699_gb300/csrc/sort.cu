@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace mpm {
@@ -289,6 +291,73 @@ extern "C" mpm_status mpm_radix_sort_pairs(const uint32_t* keys_in, const int32_
         return MPM_EINVAL;
     if (n > (int64_t)0x7fffffff)
         return MPM_EINVAL;
+    cudaError_t e = mpm::radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, scratch,
+                                          (cudaStream_t)cuda_stream, nullptr);
+    return e == cudaSuccess ? MPM_OK : MPM_ECUDA;
+}
+
+// ---- allocation-free entry point ---------------------------------------------
+// Scratch for mpm_radix_sort_pairs_noalloc lives in one file-scope device
+// array, laid out as radix_sort_pairs expects for MPM_SORT_NOALLOC_MAX_KEYS
+// keys: two ping-pong arrays of keys and values, the digit histogram of every
+// 2048-key tile, and the scan's tile sums, each rounded up to 256 bytes.
+namespace {
+
+constexpr int64_t kNoAllocKeys = MPM_SORT_NOALLOC_MAX_KEYS;
+constexpr size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr int64_t kNoAllocTiles = (kNoAllocKeys + mpm::kTile - 1) / mpm::kTile;
+constexpr size_t kNoAllocBytes = round256((size_t)kNoAllocKeys * 4) * 2 + round256((size_t)256 * kNoAllocTiles * 4) +
+                                 round256((size_t)((256 * kNoAllocTiles + mpm::kTile - 1) / mpm::kTile + 1) * 4);
+
+__device__ __align__(256) unsigned char g_sort_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_sort_scratch on the current device (looked up once per
+// device; host code must not hand the symbol itself to a kernel).
+cudaError_t noalloc_scratch(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess)
+            return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" mpm_status mpm_radix_sort_pairs_noalloc(const uint32_t* keys_in, const int32_t* vals_in,
+                                                   uint32_t* keys_out, int32_t* vals_out, int64_t n, int key_bits,
+                                                   void* cuda_stream)
+{
+    if (n < 0 || key_bits < 1 || key_bits > 32)
+        return MPM_EINVAL;
+    if (n > kNoAllocKeys)
+        return MPM_ECAPACITY;
+    if (n == 0)
+        return MPM_OK;
+    if (!keys_in || !vals_in || !keys_out || !vals_out)
+        return MPM_EINVAL;
+    if (mpm::radix_sort_scratch_bytes(n) > kNoAllocBytes)
+        return MPM_ECAPACITY;
+    void* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess)
+        return MPM_ECUDA;
+    // Every word of scratch a pass reads was written earlier in the same call
+    // (histograms, scanned offsets, ping-pong buffers), so nothing needs clearing.
     cudaError_t e = mpm::radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, scratch,
                                           (cudaStream_t)cuda_stream, nullptr);
     return e == cudaSuccess ? MPM_OK : MPM_ECUDA;

@@ -270,3 +270,22 @@ def debug_plasticity(mat, F: torch.Tensor, Jp: torch.Tensor):
     _check(load().mpm_debug_plasticity(ctypes.byref(mat), ctypes.c_void_p(F.data_ptr()),
                                        ctypes.c_void_p(Jp.data_ptr()), F.shape[0]))
     return F.reshape(-1, 3, 3), Jp
+
+
+def radix_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32,
+                             out: tuple | None = None, stream=None):
+    """Stable sort of (key, value) pairs with the library's fixed scratch array
+    (mpm_radix_sort_pairs_noalloc): no device memory is allocated by the call.
+    Pass preallocated output tensors in `out` to allocate nothing at all."""
+    lib = load()
+    assert keys.is_cuda and vals.is_cuda and keys.numel() == vals.numel()
+    n = keys.numel()
+    kin = keys.contiguous().view(torch.int32)
+    vin = vals.contiguous()
+    assert vin.dtype == torch.int32
+    kout, vout = out if out is not None else (torch.empty_like(kin), torch.empty_like(vin))
+    s = stream if stream is not None else torch.cuda.current_stream(keys.device)
+    _check(lib.mpm_radix_sort_pairs_noalloc(ctypes.c_void_p(kin.data_ptr()), ctypes.c_void_p(vin.data_ptr()),
+                                            ctypes.c_void_p(kout.data_ptr()), ctypes.c_void_p(vout.data_ptr()),
+                                            n, key_bits, ctypes.c_void_p(s.cuda_stream)))
+    return kout.view(keys.dtype), vout
