@@ -158,9 +158,15 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- main arm
 
-def _lib_variant_name(v):
+def _variant_name(kind, v):
     from paper_2111_00699_gb300 import _lib
-    return _lib.P2G_VARIANTS[v] if 0 <= v < len(_lib.P2G_VARIANTS) else None
+    names = _lib.P2G_VARIANTS if kind == "P2G" else _lib.G2P_VARIANTS
+    return names[v] if 0 <= v < len(names) else None
+
+
+KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
+                        "chunk4": "k_p2g_chunk<4>", "chunk8": "k_p2g_chunk<8>"},
+                "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>"}}
 
 
 def _traffic_for(kernel, src_hash):
@@ -183,7 +189,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
-                    help="P2G scatter variant (0 direct, 1 strided, 2 tile); -1 = autotune")
+                    help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8); -1 = autotune")
+    ap.add_argument("--g2p-variant", type=int, default=-1,
+                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8); -1 = autotune")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -213,21 +221,29 @@ def main():
     stream = torch.cuda.Stream()
     xs = torch.from_numpy(x).cuda()
 
-    def fresh_sim(variant=2):
-        sim = mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream, p2g_variant=variant)
+    def fresh_sim(variant=4, gvariant=2):
+        sim = mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream, p2g_variant=variant,
+                            g2p_variant=gvariant)
         sim.add_particles(xs)
         return sim
 
     # ---- device-resident throughput (the `value`) ----
     from paper_2111_00699_gb300 import tune
     sim = fresh_sim()
-    tuned = {"best_name": _lib_variant_name(args.p2g_variant), "ms": None}
+    tuned = {"best": args.p2g_variant, "best_name": _variant_name("P2G", args.p2g_variant), "ms": None}
+    tuned_g = {"best": args.g2p_variant, "best_name": _variant_name("G2P", args.g2p_variant), "ms": None}
     warm = args.warmup
     if args.p2g_variant < 0:
-        tuned = tune.tune_p2g(sim, DT, steps=20, rounds=2)      # advances 120 substeps
-        warm = max(3, warm - 120)
+        tuned = tune.tune_p2g(sim, DT, steps=20, rounds=2)      # advances 200 substeps
+        warm -= 200
     else:
         sim.set_p2g_variant(args.p2g_variant)
+    if args.g2p_variant < 0:
+        tuned_g = tune.tune_g2p(sim, DT, steps=20, rounds=2)    # advances 120 substeps
+        warm -= 120
+    else:
+        sim.set_g2p_variant(args.g2p_variant)
+    warm = max(3, warm)
     sim.run(warm, DT)
     sim.sync()
     launches0 = sim.stats()["kernel_launches"]
@@ -280,8 +296,8 @@ def main():
     hbm = hbm or 6800.0
     achieved = algo[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
     src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", "substep.cu"), "rb").read()).hexdigest()
-    p2g_name = "k_p2g_" + (tuned.get("best_name") or "tile")
-    kernel_name = {"p2g": p2g_name, "g2p": "k_g2p", "grid": "k_grid"}[dom]
+    kernel_name = {"p2g": KERNEL_NAMES["P2G"][tuned["best_name"]], "g2p": KERNEL_NAMES["G2P"][tuned_g["best_name"]],
+                   "grid": "k_grid"}[dom]
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_note,
                 "algorithmic_bytes_per_launch": algo[dom], "avg_launch_ms": avg[dom],
@@ -292,7 +308,7 @@ def main():
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if args.e2e_frames > 0:
-        sim = fresh_sim(tuned.get("best", max(args.p2g_variant, 0)))
+        sim = fresh_sim(tuned["best"], tuned_g["best"])
         host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
                 for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
         sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
@@ -333,7 +349,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_frame": ms_per_step * SUBSTEPS_PER_FRAME,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
-            "clocks": clk.summary(), "p2g_variant": tuned, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
+            "clocks": clk.summary(), "p2g_variant": tuned, "g2p_variant": tuned_g, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu}
     print(json.dumps(line))
     if world > 1:

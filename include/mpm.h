@@ -84,8 +84,11 @@ typedef struct {
     int64_t max_particles; /* 0: grow without bound (4x when half full) */
     int32_t use_g2p2g;     /* reserved: fused G2P2G transfer; 0 = separate phases */
     int32_t p2g_variant;   /* tuning: 0 direct float4 atomics, 1 cell-strided lanes,
-                              2 shared-memory node tile per CTA (see the autotuner) */
-    int32_t reserved[6];
+                              2 shared-memory node tile per CTA, 3/4 register
+                              accumulation over runs of 4/8 particles (see the autotuner) */
+    int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
+                              registers over runs of 4/8 particles */
+    int32_t reserved[5];
 } mpm_config;
 
 /* Device memory provider.  alloc returns device memory usable on `stream`
@@ -172,6 +175,8 @@ mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
 /* Switch the P2G scatter variant (mpm_config.p2g_variant) between substeps;
  * used by the autotuner.  Results are identical up to float summation order. */
 mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant);
+/* Same for the G2P gather variant (mpm_config.g2p_variant). */
+mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
 
 /* Per-phase timing with CUDA events on the context's stream.  Phase ids:
  * 0 rebuild, 1 P2G, 2 grid update, 3 G2P.  mpm_profile_read syncs and

@@ -21,7 +21,8 @@ ELASTIC, FLUID, SNOW, SAND = 0, 1, 2, 3
 STICKY, SLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
-P2G_VARIANTS = ("direct", "strided", "tile")
+P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8")
+G2P_VARIANTS = ("direct", "chunk4", "chunk8")
 
 
 class Material(ctypes.Structure):
@@ -33,7 +34,8 @@ class Material(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("res", ctypes.c_int32 * 3), ("dx", ctypes.c_float), ("boundary", ctypes.c_int32),
                 ("wall", ctypes.c_int32), ("gravity", ctypes.c_float * 3), ("max_particles", ctypes.c_int64),
-                ("use_g2p2g", ctypes.c_int32), ("p2g_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("use_g2p2g", ctypes.c_int32), ("p2g_variant", ctypes.c_int32), ("g2p_variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -71,6 +73,7 @@ _PROTOS = {
     "mpm_read_blocks": (I, [P, P, I64, P]),
     "mpm_debug_p2g": (I, [P, F, P, I]),
     "mpm_set_p2g_variant": (I, [P, I]),
+    "mpm_set_g2p_variant": (I, [P, I]),
     "mpm_profile_enable": (I, [P, I]),
     "mpm_profile_read": (I, [P, P, P, I]),
     "mpm_radix_sort_pairs": (I, [P, P, P, P, I64, I, P, P, P]),

@@ -386,6 +386,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         return MPM_ENOTSUP;
     if (cfg->p2g_variant < 0 || cfg->p2g_variant >= kP2GVariants)
         return MPM_EINVAL;
+    if (cfg->g2p_variant < 0 || cfg->g2p_variant >= kG2PVariants)
+        return MPM_EINVAL;
     for (int i = 0; i < n_mats; ++i)
         if (!valid_material(mats[i]))
             return MPM_EINVAL;
@@ -566,7 +568,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     launch_grid_update(ctx->sp, gv, dt, s);
     prof_end(ctx, 2, e1);
     prof_begin(ctx, e2);
-    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, s);
+    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.g2p_variant, s);
     prof_end(ctx, 3, e2);
     ctx->launches += 3;
     CK(cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s));
@@ -740,6 +742,14 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant)
     if (!ctx || variant < 0 || variant >= kP2GVariants)
         return MPM_EINVAL;
     ctx->cfg.p2g_variant = variant;
+    return MPM_OK;
+}
+
+mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant)
+{
+    if (!ctx || variant < 0 || variant >= kG2PVariants)
+        return MPM_EINVAL;
+    ctx->cfg.g2p_variant = variant;
     return MPM_OK;
 }
 

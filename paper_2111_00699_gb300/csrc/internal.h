@@ -26,7 +26,17 @@ enum P2GVariant : int {
     P2G_DIRECT = 0,   // thread per particle in storage order, float4 global atomics
     P2G_STRIDED = 1,  // lanes take every 8th particle of a 256-particle tile (distinct cells), float4 atomics
     P2G_TILE = 2,     // CTA accumulates its 256 particles into a shared-memory node tile, one flush
-    kP2GVariants = 3
+    P2G_CHUNK4 = 3,   // thread walks 4 consecutive particles, register accumulation per base-cell run
+    P2G_CHUNK8 = 4,   // same with 8 particles per thread
+    kP2GVariants = 5
+};
+
+// G2P gather variants (tuning knob mpm_config.g2p_variant).
+enum G2PVariant : int {
+    G2P_DIRECT = 0,   // thread per particle, 27 gathers
+    G2P_CHUNK4 = 1,   // thread walks 4 consecutive particles, node velocities cached per base cell
+    G2P_CHUNK8 = 2,   // same with 8 particles per thread
+    kG2PVariants = 3
 };
 
 // Device status word bits.
@@ -102,7 +112,7 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
 void launch_prepare_stress(const SimParams& sp, const PartView& pv, int64_t n, cudaStream_t s);
 void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s);
 void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
-                uint32_t* flags, uint32_t* err, cudaStream_t s);
+                uint32_t* flags, uint32_t* err, int variant, cudaStream_t s);
 MatParams make_mat_params(const mpm_material& m);
 void launch_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n, cudaStream_t s);
 void launch_debug_stress(const MatParams& mp, const float* F, const float* Jp, float* tau, int64_t n,

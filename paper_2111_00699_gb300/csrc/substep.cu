@@ -254,6 +254,115 @@ __global__ void __launch_bounds__(kTileThreads) k_p2g_tile(SimParams sp, PartVie
     }
 }
 
+// P2G_CHUNK4 / P2G_CHUNK8: a thread walks K consecutive particles of the
+// cell-sorted storage order.  Particles with the same base cell (about 8 per
+// cell after the sort of Sec. 4.2.2) add into 27 node accumulators held in
+// registers; the accumulators go to global memory (27 float4 reductions)
+// only when the base cell changes and at the end of the chunk.  Reductions
+// per particle drop from 27 to 27 x (runs per chunk) / K.
+struct NodeAcc {
+    float4 a[27];
+};
+
+__device__ __forceinline__ void acc_zero(NodeAcc& acc)
+{
+#pragma unroll
+    for (int n = 0; n < 27; ++n)
+        acc.a[n] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+// acc += contributions of particle q (same base cell as the accumulator).
+// The affine term is split per axis: (mv + A d) = (mv + A_y dy + A_z dz) +
+// A_x dx, with the (j, k) part computed once per row.
+__device__ __forceinline__ void acc_add(NodeAcc& acc, const P2GParticle& q)
+{
+    float dxo[3], dyo[3], dzo[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dxo[i] = (float)i - q.f[0];
+        dyo[i] = (float)i - q.f[1];
+        dzo[i] = (float)i - q.f[2];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float wyz = q.w[1][j] * q.w[2][k];
+            float bx = q.mv[0] + q.A[1] * dyo[j] + q.A[2] * dzo[k];
+            float by = q.mv[1] + q.A[4] * dyo[j] + q.A[5] * dzo[k];
+            float bz = q.mv[2] + q.A[7] * dyo[j] + q.A[8] * dzo[k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float wt = q.w[0][i] * wyz;
+                float4& a = acc.a[i + 3 * j + 9 * k];
+                a.x += wt * (bx + q.A[0] * dxo[i]);
+                a.y += wt * (by + q.A[3] * dxo[i]);
+                a.z += wt * (bz + q.A[6] * dxo[i]);
+                a.w += wt * q.mp;
+            }
+        }
+}
+
+__device__ __forceinline__ void acc_flush(const GridView& gv, const NodeAcc& acc, const int* b, uint32_t* err)
+{
+    int pb[8];
+    if (!stencil_blocks(gv, b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int nz = (b[2] & 3) + k;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int ny = (b[1] & 3) + j;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                int nx = (b[0] & 3) + i;
+                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
+                atomicAdd(&gv.cur[(int64_t)blk * 64 + local], acc.a[i + 3 * j + 9 * k]);
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kTransferThreads) k_p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                float dt, uint32_t* __restrict__ err)
+{
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
+    if (p0 >= n)
+        return;
+    NodeAcc acc;
+    acc_zero(acc);
+    int cb[3] = {0, 0, 0};
+    bool open = false;
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+        int64_t p = p0 + j;
+        if (p >= n)
+            break;
+        P2GParticle q;
+        if (!load_p2g_particle(sp, pv, p, dt, q, err))
+            continue;
+        if (open && (q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2])) {
+            acc_flush(gv, acc, cb, err);
+            acc_zero(acc);
+            open = false;
+        }
+        if (!open) {
+            cb[0] = q.b[0];
+            cb[1] = q.b[1];
+            cb[2] = q.b[2];
+            open = true;
+        }
+        acc_add(acc, q);
+    }
+    if (open)
+        acc_flush(gv, acc, cb, err);
+}
+
 // Kirchhoff stress of the stored F and Jp, for states P2G has not seen yet
 // (after mpm_write_state).
 __global__ void k_prepare_stress(SimParams sp, PartView pv, int64_t n)
@@ -329,15 +438,10 @@ __device__ __forceinline__ bool range_mapped(const SimParams& sp, const GridView
     return ok;
 }
 
-__global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView pv, GridView gv, int64_t n,
-                                                          float dt, uint32_t* __restrict__ flags,
-                                                          uint32_t* __restrict__ err)
+// Weights of one particle for G2P; false if its stencil left the grid.
+__device__ __forceinline__ bool g2p_weights(const SimParams& sp, const PartView& pv, int64_t p, float* x, int* b,
+                                            float* f, float (*w)[3], uint32_t* err)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
-        return;
-    float x[3], f[3], w[3][3];
-    int b[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         x[a] = pv.ch(CH_X + a)[p];
@@ -347,35 +451,32 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
     }
     if (!in_grid(sp, b, x)) {
         atomicOr(err, ST_EDOMAIN);
-        return;
+        return false;
     }
-    int pb[8];
-    if (!stencil_blocks(gv, b, pb)) {
-        atomicOr(err, ST_MISSED);
-        return;
-    }
-    float vp[3] = {0.0f, 0.0f, 0.0f};
-    float Bm[9];
+    return true;
+}
+
+// vp = sum w v_i, Bm = sum w v_i (node - f)^T over the 27 stencil nodes,
+// node velocities given by vel(i, j, k) -> float3.
+template <class Vel>
+__device__ __forceinline__ void g2p_accumulate(const float* f, const float (*w)[3], Vel vel, float* vp, float* Bm)
+{
+    vp[0] = vp[1] = vp[2] = 0.0f;
 #pragma unroll
     for (int e = 0; e < 9; ++e)
         Bm[e] = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int nz = (b[2] & 3) + k;
         float dz = (float)k - f[2];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            int ny = (b[1] & 3) + j;
             float dy = (float)j - f[1];
             float wyz = w[1][j] * w[2][k];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                int nx = (b[0] & 3) + i;
                 float dxo = (float)i - f[0];
                 float wt = w[0][i] * wyz;
-                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
-                float4 g = gv.cur[(int64_t)blk * 64 + local];
+                float3 g = vel(i, j, k);
                 float gx = wt * g.x, gy = wt * g.y, gz = wt * g.z;
                 vp[0] += gx;
                 vp[1] += gy;
@@ -386,6 +487,15 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
             }
         }
     }
+}
+
+// Everything after the gather: C, x, v, the F update with the return map and
+// the stress for the next P2G (or the fluid J update), and the free-zone test
+// of Sec. 4.2.1.
+__device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
+                                           const float* x, const int* b, const float* vp, const float* Bm, float dt,
+                                           uint32_t* __restrict__ flags, uint32_t* __restrict__ err)
+{
     // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
     float C[9];
     float c4 = 4.0f * sp.inv_dx;
@@ -460,6 +570,87 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
             int lo2[3] = {bn[0], bn[1], bn[2]}, hi2[3] = {bn[0] + 2, bn[1] + 2, bn[2] + 2};
             atomicOr(flags, range_mapped(sp, gv, lo2, hi2) ? ST_REBUILD_SOFT : (ST_REBUILD_SOFT | ST_REBUILD_HARD));
         }
+    }
+}
+
+__global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                          float dt, uint32_t* __restrict__ flags,
+                                                          uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float x[3], f[3], w[3][3];
+    int b[3];
+    if (!g2p_weights(sp, pv, p, x, b, f, w, err))
+        return;
+    int pb[8];
+    if (!stencil_blocks(gv, b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+    const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
+    float vp[3], Bm[9];
+    g2p_accumulate(f, w, [&](int i, int j, int k) {
+        int nx = bx + i, ny = by + j, nz = bz + k;
+        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+        return make_float3(g.x, g.y, g.z);
+    }, vp, Bm);
+    g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+}
+
+// A thread walks K consecutive particles (cell-sorted storage order) and keeps
+// the 27 node velocities of the current base cell in registers, loading them
+// again only when the base cell changes (about once per 8 particles after the
+// sort), instead of 27 gathers per particle.
+template <int K>
+__global__ void __launch_bounds__(kTransferThreads) k_g2p_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                float dt, uint32_t* __restrict__ flags,
+                                                                uint32_t* __restrict__ err)
+{
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
+    if (p0 >= n)
+        return;
+    float3 cache[27];
+    int cb[3] = {-1, -1, -1};
+    bool have = false;
+#pragma unroll 1
+    for (int jj = 0; jj < K; ++jj) {
+        int64_t p = p0 + jj;
+        if (p >= n)
+            break;
+        float x[3], f[3], w[3][3];
+        int b[3];
+        if (!g2p_weights(sp, pv, p, x, b, f, w, err))
+            continue;
+        if (!have || b[0] != cb[0] || b[1] != cb[1] || b[2] != cb[2]) {
+            int pb[8];
+            if (!stencil_blocks(gv, b, pb)) {
+                atomicOr(err, ST_MISSED);
+                have = false;
+                continue;
+            }
+            const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        int nx = bx + i, ny = by + j, nz = bz + k;
+                        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+                        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+                        cache[i + 3 * j + 9 * k] = make_float3(g.x, g.y, g.z);
+                    }
+            cb[0] = b[0];
+            cb[1] = b[1];
+            cb[2] = b[2];
+            have = true;
+        }
+        float vp[3], Bm[9];
+        g2p_accumulate(f, w, [&](int i, int j, int k) { return cache[i + 3 * j + 9 * k]; }, vp, Bm);
+        g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
     }
 }
 
@@ -544,7 +735,11 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n <= 0)
         return;
-    if (variant == P2G_STRIDED)
+    if (variant == P2G_CHUNK8)
+        k_p2g_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else if (variant == P2G_CHUNK4)
+        k_p2g_chunk<4><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else if (variant == P2G_STRIDED)
         k_p2g_strided<<<blocks_for(n, kTileThreads), kTileThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_TILE)
         k_p2g_tile<<<blocks_for(n, kTileThreads), kTileThreads, 0, s>>>(sp, pv, gv, n, dt, err);
@@ -565,10 +760,19 @@ void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaS
 }
 
 void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* flags,
-                uint32_t* err, cudaStream_t s)
+                uint32_t* err, int variant, cudaStream_t s)
 {
     if (n > 0)
-        k_g2p<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+    {
+        if (variant == G2P_CHUNK8)
+            k_g2p_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                                 flags, err);
+        else if (variant == G2P_CHUNK4)
+            k_g2p_chunk<4><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                                 flags, err);
+        else
+            k_g2p<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+    }
 }
 
 void launch_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n, cudaStream_t s)

@@ -49,7 +49,7 @@ class Simulator:
 
     def __init__(self, res, dx, materials, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0),
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
-                 device=None, p2g_variant: int = 2):
+                 device=None, p2g_variant: int = 4, g2p_variant: int = 2):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -68,6 +68,7 @@ class Simulator:
         cfg.max_particles = int(max_particles)
         cfg.use_g2p2g = 0
         cfg.p2g_variant = int(p2g_variant)
+        cfg.g2p_variant = int(g2p_variant)
         mats = (_lib.Material * len(self.materials))(*self.materials)
         self._alloc = None
         if torch_allocator:
@@ -205,6 +206,9 @@ class Simulator:
 
     def set_p2g_variant(self, variant: int):
         _check(load().mpm_set_p2g_variant(self._ctx, int(variant)), self._ctx)
+
+    def set_g2p_variant(self, variant: int):
+        _check(load().mpm_set_g2p_variant(self._ctx, int(variant)), self._ctx)
 
     def profile_enable(self, on: bool = True):
         _check(load().mpm_profile_enable(self._ctx, 1 if on else 0), self._ctx)

@@ -189,7 +189,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -214,7 +214,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -392,7 +392,7 @@ def test_host_buffers_and_side_stream(M):
     assert linf(host["v"].numpy(), s.v) <= 1e-4 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_p2g_sparse_cloud_tile_fallback(M, variant):
     """Particles spread over the whole domain: each 256-particle tile's box is
     far larger than the shared-memory tile, so the tile variant takes its
@@ -414,7 +414,9 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     with M.Simulator(64, 1 / 64, [gm]) as sim:
         sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
         res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1)
-        assert res["best"] in (0, 1, 2) and all(v > 0 for v in res["ms"].values())
+        assert res["best"] in range(5) and all(v > 0 for v in res["ms"].values())
+        res = tune.tune_g2p(sim, 1e-4, steps=2, rounds=1)
+        assert res["best"] in range(3) and all(v > 0 for v in res["ms"].values())
         ran = sim.stats()["substeps"]
         s = orc.State(x.astype(np.float64), vol=vol)
         for _ in range(ran):
@@ -422,3 +424,22 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
         g = {k: v.double().cpu().numpy() for k, v in sim.read_state().items()}
     assert linf(g["x"], s.x) <= 1e-4
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+
+
+@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0)])
+def test_substeps_variant_combinations(M, p2g, g2p):
+    """Every P2G / G2P launch variant computes the same substep (10 substeps
+    of a moving, deforming elastic block against the oracle)."""
+    x, _ = scenes.blocks(17, 12000, 64, 2)
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    rng = np.random.default_rng(5)
+    v = (0.5 * rng.normal(size=(len(x), 3))).astype(np.float32)
+    vol = (1 / 64) ** 3 / 8
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, p2g_variant=p2g, g2p_variant=g2p) as sim:
+        sim.add_particles(x, v=v)
+        s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+        g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+    assert linf(g["C"], s.C) <= 1e-4 * np.abs(s.C).max()
