@@ -156,6 +156,126 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------- secondary workloads
+
+BATCH_MATS = [dict(kind=0, E=1e4, nu=0.2, rho=1000.0), dict(kind=1, E=1e4, gamma=7.0, rho=1000.0),
+              dict(kind=2, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
+              dict(kind=3, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0)]
+BATCH_DT = [1e-4, 1e-4, 5e-5, 1e-4]
+
+
+def _events_time(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def bench_batched(steps=100, warmup=5):
+    """256 independent scenes (log-uniform 2K-64K particles, 32^3-128^3 grids,
+    four materials): one batched launch per phase, replayed from CUDA graphs,
+    against one Simulator (three launches per substep) per scene."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    bs = scenes.batched_scenes(4)
+    total = sum(len(b["x"]) for b in bs)
+    mats = [mpm.material(**m) for m in BATCH_MATS]
+    dts = np.array([BATCH_DT[b["material"]] for b in bs], np.float32)
+    descs = [dict(res=b["res"], dx=1.0 / b["res"], material=b["material"]) for b in bs]
+    out = {"workload": "256 scenes, %d particles, grids 32^3-128^3, 4 materials (seed 4)" % total,
+           "particles": total, "substeps": steps}
+    with mpm.BatchSimulator(descs, mats, graphs=True) as bsim:
+        for i, b in enumerate(bs):
+            bsim.add_particles(i, b["x"])
+        bsim.run(warmup, dts)
+        tune = {}
+        for k in (1, 4, 8):
+            bsim.set_p2g_chunk(k)
+            bsim.run(2, dts)
+            tune[k] = _events_time(bsim.stream, lambda: bsim.run(10, dts)) / 10
+        best = min(tune, key=tune.get)
+        bsim.set_p2g_chunk(best)
+        bsim.run(2, dts)
+        ms = _events_time(bsim.stream, lambda: bsim.run(steps, dts))
+        bsim.sync()
+        st = bsim.stats()
+    out.update({"value": total * steps / (ms / 1e3), "unit": UNIT, "ms_per_substep": ms / steps,
+                "p2g_chunk": best, "chunk_ms": {str(k): v for k, v in tune.items()}, "remaps": st["remaps"],
+                "graphs": True})
+    # per-scene launches of the plain path on the same stream
+    stream = torch.cuda.Stream()
+    sims = []
+    for b in bs:
+        sim = mpm.Simulator(b["res"], 1.0 / b["res"], [mats[b["material"]]], boundary=mpm.SLIP, stream=stream,
+                            p2g_variant=3, g2p_variant=0)
+        sim.add_particles(b["x"])
+        sims.append(sim)
+
+    def per_scene(k):
+        for _ in range(k):
+            for sim, dt in zip(sims, dts):
+                sim.substep(float(dt))
+
+    per_scene(warmup)
+    ms2 = _events_time(stream, lambda: per_scene(steps))
+    for sim in sims:
+        sim.sync()
+        sim.close()
+    out["per_scene_value"] = total * steps / (ms2 / 1e3)
+    out["per_scene_ms_per_substep"] = ms2 / steps
+    out["batched_over_per_scene"] = out["value"] / out["per_scene_value"]
+    return out
+
+
+def bench_fountain(substeps=3600):
+    """Fountain: weakly compressible fluid (K 1e4, gamma 7) emitted through a
+    disk inlet every substep up to the 143K-particle budget, 128^3, dt 1e-4."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    res, dt = 128, 1e-4
+    vol = (1.0 / res) ** 3 / 8
+    batches = [scenes.fountain_batch(2, k, dt, vol) for k in range(substeps)]
+    stream = torch.cuda.Stream()
+    with mpm.Simulator(res, 1.0 / res, [mpm.material(mpm.FLUID, E=1e4, gamma=7.0, rho=1000.0)],
+                       boundary=mpm.SLIP, stream=stream, p2g_variant=3, g2p_variant=0) as sim:
+        def run():
+            for xe, ve in batches:
+                sim.emit_particles(xe, v=ve)
+                sim.substep(dt)
+        ms = _events_time(stream, run)
+        sim.sync()
+        n_end = sim.n
+        st = sim.stats()
+    ps = sum(len(b[0]) * (substeps - k) for k, b in enumerate(batches))
+    frame = round((1.0 / 60.0) / dt)
+    return {"workload": "fountain, %d substeps, %d particles at the end, 128^3, dt=1e-4" % (substeps, n_end),
+            "value": ps / (ms / 1e3), "unit": UNIT, "ms_per_substep": ms / substeps,
+            "ms_per_frame": ms / substeps * frame, "particles_end": n_end, "rebuilds": st["rebuilds"]}
+
+
+def bench_sand(substeps=1000):
+    """Drucker-Prager sand (phi = 30 deg), 4 random boxes, ~500K particles at
+    8 per cell, 128^3, dt 1e-4."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x, _ = scenes.sand_blocks()
+    stream = torch.cuda.Stream()
+    with mpm.Simulator(128, 1.0 / 128, [mpm.material(mpm.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0)],
+                       boundary=mpm.SLIP, stream=stream, p2g_variant=3, g2p_variant=0) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        sim.run(20, 1e-4)
+        ms = _events_time(stream, lambda: sim.run(substeps, 1e-4))
+        sim.sync()
+        st = sim.stats()
+    return {"workload": "sand blocks, %d particles, 128^3, dt=1e-4" % len(x), "value": len(x) * substeps / (ms / 1e3),
+            "unit": UNIT, "ms_per_substep": ms / substeps, "rebuilds": st["rebuilds"]}
+
+
 # ---------------------------------------------------------------- main arm
 
 def _variant_name(kind, v):
@@ -187,6 +307,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=333)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the batched / fountain / sand sections")
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8); -1 = autotune")
@@ -340,6 +461,15 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    workloads = None
+    if not args.no_workloads and world == 1:
+        workloads = {}
+        for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand)):
+            try:
+                workloads[name] = fn()
+            except Exception as exc:   # report, do not lose the main line
+                workloads[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, sample = oracle_throughput(x, seconds=15.0)
@@ -350,7 +480,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
             "clocks": clk.summary(), "p2g_variant": tuned, "g2p_variant": tuned_g, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
-            "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu}
+            "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu, "workloads": workloads}
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

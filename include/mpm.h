@@ -114,6 +114,17 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
 mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
                              const float* vol0, int material, int on_device);
 
+/* Particle source between substeps (Sec. 4.1: particle addition happens
+ * between G2P and P2G; Sec. 6.4 Fountain).  Same arguments as
+ * mpm_add_particles, but asynchronous: host data is staged through pinned
+ * memory and appended on the context's stream, with no host wait unless the
+ * particle capacity must grow (4x when half full).  New particles are not
+ * sorted until the next rebuild; a rebuild is requested only if some new
+ * particle's stencil, widened by one cell per side, reaches a block that
+ * the last rebuild did not map (device-side input always requests one). */
+mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v,
+                              const float* vol0, int material, int on_device);
+
 /* Advance by one substep of size dt: [rebuild-mapping and sort, when some
  * particle neared the edge of its mapped blocks two substeps ago] ->
  * P2G (stress merged in) -> grid update (boundary merged in, next buffer
@@ -140,6 +151,52 @@ mpm_status mpm_rebuild(mpm_ctx* ctx);
 int64_t mpm_num_particles(const mpm_ctx* ctx);
 const char* mpm_last_error(const mpm_ctx* ctx); /* never NULL; owned by ctx */
 void mpm_destroy(mpm_ctx* ctx);                  /* NULL is a no-op; syncs */
+
+/* ---- batched scenes ---------------------------------------------------- */
+/* Many small independent scenes advanced together: each phase of a substep
+ * is one launch over all scenes, and the substep can be replayed from a CUDA
+ * graph (Sec. 3.1 "minimise the number of kernels", Sec. 4.1 tail effect;
+ * the batching itself is not in the paper).  Grid blocks are indexed by
+ * (scene, Morton code) without compaction, and rebuild-mapping runs per
+ * scene, only for the scenes whose free-zone test fired. */
+typedef struct mpm_batch mpm_batch; /* opaque */
+
+typedef struct {
+    int32_t res[3];        /* 8..512 per axis */
+    float dx;
+    int32_t boundary;      /* mpm_boundary */
+    int32_t wall;
+    float gravity[3];
+    int32_t material;      /* index into the batch's materials */
+} mpm_scene_desc;
+
+/* n_scenes <= 65535 scenes and n_mats <= 255 materials are copied.  Fails
+ * with MPM_ECAPACITY if the scenes' block slots need more than 26 bits. */
+mpm_status mpm_batch_create(int n_scenes, const mpm_scene_desc* scenes, const mpm_material* mats, int n_mats,
+                            const mpm_allocator* allocator, void* cuda_stream, mpm_batch** out);
+/* Host arrays (x, v: n x 3; vol0: n, NULL = dx^3/8; v NULL = 0), before the
+ * first mpm_batch_substep (MPM_ENOTSUP afterwards). */
+mpm_status mpm_batch_add_particles(mpm_batch* b, int scene, int64_t n, const float* x, const float* v,
+                                   const float* vol0);
+/* One substep of every scene; dt: n_scenes host floats.  The first call
+ * uploads and sorts the particles (syncs).  Asynchronous afterwards. */
+mpm_status mpm_batch_substep(mpm_batch* b, const float* dt);
+/* Capture the substep in CUDA graphs and replay them (one graph launch per
+ * substep instead of five stream operations).  Default off; needs a stream
+ * other than the legacy default stream (MPM_EINVAL otherwise). */
+mpm_status mpm_batch_use_graphs(mpm_batch* b, int on);
+/* Tuning: particles per thread in the batched P2G (1, 4 or 8). */
+mpm_status mpm_batch_set_p2g_chunk(mpm_batch* b, int k);
+/* Host copies of one scene's state in that scene's insertion order; any
+ * pointer may be NULL.  Syncs; returns the sticky device error, if any. */
+mpm_status mpm_batch_read_state(mpm_batch* b, int scene, float* x, float* v, float* C, float* F, float* Jp);
+mpm_status mpm_batch_sync(mpm_batch* b);
+/* out4: substeps, per-scene remaps, kernel launches, graph launches. */
+mpm_status mpm_batch_get_stats(const mpm_batch* b, int64_t* out4);
+/* Particles of one scene, or of all scenes for scene == -1. */
+int64_t mpm_batch_num_particles(const mpm_batch* b, int scene);
+const char* mpm_batch_last_error(const mpm_batch* b);
+void mpm_batch_destroy(mpm_batch* b);
 
 /* ---- introspection (tests, benchmarks) ------------------------------- */
 

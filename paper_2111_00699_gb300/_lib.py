@@ -46,6 +46,11 @@ class Allocator(ctypes.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
 
 
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("res", ctypes.c_int32 * 3), ("dx", ctypes.c_float), ("boundary", ctypes.c_int32),
+                ("wall", ctypes.c_int32), ("gravity", ctypes.c_float * 3), ("material", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("substeps", ctypes.c_int64), ("rebuilds", ctypes.c_int64), ("n_pblocks", ctypes.c_int64),
                 ("grid_capacity", ctypes.c_int64), ("particle_capacity", ctypes.c_int64),
@@ -60,6 +65,7 @@ F = ctypes.c_float
 _PROTOS = {
     "mpm_create": (I, [P, P, I, P, P, P]),
     "mpm_add_particles": (I, [P, I64, P, P, P, I, I]),
+    "mpm_emit_particles": (I, [P, I64, P, P, P, I, I]),
     "mpm_substep": (I, [P, F]),
     "mpm_read_state": (I, [P, P, P, P, P, P, I]),
     "mpm_write_state": (I, [P, P, P, P, P, P, I]),
@@ -78,6 +84,17 @@ _PROTOS = {
     "mpm_profile_read": (I, [P, P, P, I]),
     "mpm_radix_sort_pairs": (I, [P, P, P, P, I64, I, P, P, P]),
     "mpm_radix_sort_pairs_noalloc": (I, [P, P, P, P, I64, I, P]),
+    "mpm_batch_create": (I, [I, P, P, I, P, P, P]),
+    "mpm_batch_add_particles": (I, [P, I, I64, P, P, P]),
+    "mpm_batch_substep": (I, [P, P]),
+    "mpm_batch_use_graphs": (I, [P, I]),
+    "mpm_batch_set_p2g_chunk": (I, [P, I]),
+    "mpm_batch_read_state": (I, [P, I, P, P, P, P, P]),
+    "mpm_batch_sync": (I, [P]),
+    "mpm_batch_get_stats": (I, [P, P]),
+    "mpm_batch_num_particles": (I64, [P, I]),
+    "mpm_batch_last_error": (ctypes.c_char_p, [P]),
+    "mpm_batch_destroy": (None, [P]),
     "mpm_debug_svd": (I, [P, P, P, P, I64]),
     "mpm_debug_stress": (I, [P, P, P, P, I64]),
     "mpm_debug_plasticity": (I, [P, P, P, I64]),

@@ -91,6 +91,20 @@ struct mpm_ctx {
     int64_t rebuilds = 0, launches = 0;
     std::string err;
 
+    // host mirror of the block table (refreshed at every rebuild), used to
+    // decide on the host whether emitted particles land in mapped blocks
+    int32_t* htable = nullptr;
+    bool htable_valid = false;
+    // pinned staging ring for asynchronous emission
+    static constexpr int kEmitSlots = 4;
+    float* emit_host[kEmitSlots] = {};
+    size_t emit_host_bytes[kEmitSlots] = {};
+    float* emit_dev[kEmitSlots] = {};
+    size_t emit_dev_bytes[kEmitSlots] = {};
+    cudaEvent_t emit_ev[kEmitSlots] = {};
+    int emit_next = 0;
+    int64_t emitted = 0;
+
     bool prof = false;
     std::vector<ProfRec> prof_recs;
     std::vector<cudaEvent_t> ev_pool;
@@ -321,6 +335,10 @@ mpm_status rebuild(mpm_ctx* ctx)
         ctx->cur = 1 - ctx->cur;
     }
     CK(cudaMemcpyAsync(&ctx->hstat[kRing + 1], &ctx->dstat[1 + kRing], 4, cudaMemcpyDeviceToHost, s));
+    if (ctx->htable) {
+        CK(cudaMemcpyAsync(ctx->htable, ctx->table, (size_t)ctx->n_slots * 4, cudaMemcpyDeviceToHost, s));
+        ctx->htable_valid = true;
+    }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     int32_t npb = (int32_t)ctx->hstat[kRing + 1];
@@ -438,6 +456,16 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         return MPM_ENOMEM;
     }
     memset(ctx->hstat, 0, 256);
+    if (cudaMallocHost(&ctx->htable, (size_t)ctx->n_slots * 4) != cudaSuccess) {
+        ctx->htable = nullptr;
+        mpm_destroy(ctx);
+        return MPM_ENOMEM;
+    }
+    for (int i = 0; i < mpm_ctx::kEmitSlots; ++i)
+        if (cudaEventCreateWithFlags(&ctx->emit_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            mpm_destroy(ctx);
+            return MPM_ECUDA;
+        }
     for (int i = 0; i < kRing; ++i)
         if (cudaEventCreateWithFlags(&ctx->ev[i], cudaEventDisableTiming) != cudaSuccess) {
             mpm_destroy(ctx);
@@ -485,6 +513,15 @@ void mpm_destroy(mpm_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     if (ctx->hstat)
         cudaFreeHost(ctx->hstat);
+    if (ctx->htable)
+        cudaFreeHost(ctx->htable);
+    for (int i = 0; i < mpm_ctx::kEmitSlots; ++i) {
+        if (ctx->emit_host[i])
+            cudaFreeHost(ctx->emit_host[i]);
+        dfree(ctx, ctx->emit_dev[i], ctx->emit_dev_bytes[i]);
+        if (ctx->emit_ev[i])
+            cudaEventDestroy(ctx->emit_ev[i]);
+    }
     for (int i = 0; i < kRing; ++i)
         if (ctx->ev[i])
             cudaEventDestroy(ctx->ev[i]);
@@ -530,6 +567,95 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
     ctx->n += n;
     ctx->need_rebuild = true;
     ctx->keys_valid = false;
+    return MPM_OK;
+}
+
+// True if every node in [b - margin, b + 2 + margin] per axis (clipped to the
+// grid) lies in a block mapped at the last rebuild, by the host mirror.
+static bool host_stencil_mapped(const mpm_ctx* ctx, const float* x, int margin)
+{
+    const SimParams& sp = ctx->sp;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        float X = x[a] * sp.inv_dx - 0.5f;
+        if (!(X > -1.0f && X < (float)sp.res[a]))
+            return false;
+        int b = (int)floorf(X);
+        lo[a] = b - margin < 0 ? 0 : b - margin;
+        hi[a] = b + 2 + margin > sp.res[a] - 1 ? sp.res[a] - 1 : b + 2 + margin;
+        if (b < 0 || b + 2 >= sp.res[a])
+            return false;
+    }
+    for (int z = lo[2] >> 2; z <= hi[2] >> 2; ++z)
+        for (int y = lo[1] >> 2; y <= hi[1] >> 2; ++y)
+            for (int xx = lo[0] >> 2; xx <= hi[0] >> 2; ++xx)
+                if (ctx->htable[morton3((uint32_t)xx, (uint32_t)y, (uint32_t)z)] < 0)
+                    return false;
+    return true;
+}
+
+mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v, const float* vol0,
+                              int material, int on_device)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    if (n < 0 || (n > 0 && !x) || material < 0 || material >= ctx->sp.n_mats)
+        return fail(ctx, MPM_EINVAL, "mpm_emit_particles: bad argument");
+    if (n == 0)
+        return MPM_OK;
+    if (ctx->n + n > ctx->cap / 2 || !ctx->pbuf[0]) {
+        // growth (4x when half full) needs the stream idle; rare by design
+        CK(cudaStreamSynchronize(ctx->stream));
+        mpm_status st = ensure_particle_capacity(ctx, ctx->n + n);
+        if (st != MPM_OK)
+            return st;
+    }
+    const float *dx = x, *dv = v, *dvol = vol0;
+    bool mapped = !ctx->need_rebuild && ctx->htable_valid && !on_device;
+    if (!on_device) {
+        for (int64_t i = 0; i < n && mapped; ++i)
+            mapped = host_stencil_mapped(ctx, x + 3 * i, 1);
+        int slot = ctx->emit_next;
+        ctx->emit_next = (slot + 1) % mpm_ctx::kEmitSlots;
+        CK(cudaEventSynchronize(ctx->emit_ev[slot]));   // the slot's previous copy is done
+        size_t bytes = (size_t)n * 4 * 7;
+        if (bytes > ctx->emit_host_bytes[slot]) {
+            if (ctx->emit_host[slot])
+                cudaFreeHost(ctx->emit_host[slot]);
+            size_t want = bytes * 2;
+            if (cudaMallocHost(&ctx->emit_host[slot], want) != cudaSuccess) {
+                ctx->emit_host[slot] = nullptr;
+                ctx->emit_host_bytes[slot] = 0;
+                return fail(ctx, MPM_ENOMEM, "pinned staging allocation failed");
+            }
+            ctx->emit_host_bytes[slot] = want;
+        }
+        mpm_status st = realloc_buf(ctx, ctx->emit_dev[slot], ctx->emit_dev_bytes[slot], ctx->emit_host_bytes[slot]);
+        if (st != MPM_OK)
+            return st;
+        float* hx = ctx->emit_host[slot];
+        float* hv = hx + 3 * n;
+        float* hw = hv + 3 * n;
+        memcpy(hx, x, (size_t)n * 12);
+        if (v)
+            memcpy(hv, v, (size_t)n * 12);
+        if (vol0)
+            memcpy(hw, vol0, (size_t)n * 4);
+        CK(cudaMemcpyAsync(ctx->emit_dev[slot], hx, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaEventRecord(ctx->emit_ev[slot], ctx->stream));
+        dx = ctx->emit_dev[slot];
+        dv = v ? dx + 3 * n : nullptr;
+        dvol = vol0 ? dx + 6 * n : nullptr;
+    }
+    float dx3 = ctx->sp.dx * ctx->sp.dx * ctx->sp.dx;
+    launch_append(ctx->pv[ctx->cur], ctx->n, n, dx, dv, dvol, dx3 / 8.0f, material, ctx->stream);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    ctx->n += n;
+    ctx->emitted += n;
+    ctx->keys_valid = false;
+    if (!mapped)
+        ctx->need_rebuild = true;
     return MPM_OK;
 }
 

@@ -128,6 +128,17 @@ class Simulator:
             raise ValueError("x, v and vol must all be on the same side (host or device)")
         _check(load().mpm_add_particles(self._ctx, n, px, pv, pw, int(material), flags.pop()), self._ctx)
 
+    def emit_particles(self, x, v=None, vol=None, material: int = 0):
+        """Asynchronous particle source between substeps (mpm_emit_particles)."""
+        n = len(x)
+        px, dx_, kx = _buf(x, torch.float32, (n, 3))
+        pv, dv, kv = _buf(v, torch.float32, (n, 3))
+        pw, dw, kw = _buf(vol, torch.float32, (n,))
+        flags = {f for f, p in ((dx_, px), (dv, pv), (dw, pw)) if p is not None}
+        if len(flags) != 1:
+            raise ValueError("x, v and vol must all be on the same side (host or device)")
+        _check(load().mpm_emit_particles(self._ctx, n, px, pv, pw, int(material), flags.pop()), self._ctx)
+
     def substep(self, dt: float):
         _check(load().mpm_substep(self._ctx, float(dt)), self._ctx)
 
@@ -219,6 +230,123 @@ class Simulator:
         _check(load().mpm_profile_read(self._ctx, ms, la, _lib.PHASES), self._ctx)
         names = ("rebuild", "p2g", "grid", "g2p")
         return {names[i]: (float(ms[i]), int(la[i])) for i in range(_lib.PHASES)}
+
+
+class BatchSimulator:
+    """Many small independent scenes advanced together (mpm_batch_*)."""
+
+    def __init__(self, scenes, materials, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
+                 graphs: bool = True, p2g_chunk: int = 4):
+        lib = load()
+        # graph capture needs a stream other than the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.materials = [materials] if isinstance(materials, _lib.Material) else list(materials)
+        descs = (_lib.SceneDesc * len(scenes))()
+        for d, sc in zip(descs, scenes):
+            res = sc["res"] if hasattr(sc["res"], "__len__") else (sc["res"],) * 3
+            d.res = (ctypes.c_int32 * 3)(*[int(r) for r in res])
+            d.dx = float(sc.get("dx", 1.0 / res[0]))
+            d.boundary = int(sc.get("boundary", SLIP))
+            d.wall = int(sc.get("wall", 3))
+            d.gravity = (ctypes.c_float * 3)(*sc.get("gravity", (0.0, -9.8, 0.0)))
+            d.material = int(sc.get("material", 0))
+        self.n_scenes = len(scenes)
+        mats = (_lib.Material * len(self.materials))(*self.materials)
+        self._alloc = None
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+
+            def _a(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+                except Exception:
+                    return None
+
+            def _f(ptr, nbytes, stream, user):
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
+
+            self._alloc_fns = (_lib.ALLOC_FN(_a), _lib.FREE_FN(_f))
+            self._alloc = _lib.Allocator(self._alloc_fns[0], self._alloc_fns[1], None)
+        self._b = ctypes.c_void_p()
+        _check(lib.mpm_batch_create(self.n_scenes, descs, mats, len(self.materials),
+                                    ctypes.byref(self._alloc) if self._alloc is not None else None,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._b)))
+        self.use_graphs(graphs)
+        self.set_p2g_chunk(p2g_chunk)
+
+    def _err(self, st):
+        if st:
+            raw = load().mpm_batch_last_error(self._b)
+            raise MpmError(st, raw.decode() if raw else "")
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            load().mpm_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_particles(self, scene: int, x, v=None, vol=None):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
+        n = len(x)
+        v = None if v is None else np.ascontiguousarray(v, dtype=np.float32).reshape(n, 3)
+        vol = None if vol is None else np.ascontiguousarray(vol, dtype=np.float32).reshape(n)
+        P = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+        self._err(load().mpm_batch_add_particles(self._b, int(scene), n, P(x), P(v), P(vol)))
+
+    def substep(self, dt):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float32), (self.n_scenes,)))
+        self._dt_keep = d
+        self._err(load().mpm_batch_substep(self._b, d.ctypes.data_as(ctypes.c_void_p)))
+
+    def run(self, steps: int, dt):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float32), (self.n_scenes,)))
+        ptr = d.ctypes.data_as(ctypes.c_void_p)
+        fn = load().mpm_batch_substep
+        for _ in range(steps):
+            st = fn(self._b, ptr)
+            if st:
+                self._err(st)
+
+    def use_graphs(self, on: bool = True):
+        self._err(load().mpm_batch_use_graphs(self._b, 1 if on else 0))
+
+    def set_p2g_chunk(self, k: int):
+        self._err(load().mpm_batch_set_p2g_chunk(self._b, int(k)))
+
+    def sync(self):
+        self._err(load().mpm_batch_sync(self._b))
+
+    def n_particles(self, scene: int = -1) -> int:
+        return int(load().mpm_batch_num_particles(self._b, int(scene)))
+
+    def read_state(self, scene: int) -> dict:
+        n = self.n_particles(scene)
+        out = {"x": np.zeros((n, 3), np.float32), "v": np.zeros((n, 3), np.float32),
+               "C": np.zeros((n, 3, 3), np.float32), "F": np.zeros((n, 3, 3), np.float32),
+               "Jp": np.zeros(n, np.float32)}
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self._err(load().mpm_batch_read_state(self._b, int(scene), P(out["x"]), P(out["v"]), P(out["C"]),
+                                              P(out["F"]), P(out["Jp"])))
+        return out
+
+    def stats(self) -> dict:
+        a = (ctypes.c_int64 * 4)()
+        self._err(load().mpm_batch_get_stats(self._b, a))
+        return {"substeps": a[0], "remaps": a[1], "kernel_launches": a[2], "graph_launches": a[3]}
 
 
 # ---- stand-alone kernels ----------------------------------------------------
