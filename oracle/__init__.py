@@ -19,7 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRCS = ["bspline.c", "svd.c", "material.c", "transfer.c", "keys.c"]
+_SRCS = ["bspline.c", "svd.c", "material.c", "transfer.c", "keys.c", "adjoint.c"]
 
 ELASTIC, FLUID, SNOW, SAND = 0, 1, 2, 3
 STICKY, SLIP = 0, 1
@@ -89,6 +89,10 @@ def lib():
         L.orc_stable_sort.argtypes = [i64, P, P]
         L.orc_pblocks.argtypes = [i64, P, ctypes.c_int32, P]
         L.orc_pblocks.restype = i64
+        L.orc_diff_forward.argtypes = [P, ctypes.c_double, ctypes.c_double, i64, P, P, ctypes.c_double, P, P]
+        L.orc_diff_forward.restype = ctypes.c_int
+        L.orc_diff_adjoint.argtypes = [P, ctypes.c_double, ctypes.c_double, i64, P, P, ctypes.c_double, P, P, P, P]
+        L.orc_diff_adjoint.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -272,3 +276,34 @@ def pblocks(keys, L: int):
     out = np.zeros(max(n, 1), dtype=np.int32)
     lib().orc_pblocks(len(keys), _p(keys), int(L), _p(out))
     return out[:n]
+
+
+def pack_state(x, v, C, F):
+    """(n, 24) FP64 state rows x, v, C, F."""
+    n = len(x)
+    return np.ascontiguousarray(np.concatenate([np.reshape(x, (n, 3)), np.reshape(v, (n, 3)), np.reshape(C, (n, 9)),
+                                                np.reshape(F, (n, 9))], axis=1), dtype=np.float64)
+
+
+def diff_forward(cfg: Config, nu, rho, vol, E, dt, s_in):
+    s_in = _f64(s_in)
+    n = len(s_in)
+    vol = _f64(np.broadcast_to(vol, (n,)))
+    E = _f64(E)
+    out = np.zeros_like(s_in)
+    st = lib().orc_diff_forward(ctypes.byref(cfg), float(nu), float(rho), n, _p(vol), _p(E), float(dt), _p(s_in),
+                                _p(out))
+    return out, st
+
+
+def diff_adjoint(cfg: Config, nu, rho, vol, E, dt, s_in, g_out):
+    s_in = _f64(s_in)
+    n = len(s_in)
+    vol = _f64(np.broadcast_to(vol, (n,)))
+    E = _f64(E)
+    g_out = _f64(g_out)
+    g_in = np.zeros_like(s_in)
+    gE = np.zeros(n)
+    st = lib().orc_diff_adjoint(ctypes.byref(cfg), float(nu), float(rho), n, _p(vol), _p(E), float(dt), _p(s_in),
+                                _p(g_out), _p(g_in), _p(gE))
+    return g_in, gE, st

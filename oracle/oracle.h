@@ -137,6 +137,15 @@ void orc_stable_sort(int64_t n, const uint32_t* keys, int32_t* perm);
  * code).  Returns the count; out may be NULL to count only. */
 int64_t orc_pblocks(int64_t n, const uint32_t* keys, int32_t L, int32_t* out);
 
+/* Differentiable elastic substep (fixed-corotated, per-particle E, common
+ * nu and rho).  State per particle: x[3] v[3] C[9] F[9] (24 doubles).
+ * orc_diff_adjoint maps the adjoint of the output state to the adjoint of
+ * the input state (written to g_in) and adds dL/dE into gE. */
+int orc_diff_forward(const orc_config* cfg, double nu, double rho, int64_t n, const double* vol, const double* E,
+                     double dt, const double* s_in, double* s_out);
+int orc_diff_adjoint(const orc_config* cfg, double nu, double rho, int64_t n, const double* vol, const double* E,
+                     double dt, const double* s_in, const double* g_out, double* g_in, double* gE);
+
 #ifdef __cplusplus
 }
 #endif
