@@ -198,6 +198,29 @@ int64_t mpm_batch_num_particles(const mpm_batch* b, int scene);
 const char* mpm_batch_last_error(const mpm_batch* b);
 void mpm_batch_destroy(mpm_batch* b);
 
+/* ---- differentiable substep -------------------------------------------- */
+/* A differentiable form of the substep (not in the paper): fixed-corotated
+ * elasticity with a per-particle Young's modulus E_p, a common Poisson ratio
+ * and density, MLS-MPM transfers on a dense grid (res0 x res1 x res2 nodes,
+ * walls as in mpm_config).  State of one particle: 24 floats x[3] v[3] C[9]
+ * F[9], row-major; all arrays are device pointers with n rows.  The caller
+ * keeps the states (checkpointing is the caller's choice). */
+typedef struct mpm_diff mpm_diff; /* opaque */
+
+/* vol0: n device floats, or NULL for dx^3/8 each. */
+mpm_status mpm_diff_create(const mpm_config* cfg, float nu, float rho, int64_t n, const float* vol0,
+                           const mpm_allocator* allocator, void* cuda_stream, mpm_diff** out);
+/* s_out = one substep of s_in with moduli E (n floats); s_out must not alias s_in. */
+mpm_status mpm_diff_forward(mpm_diff* d, float dt, const float* E, const float* s_in, float* s_out);
+/* Hand-written adjoint of mpm_diff_forward at s_in: given g_out = dL/ds_out,
+ * writes g_in = dL/ds_in and adds dL/dE into gE (n floats).  Re-runs the
+ * forward P2G and grid update, then the reverse G2P, grid update and P2G. */
+mpm_status mpm_diff_adjoint(mpm_diff* d, float dt, const float* E, const float* s_in, const float* g_out,
+                            float* g_in, float* gE);
+/* Wait for the stream; MPM_EDOMAIN if a particle's stencil left the grid. */
+mpm_status mpm_diff_sync(mpm_diff* d);
+void mpm_diff_destroy(mpm_diff* d);
+
 /* ---- introspection (tests, benchmarks) ------------------------------- */
 
 typedef struct {

@@ -95,6 +95,11 @@ _PROTOS = {
     "mpm_batch_num_particles": (I64, [P, I]),
     "mpm_batch_last_error": (ctypes.c_char_p, [P]),
     "mpm_batch_destroy": (None, [P]),
+    "mpm_diff_create": (I, [P, F, F, I64, P, P, P, P]),
+    "mpm_diff_forward": (I, [P, F, P, P, P]),
+    "mpm_diff_adjoint": (I, [P, F, P, P, P, P, P]),
+    "mpm_diff_sync": (I, [P]),
+    "mpm_diff_destroy": (None, [P]),
     "mpm_debug_svd": (I, [P, P, P, P, I64]),
     "mpm_debug_stress": (I, [P, P, P, P, I64]),
     "mpm_debug_plasticity": (I, [P, P, P, I64]),

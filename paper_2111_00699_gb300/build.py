@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpm.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["sort.cu", "rebuild.cu", "substep.cu", "api.cu", "batch.cu"]
+SOURCES = ["sort.cu", "rebuild.cu", "substep.cu", "api.cu", "batch.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-use_fast_math", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]
