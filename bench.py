@@ -276,6 +276,41 @@ def bench_sand(substeps=1000):
             "unit": UNIT, "ms_per_substep": ms / substeps, "rebuilds": st["rebuilds"]}
 
 
+def bench_adjoint(steps=200, k=20):
+    """Differentiable rollout: 32,768-particle jelly cube (E = 1e4, nu = 0.2,
+    rho = 1), 64^3, dt = 1e-4, 200 substeps with checkpoints every 20; the
+    centre-of-mass loss and its gradients in v0 and E (forward + backward)."""
+    import torch
+    from paper_2111_00699_gb300 import diff, scenes
+    x, v = scenes.jelly_cube(5, n_side=32)
+    n = len(x)
+    vol = torch.full((n,), 0.008 / n, device="cuda")
+    sim = diff.DiffSim(64, 1 / 64, n, nu=0.2, rho=1.0, vol=vol)
+    xt = torch.from_numpy(x).cuda()
+
+    def once():
+        vt = torch.from_numpy(v).cuda().requires_grad_(True)
+        Et = torch.full((n,), 1e4, device="cuda", requires_grad=True)
+        out = diff.rollout(xt, vt, Et, sim, steps, k=k, dt=1e-4)
+        loss = diff.center_of_mass_loss(out, vol, (0.5, 0.3, 0.5))
+        loss.backward()
+        return loss
+
+    once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        once()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / reps
+    sim.close()
+    # forward substeps: steps (forward) + steps - steps/k (segment recomputation); adjoint substeps: steps
+    return {"workload": "jelly cube %d particles, 64^3, %d substeps, checkpoints every %d" % (n, steps, k),
+            "ms_per_gradient": el * 1e3, "gradients_per_s": 1.0 / el,
+            "particle_substeps_per_s_forward_plus_adjoint": n * steps / el, "unit": "gradient evaluations/s"}
+
+
 # ---------------------------------------------------------------- main arm
 
 def _variant_name(kind, v):
@@ -464,7 +499,8 @@ def main():
     workloads = None
     if not args.no_workloads and world == 1:
         workloads = {}
-        for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand)):
+        for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand),
+                         ("adjoint", bench_adjoint)):
             try:
                 workloads[name] = fn()
             except Exception as exc:   # report, do not lose the main line

@@ -203,8 +203,11 @@ void mpm_batch_destroy(mpm_batch* b);
  * elasticity with a per-particle Young's modulus E_p, a common Poisson ratio
  * and density, MLS-MPM transfers on a dense grid (res0 x res1 x res2 nodes,
  * walls as in mpm_config).  State of one particle: 24 floats x[3] v[3] C[9]
- * F[9], row-major; all arrays are device pointers with n rows.  The caller
- * keeps the states (checkpointing is the caller's choice). */
+ * H[9], row-major, where H = F - I is the displacement gradient (kept instead
+ * of F so that FP32 resolves small strains to full relative precision; the
+ * adjoint with respect to H equals the adjoint with respect to F).  All
+ * arrays are device pointers with n rows.  The caller keeps the states
+ * (checkpointing is the caller's choice). */
 typedef struct mpm_diff mpm_diff; /* opaque */
 
 /* vol0: n device floats, or NULL for dx^3/8 each. */

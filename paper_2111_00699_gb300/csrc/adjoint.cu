@@ -10,7 +10,8 @@
 // rollouts this serves are small (tens of thousands of particles on 64^3),
 // so mapping and sorting would only add state to differentiate through.
 //
-// State of one particle: 24 floats x[3] v[3] C[9] F[9] (row-major).  The
+// State of one particle: 24 floats x[3] v[3] C[9] H[9], with H = F - I the
+// displacement gradient (row-major).  The
 // adjoint of one substep runs the forward P2G and grid update again, then
 // the reverse of G2P (scatter of the velocity adjoint to the grid), of the
 // grid update, and of P2G (gather), by the chain rule.  The stress adjoint
@@ -72,27 +73,84 @@ __device__ __forceinline__ int64_t d_node(const DiffParams& dp, const DStencil& 
     return (int64_t)(s.b[0] + i) + (int64_t)dp.res[0] * ((int64_t)(s.b[1] + j) + (int64_t)dp.res[1] * (s.b[2] + k));
 }
 
-// Fixed-corotated tau for modulus E (rotation R and SVD returned for reuse).
-__device__ __forceinline__ void fc_tau(const DiffParams& dp, float E, const float* F, float* tau, float* U, float* s,
-                                       float* V, float* R)
+// Fixed-corotated stress from the displacement gradient H = F - I, keeping
+// full FP32 relative precision for small strains (F itself in FP32 resolves
+// a strain of 1e-4 to only ~6e-4 relative).  With E = F^T F - I = H + H^T +
+// H^T H = V diag(l) V^T (Jacobi on the small matrix E):
+//   sigma_i - 1 = l_i / (sqrt(1 + l_i) + 1),
+//   F - R = F (I - S^-1) = F V diag((sigma_i - 1) / sigma_i) V^T,
+//   J - 1 = tr H + ((tr H)^2 - tr(H^2)) / 2 + det H,
+//   tau = 2 mu (F - R) F^T + lambda J (J - 1) I,
+// and U = F V diag(1 / sigma) for the rotation adjoint.  (Polar form: for an
+// inverted F, det F < 0, R would be a reflection; the rollouts this serves
+// stay far from inversion.)
+struct FCDecomp {
+    float F[9], U[9], V[9], sg[3], FmR[9], J, Jm1;
+};
+
+__device__ __forceinline__ void fc_decomp(const float* H, FCDecomp& d)
 {
-    svd3(F, U, s, V);
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        d.F[e] = H[e] + ((e % 4 == 0) ? 1.0f : 0.0f);
+    // E = H + H^T + H^T H
+    float e00 = 2.f * H[0] + H[0] * H[0] + H[3] * H[3] + H[6] * H[6];
+    float e11 = 2.f * H[4] + H[1] * H[1] + H[4] * H[4] + H[7] * H[7];
+    float e22 = 2.f * H[8] + H[2] * H[2] + H[5] * H[5] + H[8] * H[8];
+    float e01 = H[1] + H[3] + H[0] * H[1] + H[3] * H[4] + H[6] * H[7];
+    float e02 = H[2] + H[6] + H[0] * H[2] + H[3] * H[5] + H[6] * H[8];
+    float e12 = H[5] + H[7] + H[1] * H[2] + H[4] * H[5] + H[7] * H[8];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        d.V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int sweep = 0; sweep < 5; ++sweep) {
+        jacobi_pair(e00, e11, e01, e02, e12, d.V, 0, 1);
+        jacobi_pair(e00, e22, e02, e01, e12, d.V, 0, 2);
+        jacobi_pair(e11, e22, e12, e01, e02, d.V, 1, 2);
+    }
+    if (e00 < e11) swap_neg_cols(d.V, e00, e11, 0, 1);
+    if (e00 < e22) swap_neg_cols(d.V, e00, e22, 0, 2);
+    if (e11 < e22) swap_neg_cols(d.V, e11, e22, 1, 2);
+    const float l[3] = {e00, e11, e22};
+    float q[3], inv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float s = sqrtf(fmaxf(1.0f + l[i], 1e-12f));
+        d.sg[i] = s;
+        float sm1 = l[i] / (s + 1.0f);
+        inv[i] = 1.0f / s;
+        q[i] = sm1 * inv[i];          // (sigma - 1) / sigma
+    }
+    float FV[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            FV[3 * r + c] = d.F[3 * r] * d.V[c] + d.F[3 * r + 1] * d.V[3 + c] + d.F[3 * r + 2] * d.V[6 + c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            d.U[3 * r + c] = FV[3 * r + c] * inv[c];
+            d.FmR[3 * r + c] = FV[3 * r] * q[0] * d.V[3 * c] + FV[3 * r + 1] * q[1] * d.V[3 * c + 1] +
+                               FV[3 * r + 2] * q[2] * d.V[3 * c + 2];
+        }
+    float trH = H[0] + H[4] + H[8];
+    float trHH = H[0] * H[0] + H[4] * H[4] + H[8] * H[8] + 2.f * (H[1] * H[3] + H[2] * H[6] + H[5] * H[7]);
+    d.Jm1 = trH + 0.5f * (trH * trH - trHH) + det3(H);
+    d.J = 1.0f + d.Jm1;
+}
+
+__device__ __forceinline__ void fc_tau(const DiffParams& dp, float E, const FCDecomp& d, float* tau)
+{
     float mu = E * dp.mu1, la = E * dp.la1;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            R[3 * i + j] = U[3 * i] * V[3 * j] + U[3 * i + 1] * V[3 * j + 1] + U[3 * i + 2] * V[3 * j + 2];
-    float J = det3(F);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                acc += (F[3 * i + k] - R[3 * i + k]) * F[3 * j + k];
-            tau[3 * i + j] = 2.0f * mu * acc + (i == j ? la * J * (J - 1.0f) : 0.0f);
+            float acc = d.FmR[3 * i] * d.F[3 * j] + d.FmR[3 * i + 1] * d.F[3 * j + 1] + d.FmR[3 * i + 2] * d.F[3 * j + 2];
+            tau[3 * i + j] = 2.0f * mu * acc + (i == j ? la * d.J * d.Jm1 : 0.0f);
         }
 }
 
@@ -108,8 +166,10 @@ __global__ void dk_p2g(DiffParams dp, int64_t n, const float* __restrict__ s, co
         atomicOr(err, ST_EDOMAIN);
         return;
     }
-    float tau[9], U[9], sg[3], V[9], R[9];
-    fc_tau(dp, E[p], q + 15, tau, U, sg, V, R);
+    FCDecomp dec;
+    fc_decomp(q + 15, dec);
+    float tau[9];
+    fc_tau(dp, E[p], dec, tau);
     float mp = dp.rho * vol[p];
     float k = 4.0f * dt * vol[p] * dp.inv_dx * dp.inv_dx;
     float A[9];
@@ -211,12 +271,14 @@ __global__ void dk_g2p(DiffParams dp, int64_t n, const float* __restrict__ s, co
 #pragma unroll
     for (int e = 0; e < 9; ++e)
         o[6 + e] = C[e];
-    const float* F = q + 15;
+    // F' = (I + dt C) F with F = I + H:  H' = H + dt (C + C H)
+    const float* H = q + 15;
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            o[15 + 3 * r + c] = F[3 * r + c] + dt * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
+            o[15 + 3 * r + c] = H[3 * r + c] + dt * (C[3 * r + c] + C[3 * r] * H[c] + C[3 * r + 1] * H[3 + c] +
+                                                      C[3 * r + 2] * H[6 + c]);
 }
 
 // ---- adjoint ------------------------------------------------------------------------
@@ -258,7 +320,10 @@ __global__ void dk_g2p_adj(DiffParams dp, int64_t n, const float* __restrict__ s
                     for (int b = 0; b < 3; ++b)
                         Cn[3 * a + b] += D * wt * gv[a] * d[b];
             }
-    const float* F = q + 15;
+    float F[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        F[e] = q[15 + e] + ((e % 4 == 0) ? 1.0f : 0.0f);
     const float* Fb1 = g1 + 15;
     // F' = (I + dt C') F
 #pragma unroll
@@ -364,19 +429,20 @@ __global__ void dk_grid_adj(DiffParams dp, int64_t nodes, float dt, const float4
     Pmbar[id] = out;
 }
 
-// Fbar += d tau / dF contracted with taubar (fixed-corotated, closed form).
-__device__ __forceinline__ void fc_tau_vjp(float mu, float la, const float* F, const float* U, const float* sg,
-                                           const float* V, const float* R, const float* tb, float* Fb)
+// Fbar += d tau / dF contracted with taubar (fixed-corotated, closed form):
+//   Fbar = 2 mu [taubar F + taubar^T (F - R) - U Z V^T] + lambda (2J - 1) tr(taubar) cof(F)
+// with Z_ij = (G_ij - G_ji) / (s_i + s_j), G = U^T (taubar F) V.
+__device__ __forceinline__ void fc_tau_vjp(float mu, float la, const FCDecomp& d, const float* tb, float* Fb)
 {
-    float M[9], G[9], Z[9], UZ[9];
-    // M = taubar F
+    const float* F = d.F;
+    const float* U = d.U;
+    const float* V = d.V;
+    float M[9], G[9], Z[9], UZ[9], MV[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             M[3 * i + j] = tb[3 * i] * F[j] + tb[3 * i + 1] * F[3 + j] + tb[3 * i + 2] * F[6 + j];
-    // G = U^T M V
-    float MV[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -391,28 +457,26 @@ __device__ __forceinline__ void fc_tau_vjp(float mu, float la, const float* F, c
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float den = sg[i] + sg[j];
+            float den = d.sg[i] + d.sg[j];
             den = fabsf(den) < 1e-6f ? copysignf(1e-6f, den) : den;
             Z[3 * i + j] = (i == j) ? 0.0f : (G[3 * i + j] - G[3 * j + i]) / den;
         }
-    // U Z V^T
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             UZ[3 * i + j] = U[3 * i] * Z[j] + U[3 * i + 1] * Z[3 + j] + U[3 * i + 2] * Z[6 + j];
-    float J = det3(F);
     float tr = tb[0] + tb[4] + tb[8];
     float cof[9] = {F[4] * F[8] - F[5] * F[7], F[5] * F[6] - F[3] * F[8], F[3] * F[7] - F[4] * F[6],
                     F[2] * F[7] - F[1] * F[8], F[0] * F[8] - F[2] * F[6], F[1] * F[6] - F[0] * F[7],
                     F[1] * F[5] - F[2] * F[4], F[2] * F[3] - F[0] * F[5], F[0] * F[4] - F[1] * F[3]};
-    float cj = la * (2.0f * J - 1.0f) * tr;
+    float cj = la * (2.0f * d.J - 1.0f) * tr;
+    const float* FmR = d.FmR;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            // taubar^T (F - R)
-            float t2 = tb[i] * (F[j] - R[j]) + tb[3 + i] * (F[3 + j] - R[3 + j]) + tb[6 + i] * (F[6 + j] - R[6 + j]);
+            float t2 = tb[i] * FmR[j] + tb[3 + i] * FmR[3 + j] + tb[6 + i] * FmR[6 + j];
             float ZV = UZ[3 * i] * V[3 * j] + UZ[3 * i + 1] * V[3 * j + 1] + UZ[3 * i + 2] * V[3 * j + 2];
             Fb[3 * i + j] += 2.0f * mu * (M[3 * i + j] + t2 - ZV) + cj * cof[3 * i + j];
         }
@@ -432,9 +496,11 @@ __global__ void dk_p2g_adj(DiffParams dp, int64_t n, const float* __restrict__ s
     if (!d_stencil(dp, q, S))
         return;
     const float h = dp.dx;
-    float tau[9], U[9], sg[3], V[9], R[9];
     const float Ep = E[p];
-    fc_tau(dp, Ep, q + 15, tau, U, sg, V, R);
+    FCDecomp dec;
+    fc_decomp(q + 15, dec);
+    float tau[9];
+    fc_tau(dp, Ep, dec, tau);
     float mp = dp.rho * vol[p];
     float k = 4.0f * dt * vol[p] * dp.inv_dx * dp.inv_dx;
     float A[9];
@@ -484,7 +550,7 @@ __global__ void dk_p2g_adj(DiffParams dp, int64_t n, const float* __restrict__ s
         gi[3 + a] += vb[a];
     }
     float Fb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    fc_tau_vjp(Ep * dp.mu1, Ep * dp.la1, q + 15, U, sg, V, R, tb, Fb);
+    fc_tau_vjp(Ep * dp.mu1, Ep * dp.la1, dec, tb, Fb);
 #pragma unroll
     for (int e = 0; e < 9; ++e)
         gi[15 + e] += Fb[e];

@@ -1,7 +1,8 @@
 """Differentiable rollouts of the elastic MLS-MPM substep.
 
 `DiffSim` wraps the C ABI's mpm_diff_* calls (forward and hand-written
-adjoint of one substep, device memory from PyTorch).  `rollout` is a
+adjoint of one substep, device memory from PyTorch).  A state row is x, v, C
+and H = F - I (the displacement gradient), 24 floats.  `rollout` is a
 torch.autograd.Function: its forward runs `steps` substeps keeping a
 checkpoint of the particle state every `k` substeps; its backward walks the
 segments in reverse, recomputes each segment's states from its checkpoint,
@@ -66,14 +67,11 @@ class DiffSim:
 
 
 def pack_state(x: torch.Tensor, v: torch.Tensor) -> torch.Tensor:
-    """(n, 24) state with C = 0 and F = I."""
+    """(n, 24) state x, v, C = 0, H = F - I = 0 (rest shape)."""
     n = x.shape[0]
     s = torch.zeros((n, 24), dtype=torch.float32, device=x.device)
     s[:, 0:3] = x
     s[:, 3:6] = v
-    s[:, 15] = 1.0
-    s[:, 19] = 1.0
-    s[:, 23] = 1.0
     return s
 
 

@@ -50,7 +50,8 @@ def test_diff_forward_matches_oracle(D):
     g = s.double().cpu().numpy()
     assert np.abs(g[:, 0:3] - so[:, 0:3]).max() <= 1e-4
     assert _rel(g[:, 3:6], so[:, 3:6]) <= 1e-4
-    assert np.abs(g[:, 15:] - so[:, 15:]).max() <= 1e-4
+    H_oracle = so[:, 15:] - np.eye(3).reshape(1, 9)        # the GPU state holds H = F - I
+    assert np.abs(g[:, 15:] - H_oracle).max() <= 1e-4
     sim.close()
 
 
@@ -62,7 +63,10 @@ def test_diff_adjoint_matches_oracle_adjoint(D):
     C = (2.0 * rng.normal(size=(n, 9))).astype(np.float32)
     F = (np.eye(3) + 0.05 * rng.normal(size=(n, 3, 3))).reshape(n, 9).astype(np.float32)
     s64 = orc.pack_state(x.astype(np.float64), v.astype(np.float64), C.astype(np.float64), F.astype(np.float64))
-    s32 = torch.from_numpy(s64.astype(np.float32)).cuda()
+    s_gpu = s64.copy()
+    s_gpu[:, 15:] -= np.eye(3).reshape(1, 9)                 # GPU state: H = F - I
+    s32 = torch.from_numpy(s_gpu.astype(np.float32)).cuda()
+    s64[:, 15:] = s32[:, 15:].double().cpu().numpy() + np.eye(3).reshape(1, 9)   # same rounded input for both
     g_out = rng.normal(size=s64.shape)
     vol = np.full(n, (1 / 64) ** 3 / 8)
     cfg = orc.config(64, 1 / 64, orc.STICKY)
