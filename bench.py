@@ -348,6 +348,8 @@ def main():
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8); -1 = autotune")
+    ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
+                    help="1: fused G2P2G transfer, 0: separate phases; default: the faster one")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -399,6 +401,17 @@ def main():
         warm -= 120
     else:
         sim.set_g2p_variant(args.g2p_variant)
+    # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene
+    fused_ms = {}
+    for on in (False, True, False, True):
+        sim.set_g2p2g(on)
+        sim.run(3, DT)
+        fused_ms.setdefault("g2p2g" if on else "separate", []).append(
+            _events_time(stream, lambda: sim.run(20, DT)) / 20)
+        warm -= 23
+    fused_ms = {k: min(v) for k, v in fused_ms.items()}
+    use_fused = args.g2p2g if args.g2p2g is not None else fused_ms["g2p2g"] < fused_ms["separate"]
+    sim.set_g2p2g(bool(use_fused))
     warm = max(3, warm)
     sim.run(warm, DT)
     sim.sync()
@@ -452,7 +465,11 @@ def main():
     hbm = hbm or 6800.0
     achieved = algo[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
     src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", "substep.cu"), "rb").read()).hexdigest()
-    kernel_name = {"p2g": KERNEL_NAMES["P2G"][tuned["best_name"]], "g2p": KERNEL_NAMES["G2P"][tuned_g["best_name"]],
+    if use_fused:
+        # per substep: grid update + k_g2p2g (reads x F Jp vol mat 57 B, writes x v C F Jp 100 B)
+        algo["g2p"] = 157 * n_now
+    kernel_name = {"p2g": KERNEL_NAMES["P2G"][tuned["best_name"]],
+                   "g2p": "k_g2p2g" if use_fused else KERNEL_NAMES["G2P"][tuned_g["best_name"]],
                    "grid": "k_grid"}[dom]
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_note,
@@ -465,6 +482,7 @@ def main():
     e2e = None
     if args.e2e_frames > 0:
         sim = fresh_sim(tuned["best"], tuned_g["best"])
+        sim.set_g2p2g(bool(use_fused))
         host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
                 for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
         sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
@@ -515,7 +533,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_frame": ms_per_step * SUBSTEPS_PER_FRAME,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
-            "clocks": clk.summary(), "p2g_variant": tuned, "g2p_variant": tuned_g, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
+            "clocks": clk.summary(), "p2g_variant": tuned, "g2p_variant": tuned_g,
+            "transfer": {"mode": "g2p2g" if use_fused else "separate", "ms_per_substep": fused_ms}, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu, "workloads": workloads}
     print(json.dumps(line))
     if world > 1:

@@ -82,7 +82,9 @@ typedef struct {
     int32_t wall;          /* wall layer thickness in nodes (3 is usual) */
     float gravity[3];
     int64_t max_particles; /* 0: grow without bound (4x when half full) */
-    int32_t use_g2p2g;     /* reserved: fused G2P2G transfer; 0 = separate phases */
+    int32_t use_g2p2g;     /* 1: fused G2P2G transfer (Sec. 4.1) -- per substep the grid
+                              update and one kernel doing G2P and the next P2G;
+                              0: separate P2G, grid update, G2P */
     int32_t p2g_variant;   /* tuning: 0 direct float4 atomics, 1 cell-strided lanes,
                               2 shared-memory node tile per CTA, 3/4 register
                               accumulation over runs of 4/8 particles (see the autotuner) */
@@ -260,6 +262,9 @@ mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
 mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant);
 /* Same for the G2P gather variant (mpm_config.g2p_variant). */
 mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
+/* Switch between separate phases (0) and the fused G2P2G transfer (1)
+ * between substeps (mpm_config.use_g2p2g). */
+mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on);
 
 /* Per-phase timing with CUDA events on the context's stream.  Phase ids:
  * 0 rebuild, 1 P2G, 2 grid update, 3 G2P.  mpm_profile_read syncs and

@@ -80,6 +80,7 @@ _PROTOS = {
     "mpm_debug_p2g": (I, [P, F, P, I]),
     "mpm_set_p2g_variant": (I, [P, I]),
     "mpm_set_g2p_variant": (I, [P, I]),
+    "mpm_set_g2p2g": (I, [P, I]),
     "mpm_profile_enable": (I, [P, I]),
     "mpm_profile_read": (I, [P, P, P, I]),
     "mpm_radix_sort_pairs": (I, [P, P, P, P, I64, I, P, P, P]),

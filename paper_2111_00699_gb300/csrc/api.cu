@@ -87,6 +87,10 @@ struct mpm_ctx {
     cudaEvent_t ev[kRing] = {};
     int64_t step = 0, last_rebuild = -1;
     bool need_rebuild = true;
+    // fused G2P2G mode: grid[gcur] holds the momentum of the current state
+    // (primed); the stress channels are stale after fused substeps
+    bool primed = false;
+    bool tau_valid = true;
 
     int64_t rebuilds = 0, launches = 0;
     std::string err;
@@ -360,6 +364,7 @@ mpm_status rebuild(mpm_ctx* ctx)
         CK(cudaMemsetAsync(ctx->grid[1], 0, (size_t)npb * 1024, s));
     }
     ctx->gcur = 0;
+    ctx->primed = false;
     ctx->keys_valid = true;
     ctx->need_rebuild = false;
     ctx->last_rebuild = ctx->step;
@@ -400,8 +405,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
             return MPM_EINVAL;
         maxres = cfg->res[a] > maxres ? cfg->res[a] : maxres;
     }
-    if (cfg->use_g2p2g != 0)
-        return MPM_ENOTSUP;
+    if (cfg->use_g2p2g != 0 && cfg->use_g2p2g != 1)
+        return MPM_EINVAL;
     if (cfg->p2g_variant < 0 || cfg->p2g_variant >= kP2GVariants)
         return MPM_EINVAL;
     if (cfg->g2p_variant < 0 || cfg->g2p_variant >= kG2PVariants)
@@ -566,6 +571,7 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
     CK(cudaGetLastError());
     ctx->n += n;
     ctx->need_rebuild = true;
+    ctx->primed = false;
     ctx->keys_valid = false;
     return MPM_OK;
 }
@@ -592,6 +598,47 @@ static bool host_stencil_mapped(const mpm_ctx* ctx, const float* x, int margin)
                 if (ctx->htable[morton3((uint32_t)xx, (uint32_t)y, (uint32_t)z)] < 0)
                     return false;
     return true;
+}
+
+// Fused G2P2G substep (Sec. 4.1): grid update of the primed momentum, then
+// one kernel doing this substep's G2P and the next substep's P2G.  Priming
+// (after a rebuild, a state write or an emission) is one plain P2G.
+static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
+{
+    cudaStream_t s = ctx->stream;
+    const PartView& pv = ctx->pv[ctx->cur];
+    if (!ctx->primed) {
+        if (!ctx->tau_valid) {
+            launch_prepare_stress(ctx->sp, pv, ctx->n, s);
+            ctx->launches += 1;
+            ctx->tau_valid = true;
+        }
+        if (ctx->n_pblocks > 0)
+            CK(cudaMemsetAsync(ctx->grid[ctx->gcur], 0, (size_t)ctx->n_pblocks * 1024, s));
+        cudaEvent_t e0 = nullptr;
+        prof_begin(ctx, e0);
+        launch_p2g(ctx->sp, pv, grid_view(ctx), ctx->n, dt, ctx->dstat, ctx->cfg.p2g_variant, s);
+        prof_end(ctx, 1, e0);
+        ctx->launches += 1;
+        ctx->primed = true;
+    }
+    CK(cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s));
+    GridView gv = grid_view(ctx);
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    prof_begin(ctx, e1);
+    launch_grid_update(ctx->sp, gv, dt, s);
+    prof_end(ctx, 2, e1);
+    prof_begin(ctx, e2);
+    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, s);
+    prof_end(ctx, 3, e2);
+    ctx->launches += 2;
+    CK(cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev[slot], s));
+    CK(cudaGetLastError());
+    ctx->gcur = 1 - ctx->gcur;   // grid[gcur] now holds the momentum of the new state
+    ctx->step += 1;
+    ctx->tau_valid = false;
+    return MPM_OK;
 }
 
 mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v, const float* vol0,
@@ -654,6 +701,7 @@ mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const flo
     ctx->n += n;
     ctx->emitted += n;
     ctx->keys_valid = false;
+    ctx->primed = false;   // the new particles are not in the fused path's momentum
     if (!mapped)
         ctx->need_rebuild = true;
     return MPM_OK;
@@ -683,6 +731,8 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     }
     cudaStream_t s = ctx->stream;
     int slot = (int)(ctx->step % kRing);
+    if (ctx->cfg.use_g2p2g)
+        return substep_fused(ctx, dt, slot);
     CK(cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s));
     GridView gv = grid_view(ctx);
     const PartView& pv = ctx->pv[ctx->cur];
@@ -702,6 +752,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     CK(cudaGetLastError());
     ctx->gcur = 1 - ctx->gcur;
     ctx->step += 1;
+    ctx->tau_valid = true;
     return MPM_OK;
 }
 
@@ -773,10 +824,12 @@ mpm_status mpm_write_state(mpm_ctx* ctx, const float* x, const float* v, const f
         }
         ctx->launches += 1;
     }
-    if (F || Jp) {
+    if (F || Jp || !ctx->tau_valid) {
         launch_prepare_stress(ctx->sp, ctx->pv[ctx->cur], n, ctx->stream);
         ctx->launches += 1;
+        ctx->tau_valid = true;
     }
+    ctx->primed = false;
     if (x) {
         ctx->need_rebuild = true;
         ctx->keys_valid = false;
@@ -851,6 +904,15 @@ mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
         dense = (float*)ctx->stage;
     }
     CK(cudaMemsetAsync(dense, 0, bytes, s));
+    if (!ctx->tau_valid) {
+        launch_prepare_stress(ctx->sp, ctx->pv[ctx->cur], ctx->n, s);
+        ctx->launches += 1;
+        ctx->tau_valid = true;
+    }
+    if (ctx->primed && ctx->n_pblocks > 0) {   // fused mode keeps momentum there; rebuild it later
+        CK(cudaMemsetAsync(ctx->grid[ctx->gcur], 0, (size_t)ctx->n_pblocks * 1024, s));
+        ctx->primed = false;
+    }
     GridView gv = grid_view(ctx);
     launch_p2g(ctx->sp, ctx->pv[ctx->cur], gv, ctx->n, dt, ctx->dstat, ctx->cfg.p2g_variant, s);
     launch_grid_to_dense(ctx->sp, gv.cur, ctx->pslot, ctx->n_pblocks, dense, s);
@@ -868,6 +930,25 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant)
     if (!ctx || variant < 0 || variant >= kP2GVariants)
         return MPM_EINVAL;
     ctx->cfg.p2g_variant = variant;
+    return MPM_OK;
+}
+
+mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on)
+{
+    if (!ctx || (on != 0 && on != 1))
+        return MPM_EINVAL;
+    if (ctx->cfg.use_g2p2g && !on && ctx->primed) {
+        // back to separate phases: the next P2G needs a zero grid and the stress
+        if (ctx->n_pblocks > 0)
+            CK(cudaMemsetAsync(ctx->grid[ctx->gcur], 0, (size_t)ctx->n_pblocks * 1024, ctx->stream));
+        ctx->primed = false;
+    }
+    if (!on && !ctx->tau_valid) {
+        launch_prepare_stress(ctx->sp, ctx->pv[ctx->cur], ctx->n, ctx->stream);
+        ctx->launches += 1;
+        ctx->tau_valid = true;
+    }
+    ctx->cfg.use_g2p2g = on;
     return MPM_OK;
 }
 

@@ -110,6 +110,8 @@ void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t
 void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                 uint32_t* err, int variant, cudaStream_t s);
 void launch_prepare_stress(const SimParams& sp, const PartView& pv, int64_t n, cudaStream_t s);
+void launch_g2p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
+                  uint32_t* flags, uint32_t* err, cudaStream_t s);
 void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s);
 void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                 uint32_t* flags, uint32_t* err, int variant, cudaStream_t s);

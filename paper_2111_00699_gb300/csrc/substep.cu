@@ -120,8 +120,9 @@ __device__ __forceinline__ float4 node_contribution(const P2GParticle& q, int i,
     return val;
 }
 
-// 27 float4 global atomics (native vector reductions on sm_90+).
-__device__ __forceinline__ void scatter_global(const GridView& gv, const P2GParticle& q, uint32_t* err)
+// 27 float4 global atomics (native vector reductions on sm_90+) into `target`
+// (a grid buffer with the mapping of gv).
+__device__ __forceinline__ void scatter_to(const GridView& gv, float4* target, const P2GParticle& q, uint32_t* err)
 {
     int pb[8];
     if (!stencil_blocks(gv, q.b, pb)) {
@@ -139,10 +140,15 @@ __device__ __forceinline__ void scatter_global(const GridView& gv, const P2GPart
                 int nx = (q.b[0] & 3) + i;
                 int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
                 int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
-                atomicAdd(&gv.cur[(int64_t)blk * 64 + local], node_contribution(q, i, j, k));
+                atomicAdd(&target[(int64_t)blk * 64 + local], node_contribution(q, i, j, k));
             }
         }
     }
+}
+
+__device__ __forceinline__ void scatter_global(const GridView& gv, const P2GParticle& q, uint32_t* err)
+{
+    scatter_to(gv, gv.cur, q, err);
 }
 
 constexpr int kTileThreads = 256;       // particles per CTA in the strided / tile variants
@@ -492,9 +498,15 @@ __device__ __forceinline__ void g2p_accumulate(const float* f, const float (*w)[
 // Everything after the gather: C, x, v, the F update with the return map and
 // the stress for the next P2G (or the fluid J update), and the free-zone test
 // of Sec. 4.2.1.
-__device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
-                                           const float* x, const int* b, const float* vp, const float* Bm, float dt,
-                                           uint32_t* __restrict__ flags, uint32_t* __restrict__ err)
+// The particle after G2P, as the fused G2P2G kernel scatters it.
+struct G2POut {
+    float xn[3], vp[3], C[9], t6[6];
+};
+
+template <bool kFused>
+__device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
+                                             const float* x, const int* b, const float* vp, const float* Bm, float dt,
+                                             uint32_t* __restrict__ flags, uint32_t* __restrict__ err, G2POut* out)
 {
     // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
     float C[9];
@@ -537,13 +549,30 @@ __device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& 
         if (m.kind == MPM_SNOW)
             pv.ch(CH_JP)[p] = Jn;
     }
+    if (kFused) {
+        // the fused kernel scatters the new state at once: tau is not stored
 #pragma unroll
-    for (int e = 0; e < 6; ++e)
-        pv.ch(CH_TAU + e)[p] = t6[e];
+        for (int a = 0; a < 3; ++a) {
+            out->xn[a] = xn[a];
+            out->vp[a] = vp[a];
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            out->C[e] = C[e];
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+            out->t6[e] = t6[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+            pv.ch(CH_TAU + e)[p] = t6[e];
+    }
     // Free-zone test (Sec. 4.2.1): while every particle's stencil stays in
     // mapped blocks no rebuild is needed.  A particle that changed cell
-    // checks the stencil one cell wider on each side (one more substep of
-    // travel); failing that asks for a rebuild before the substep after next.
+    // checks the stencil widened by kM cells per side; failing that asks for
+    // a rebuild before the substep after next.  kM = 1 when the next P2G is
+    // a separate launch (one substep of travel before it); kM = 2 for the
+    // fused G2P2G, whose scatter already happens at the new position.
     int bn[3];
     bool moved = false, bad = false;
 #pragma unroll
@@ -554,23 +583,32 @@ __device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& 
     }
     if (bad) {
         atomicOr(err, ST_ENONFINITE);
-        return;
+        return false;
     }
     if (moved) {
+        constexpr int kM = kFused ? 2 : 1;
         bool dom = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             dom = dom && bn[a] >= 0 && bn[a] + 2 < sp.res[a] && ((bn[a] + 2) >> 2) < (1 << sp.L);
         if (!dom) {
             atomicOr(err, ST_EDOMAIN);
-            return;
+            return false;
         }
-        int lo[3] = {bn[0] - 1, bn[1] - 1, bn[2] - 1}, hi[3] = {bn[0] + 3, bn[1] + 3, bn[2] + 3};
+        int lo[3] = {bn[0] - kM, bn[1] - kM, bn[2] - kM}, hi[3] = {bn[0] + 2 + kM, bn[1] + 2 + kM, bn[2] + 2 + kM};
         if (!range_mapped(sp, gv, lo, hi)) {
             int lo2[3] = {bn[0], bn[1], bn[2]}, hi2[3] = {bn[0] + 2, bn[1] + 2, bn[2] + 2};
             atomicOr(flags, range_mapped(sp, gv, lo2, hi2) ? ST_REBUILD_SOFT : (ST_REBUILD_SOFT | ST_REBUILD_HARD));
         }
     }
+    return true;
+}
+
+__device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
+                                           const float* x, const int* b, const float* vp, const float* Bm, float dt,
+                                           uint32_t* __restrict__ flags, uint32_t* __restrict__ err)
+{
+    g2p_finish_t<false>(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err, nullptr);
 }
 
 __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView pv, GridView gv, int64_t n,
@@ -652,6 +690,65 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p_chunk(SimParams sp, Pa
         g2p_accumulate(f, w, [&](int i, int j, int k) { return cache[i + 3 * j + 9 * k]; }, vp, Bm);
         g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
     }
+}
+
+// Fused G2P2G (Sec. 4.1: G2P of substep n and P2G of substep n + 1 in one
+// kernel, the paper's choice below ~100K particles without particle
+// addition): gather from gv.cur at x_n, update the particle (one SVD for the
+// return map and the stress), write x, v, C, F, Jp, and scatter the new
+// particle's momentum into gv.nxt at x_{n+1}.  gv.nxt must be zero (the grid
+// update of this substep cleared it).
+__global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                            float dt, uint32_t* __restrict__ flags,
+                                                            uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float x[3], f[3], w[3][3];
+    int b[3];
+    if (!g2p_weights(sp, pv, p, x, b, f, w, err))
+        return;
+    int pb[8];
+    if (!stencil_blocks(gv, b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+    const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
+    float vp[3], Bm[9];
+    g2p_accumulate(f, w, [&](int i, int j, int k) {
+        int nx = bx + i, ny = by + j, nz = bz + k;
+        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+        return make_float3(g.x, g.y, g.z);
+    }, vp, Bm);
+    G2POut o;
+    if (!g2p_finish_t<true>(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err, &o))
+        return;
+    // P2G of the new state (same arithmetic as load_p2g_particle)
+    P2GParticle q;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        q.b[a] = base_of(o.xn[a], sp.inv_dx);
+        q.f[a] = __fmul_rn(o.xn[a], sp.inv_dx) - (float)q.b[a];
+        bspline(q.f[a], q.w[a]);
+    }
+    if (!in_grid(sp, q.b, o.xn)) {
+        atomicOr(err, ST_EDOMAIN);
+        return;
+    }
+    const float rho = sp.mat[pv.mat[p]].rho;
+    float vol = pv.ch(CH_VOL)[p];
+    q.mp = rho * vol;
+    float kst = 4.0f * dt * vol * sp.inv_dx * sp.inv_dx;
+    const float tm[9] = {o.t6[0], o.t6[3], o.t6[4], o.t6[3], o.t6[1], o.t6[5], o.t6[4], o.t6[5], o.t6[2]};
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+        q.A[e] = (q.mp * o.C[e] - kst * tm[e]) * sp.dx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        q.mv[a] = q.mp * o.vp[a];
+    scatter_to(gv, gv.nxt, q, err);
 }
 
 __global__ void k_debug_svd(const float* __restrict__ F, float* U, float* sig, float* V, int64_t n)
@@ -793,4 +890,14 @@ void launch_debug_plasticity(const MatParams& mp, float* F, float* Jp, int64_t n
         k_debug_plasticity<<<blocks_for(n, 128), 128, 0, s>>>(mp, F, Jp, n);
 }
 
+}  // namespace mpm
+
+namespace mpm {
+void launch_g2p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* flags,
+                  uint32_t* err, cudaStream_t s)
+{
+    if (n > 0)
+        k_g2p2g<<<(unsigned)((n + kTransferThreads - 1) / kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                                     flags, err);
+}
 }  // namespace mpm

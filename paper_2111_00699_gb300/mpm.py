@@ -49,7 +49,7 @@ class Simulator:
 
     def __init__(self, res, dx, materials, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0),
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
-                 device=None, p2g_variant: int = 4, g2p_variant: int = 2):
+                 device=None, p2g_variant: int = 3, g2p_variant: int = 0, g2p2g: bool = False):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -66,7 +66,7 @@ class Simulator:
         cfg.wall = int(wall)
         cfg.gravity = (ctypes.c_float * 3)(*gravity)
         cfg.max_particles = int(max_particles)
-        cfg.use_g2p2g = 0
+        cfg.use_g2p2g = 1 if g2p2g else 0
         cfg.p2g_variant = int(p2g_variant)
         cfg.g2p_variant = int(g2p_variant)
         mats = (_lib.Material * len(self.materials))(*self.materials)
@@ -217,6 +217,9 @@ class Simulator:
 
     def set_p2g_variant(self, variant: int):
         _check(load().mpm_set_p2g_variant(self._ctx, int(variant)), self._ctx)
+
+    def set_g2p2g(self, on: bool):
+        _check(load().mpm_set_g2p2g(self._ctx, 1 if on else 0), self._ctx)
 
     def set_g2p_variant(self, variant: int):
         _check(load().mpm_set_g2p_variant(self._ctx, int(variant)), self._ctx)

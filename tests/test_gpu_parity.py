@@ -498,3 +498,74 @@ def test_sand_blocks_full_size_parity(M):
     assert linf(g["x"], s.x) <= 1e-4
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
     assert linf(g["F"], s.F) <= 1e-4
+
+
+# ------------------------------------------------------------ fused G2P2G (a6')
+
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+def test_g2p2g_matches_oracle(M, kind):
+    """The fused transfer computes the same substeps as the separate phases."""
+    kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
+              snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0),
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0))[kind]
+    k = kw.pop("kind")
+    gm, om = mats_pair(M, k, **kw)
+    dt = 5e-5 if k == M.SNOW else 1e-4
+    x, _ = scenes.blocks(19, 15000, 64, 2)
+    vol = (1 / 64) ** 3 / 8
+    rng = np.random.default_rng(8)
+    v = (0.3 * rng.normal(size=(len(x), 3))).astype(np.float32)
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=True) as sim:
+        sim.add_particles(x, v=v)
+        s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+        g = _run_both(M, sim, [om], s, 10, dt, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+    assert linf(g["C"], s.C) <= 1e-4 * np.abs(s.C).max()
+    assert linf(g["Jp"], s.Jp) <= 1e-4
+
+
+def test_g2p2g_rebuilds_switches_and_reads(M):
+    """Fused mode with a fast block (rebuilds through the two-cell margin),
+    switching to separate phases and back mid-run, and reading the state in
+    between: every segment matches the oracle."""
+    x = scenes.cube_uniform(4, 3000, 0.3, 0.4)
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    v = np.tile(np.array([30.0, 20.0, 10.0], np.float32), (len(x), 1))
+    vol = (1 / 64) ** 3 / 8
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=True) as sim:
+        sim.add_particles(x, v=v)
+        for fused, steps in ((True, 25), (False, 10), (True, 25)):
+            sim.set_g2p2g(fused)
+            g = _run_both(M, sim, [om], s, steps, 1e-4, cfg)
+            assert linf(g["x"], s.x) <= 1e-4
+            assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        stats = sim.stats()
+    assert stats["rebuilds"] >= 3, stats
+
+
+def test_g2p2g_with_emission(M):
+    """Emission between substeps in fused mode re-primes the momentum."""
+    res, dt, steps = 128, 1e-4, 60
+    vol = (1 / res) ** 3 / 8
+    gm, om = mats_pair(M, M.FLUID, E=1e4, gamma=7.0, rho=1000.0)
+    cfg = orc.config(res, 1 / res, orc.SLIP)
+    s = None
+    with M.Simulator(res, 1 / res, [gm], boundary=M.SLIP, g2p2g=True) as sim:
+        for k in range(steps):
+            xe, ve = scenes.fountain_batch(2, k, dt, vol)
+            sim.emit_particles(xe, v=ve)
+            add = orc.State(xe.astype(np.float64), ve.astype(np.float64), vol=vol)
+            s = add if s is None else orc.State(np.concatenate([s.x, add.x]), np.concatenate([s.v, add.v]),
+                                                np.concatenate([s.C, add.C]), np.concatenate([s.F, add.F]),
+                                                np.concatenate([s.Jp, add.Jp]), np.concatenate([s.vol, add.vol]),
+                                                np.concatenate([s.mat, add.mat]))
+            sim.substep(dt)
+            assert orc.substep(cfg, om, s, dt) == 0
+        g = {k: v.double().cpu().numpy() for k, v in sim.read_state().items()}
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
