@@ -321,7 +321,8 @@ def _variant_name(kind, v):
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
                         "chunk4": "k_p2g_chunk<4>", "chunk8": "k_p2g_chunk<8>"},
-                "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>"}}
+                "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
+                        "occ": "k_g2p_occ"}}
 
 
 def _traffic_for(kernel, src_hash):
@@ -347,7 +348,7 @@ def main():
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
-                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8); -1 = autotune")
+                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ); -1 = autotune")
     ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
                     help="1: fused G2P2G transfer, 0: separate phases; default: the faster one")
     args = ap.parse_args()

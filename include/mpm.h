@@ -89,7 +89,9 @@ typedef struct {
                               2 shared-memory node tile per CTA, 3/4 register
                               accumulation over runs of 4/8 particles (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
-                              registers over runs of 4/8 particles */
+                              registers over runs of 4/8 particles, 3 grid tile staged
+                              in shared memory per CTA, 4 thread per particle at 64
+                              registers */
     int32_t reserved[5];
 } mpm_config;
 

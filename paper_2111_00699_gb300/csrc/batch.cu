@@ -461,30 +461,32 @@ __global__ void __launch_bounds__(kT) bk_g2p(BatchView bv, PartView pv, int64_t 
         pv.ch(CH_V + a)[p] = vp[a];
     }
     const MatParams m = bv.mats[pv.mat[p]];
-    float Jp = pv.ch(CH_JP)[p];
+    float jm1 = pv.ch(CH_JP)[p];   // Jp - 1 (snow) or J - 1 (fluid)
     float t6[6];
     if (m.kind == MPM_FLUID) {
-        Jp *= 1.0f + dt * (C[0] + C[4] + C[8]);
-        pv.ch(CH_JP)[p] = Jp;
-        float Fd[9];
-        constitutive_update(m, Fd, Jp, t6);
+        jm1 += dt * (C[0] + C[4] + C[8]) * (1.0f + jm1);
+        pv.ch(CH_JP)[p] = jm1;
+        float Hd[9];
+        constitutive_update(m, Hd, jm1, t6);
     } else {
-        float F[9], Fn[9];
+        // H = F - I: F <- (I + dt C) F is H <- H + dt (C + C H)
+        float H[9], Hn[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e)
-            F[e] = pv.ch(CH_F + e)[p];
+            H[e] = pv.ch(CH_F + e)[p];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                Fn[3 * r + c] = F[3 * r + c] + dt * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
-        float Jn = Jp;
-        constitutive_update(m, Fn, Jn, t6);
+                Hn[3 * r + c] = H[3 * r + c] + dt * (C[3 * r + c] + C[3 * r] * H[c] + C[3 * r + 1] * H[3 + c] +
+                                                     C[3 * r + 2] * H[6 + c]);
+        float jn = jm1;
+        constitutive_update(m, Hn, jn, t6);
 #pragma unroll
         for (int e = 0; e < 9; ++e)
-            pv.ch(CH_F + e)[p] = Fn[e];
+            pv.ch(CH_F + e)[p] = Hn[e];
         if (m.kind == MPM_SNOW)
-            pv.ch(CH_JP)[p] = Jn;
+            pv.ch(CH_JP)[p] = jn;
     }
 #pragma unroll
     for (int e = 0; e < 6; ++e)
@@ -1019,6 +1021,7 @@ mpm_status mpm_batch_read_state(mpm_batch* b, int scene, float* x, float* v, flo
     float* outs[5] = {x, v, C, F, Jp};
     static const int first[5] = {CH_X, CH_V, CH_C, CH_F, CH_JP};
     static const int width[5] = {3, 3, 9, 9, 1};
+    static const int bias_step[5] = {0, 0, 0, 4, 1};   // F and Jp are held as F - I and Jp - 1
     // particles of a scene are stored contiguously; ids give insertion order
     std::vector<int32_t> id((size_t)m);
     const PartView& pv = b->pv[b->cur];
@@ -1030,8 +1033,9 @@ mpm_status mpm_batch_read_state(mpm_batch* b, int scene, float* x, float* v, flo
             continue;
         for (int e = 0; e < width[f]; ++e) {
             BCK(cudaMemcpy(ch.data(), pv.ch(first[f] + e) + sc.p_begin, (size_t)m * 4, cudaMemcpyDeviceToHost));
+            const float bias = (bias_step[f] && e % bias_step[f] == 0) ? 1.0f : 0.0f;
             for (int64_t j = 0; j < m; ++j)
-                outs[f][(int64_t)(id[(size_t)j] - sc.p_begin) * width[f] + e] = ch[(size_t)j];
+                outs[f][(int64_t)(id[(size_t)j] - sc.p_begin) * width[f] + e] = ch[(size_t)j] + bias;
         }
     }
     uint32_t errw = 0;

@@ -54,12 +54,10 @@ __device__ __forceinline__ void bspline(float f, float w[3])
     w[2] = 0.5f * c * c;
 }
 
-// ---- 3x3 SVD -----------------------------------------------------------------
-// Eigen-decomposition of the symmetric F^T F by cyclic Jacobi rotations
-// (V), then a Givens QR of F V, whose triangular factor is diagonal up to
-// rounding (U, sigma); the approach of McAdams et al. 2011, written with
-// exact Jacobi angles.  Result: F = U diag(sig) V^T, det U = det V = +1,
-// sig[0] >= sig[1] >= |sig[2]|, sig[2] < 0 for inverted F.
+// ---- 3x3 SVD helpers -------------------------------------------------------------
+// The SVD (svd_h below) diagonalises the symmetric F^T F - I by cyclic Jacobi
+// rotations with exact angles (V and the singular values), as in McAdams et
+// al. 2011, then orthonormalises the columns of F V (U).
 
 // 1/sqrt(x) to ~1 ulp: the fast-math rsqrt plus one Newton step.  The
 // orthogonality of a rotation (c^2 + s^2 = 1 with s = t c) depends only on
@@ -112,246 +110,319 @@ __device__ __forceinline__ void swap_neg_cols(float* V, float& la, float& lb, in
     }
 }
 
-__device__ __forceinline__ void givens_rows(float* B, float* U, int i, int j)
-{
-    float a = B[3 * i + i], b = B[3 * j + i];
-    if (!(fabsf(b) > 6e-8f * fabsf(a))) {
-        // b is zero to working precision: the rotation is the identity, or a
-        // half turn (exact sign flips of rows i, j) when the pivot is negative.
-        if (a < 0.0f) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                B[3 * i + k] = -B[3 * i + k];
-                B[3 * j + k] = -B[3 * j + k];
-                U[3 * k + i] = -U[3 * k + i];
-                U[3 * k + j] = -U[3 * k + j];
-            }
-        }
-        return;
-    }
-    float r2 = a * a + b * b;
-    float ir = rsqrt_nr(r2);
-    float c = a * ir, s = b * ir;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float bi = B[3 * i + k], bj = B[3 * j + k];
-        B[3 * i + k] = c * bi + s * bj;
-        B[3 * j + k] = -s * bi + c * bj;
-        float ui = U[3 * k + i], uj = U[3 * k + j];
-        U[3 * k + i] = c * ui + s * uj;
-        U[3 * k + j] = -s * ui + c * uj;
-    }
-}
-
-__device__ __forceinline__ void svd3(const float* F, float* U, float* sig, float* V)
-{
-    // S = F^T F
-    float s00 = F[0] * F[0] + F[3] * F[3] + F[6] * F[6];
-    float s01 = F[0] * F[1] + F[3] * F[4] + F[6] * F[7];
-    float s02 = F[0] * F[2] + F[3] * F[5] + F[6] * F[8];
-    float s11 = F[1] * F[1] + F[4] * F[4] + F[7] * F[7];
-    float s12 = F[1] * F[2] + F[4] * F[5] + F[7] * F[8];
-    float s22 = F[2] * F[2] + F[5] * F[5] + F[8] * F[8];
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-        V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
-#pragma unroll
-    for (int sweep = 0; sweep < 5; ++sweep) {
-        jacobi_pair(s00, s11, s01, s02, s12, V, 0, 1);
-        jacobi_pair(s00, s22, s02, s01, s12, V, 0, 2);
-        jacobi_pair(s11, s22, s12, s01, s02, V, 1, 2);
-    }
-    // order eigenvalues descending
-    if (s00 < s11) swap_neg_cols(V, s00, s11, 0, 1);
-    if (s00 < s22) swap_neg_cols(V, s00, s22, 0, 2);
-    if (s11 < s22) swap_neg_cols(V, s11, s22, 1, 2);
-    // B = F V, then B = U R by Givens rotations
-    float B[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            B[3 * r + c] = F[3 * r] * V[c] + F[3 * r + 1] * V[3 + c] + F[3 * r + 2] * V[6 + c];
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-        U[i] = (i % 4 == 0) ? 1.0f : 0.0f;
-    givens_rows(B, U, 0, 1);
-    givens_rows(B, U, 0, 2);
-    givens_rows(B, U, 1, 2);
-    sig[0] = B[0];
-    sig[1] = B[4];
-    sig[2] = B[8];
-}
-
 __device__ __forceinline__ float det3(const float* M)
 {
     return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
            M[2] * (M[3] * M[7] - M[4] * M[6]);
 }
 
-// out = U diag(d) W^T
-__device__ __forceinline__ void udwt(const float* U, const float* d, const float* W, float* out)
+// ---- constitutive models (Sec. 4.1: SVD, projection and stress merged) --------
+// The deformation gradient is held as H = F - I, the displacement gradient,
+// and the snow/fluid volume ratios as Jp - 1 and J - 1: near the rest shape
+// F is I plus a strain of 1e-3 or less, which an FP32 F resolves to ~1e-4
+// relative (an FP32 SVD of F then returns sigma - 1 with ~1e-7 absolute
+// error, i.e. 1e-4 relative stress error).  All quantities below that are
+// small near the rest shape are computed from small quantities only.
+
+// prod(1 + a_i) - 1, without forming the products near 1.
+__device__ __forceinline__ float prod_m1(const float* a)
 {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            out[3 * i + j] = U[3 * i] * d[0] * W[3 * j] + U[3 * i + 1] * d[1] * W[3 * j + 1] +
-                             U[3 * i + 2] * d[2] * W[3 * j + 2];
+    return a[0] + a[1] + a[2] + a[0] * a[1] + a[0] * a[2] + a[1] * a[2] + a[0] * a[1] * a[2];
 }
 
-// ---- constitutive models (Sec. 4.1: SVD, projection and stress merged) --------
-// Kirchhoff stress tau = P F^T.  Fixed-corotated, written through the SVD:
-// (F - R) F^T = U (Sigma - I) Sigma U^T, so tau = U diag(2 mu (s - 1) s) U^T
-// + lambda J (J - 1) I.  Sand: tau = U diag(2 mu eps + lambda tr eps) U^T with
-// eps = ln(max(s, 1e-4)).  Fluid: tau = -p J I, p = K (J^-gamma - 1).
-__device__ __forceinline__ void kirchhoff(const MatParams& m, const float* F, float Jp, float* tau)
+// det(I + H) - 1 = tr H + ((tr H)^2 - tr(H^2)) / 2 + det H.
+__device__ __forceinline__ float det_m1(const float* H)
 {
-    if (m.kind == MPM_FLUID) {
-        float J = Jp;
-        float p = m.K * (__powf(J, -m.gamma) - 1.0f);
+    float tr = H[0] + H[4] + H[8];
+    float trHH = H[0] * H[0] + H[4] * H[4] + H[8] * H[8] + 2.0f * (H[1] * H[3] + H[2] * H[6] + H[5] * H[7]);
+    return tr + 0.5f * (tr * tr - trHH) + det3(H);
+}
+
+// Rotation-variant SVD of F = I + H: F = U diag(s) V^T, det U = det V = +1,
+// s sorted descending with only s[2] possibly negative (inverted F), and
+// sm1 = s - 1 to full relative precision.  V and the s come from Jacobi
+// rotations of the small symmetric E = F^T F - I = H + H^T + H^T H, with
+// s_i - 1 = l_i / (sqrt(1 + l_i) + 1) for its eigenvalues l_i.
+struct SVDH {
+    float U[9], V[9], s[3], sm1[3];
+    float Jm1;      // det F - 1
+    bool inverted;  // det F < 0 (s[2] negated, U's last column flipped)
+};
+
+__device__ __forceinline__ void svd_h(const float* H, SVDH& d)
+{
+    float e00 = 2.f * H[0] + H[0] * H[0] + H[3] * H[3] + H[6] * H[6];
+    float e11 = 2.f * H[4] + H[1] * H[1] + H[4] * H[4] + H[7] * H[7];
+    float e22 = 2.f * H[8] + H[2] * H[2] + H[5] * H[5] + H[8] * H[8];
+    float e01 = H[1] + H[3] + H[0] * H[1] + H[3] * H[4] + H[6] * H[7];
+    float e02 = H[2] + H[6] + H[0] * H[2] + H[3] * H[5] + H[6] * H[8];
+    float e12 = H[5] + H[7] + H[1] * H[2] + H[4] * H[5] + H[7] * H[8];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            tau[i] = 0.0f;
-        tau[0] = tau[4] = tau[8] = -p * J;
+    for (int i = 0; i < 9; ++i)
+        d.V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int sweep = 0; sweep < 4; ++sweep) {
+        jacobi_pair(e00, e11, e01, e02, e12, d.V, 0, 1);
+        jacobi_pair(e00, e22, e02, e01, e12, d.V, 0, 2);
+        jacobi_pair(e11, e22, e12, e01, e02, d.V, 1, 2);
+    }
+    if (e00 < e11) swap_neg_cols(d.V, e00, e11, 0, 1);
+    if (e00 < e22) swap_neg_cols(d.V, e00, e22, 0, 2);
+    if (e11 < e22) swap_neg_cols(d.V, e11, e22, 1, 2);
+    const float l[3] = {e00, e11, e22};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float r = sqrtf(fmaxf(1.0f + l[i], 0.0f));
+        d.sm1[i] = l[i] / (r + 1.0f);
+        d.s[i] = 1.0f + d.sm1[i];
+    }
+    // U by Gram-Schmidt on the columns b_c = (I + H) v_c, closed by a cross
+    // product so that det U = +1 even when F is singular or inverted.
+    float b[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            b[3 * r + c] = d.V[3 * r + c] + H[3 * r] * d.V[c] + H[3 * r + 1] * d.V[3 + c] + H[3 * r + 2] * d.V[6 + c];
+    float n0 = b[0] * b[0] + b[3] * b[3] + b[6] * b[6];
+    float u0[3], u1[3];
+    if (n0 > 1e-30f) {
+        float in0 = rsqrt_nr(n0);
+        u0[0] = b[0] * in0; u0[1] = b[3] * in0; u0[2] = b[6] * in0;
+    } else {
+        u0[0] = 1.0f; u0[1] = 0.0f; u0[2] = 0.0f;
+    }
+    float pr = u0[0] * b[1] + u0[1] * b[4] + u0[2] * b[7];
+    float w[3] = {b[1] - pr * u0[0], b[4] - pr * u0[1], b[7] - pr * u0[2]};
+    float n1 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const float s1_qr = sqrtf(n1);
+    if (!(n1 > 1e-12f * n0 + 1e-30f)) {
+        // rank <= 1: any unit vector orthogonal to u0
+        // u0 x e_k for the axis k along which u0 is smallest
+        float ax = fabsf(u0[0]), ay = fabsf(u0[1]), az = fabsf(u0[2]);
+        if (ax <= ay && ax <= az) {
+            w[0] = 0.0f; w[1] = u0[2]; w[2] = -u0[1];
+        } else if (ay <= az) {
+            w[0] = -u0[2]; w[1] = 0.0f; w[2] = u0[0];
+        } else {
+            w[0] = u0[1]; w[1] = -u0[0]; w[2] = 0.0f;
+        }
+        n1 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    }
+    float in1 = rsqrt_nr(n1);
+    u1[0] = w[0] * in1; u1[1] = w[1] * in1; u1[2] = w[2] * in1;
+    d.U[0] = u0[0]; d.U[3] = u0[1]; d.U[6] = u0[2];
+    d.U[1] = u1[0]; d.U[4] = u1[1]; d.U[7] = u1[2];
+    d.U[2] = u0[1] * u1[2] - u0[2] * u1[1];
+    d.U[5] = u0[2] * u1[0] - u0[0] * u1[2];
+    d.U[8] = u0[0] * u1[1] - u0[1] * u1[0];
+    d.Jm1 = det_m1(H);
+    // A singular value far below 1 is ill-determined by the eigenvalue
+    // 1 + l = s^2 of F^T F; there the projections of F V on U (the diagonal
+    // of the QR factor of F V) give it to FP32 absolute accuracy instead.
+    if (l[1] < -0.75f) {
+        d.s[1] = s1_qr;
+        d.sm1[1] = d.s[1] - 1.0f;
+    }
+    if (l[2] < -0.75f) {
+        float b2[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            b2[r] = d.V[3 * r + 2] + H[3 * r] * d.V[2] + H[3 * r + 1] * d.V[5] + H[3 * r + 2] * d.V[8];
+        d.s[2] = d.U[2] * b2[0] + d.U[5] * b2[1] + d.U[8] * b2[2];   // signed: det U = det V = +1
+        d.sm1[2] = d.s[2] - 1.0f;
+        d.inverted = d.s[2] < 0.0f;
+    } else {
+        d.inverted = d.Jm1 < -1.0f;
+        if (d.inverted) {
+            d.s[2] = -d.s[2];
+            d.sm1[2] = d.s[2] - 1.0f;
+        }
+    }
+}
+
+// tau = U diag(dg) U^T + vol I, as (xx, yy, zz, xy, xz, yz).
+__device__ __forceinline__ void tau6(const float* U, const float* dg, float vol, float* t6)
+{
+    t6[0] = U[0] * U[0] * dg[0] + U[1] * U[1] * dg[1] + U[2] * U[2] * dg[2] + vol;
+    t6[1] = U[3] * U[3] * dg[0] + U[4] * U[4] * dg[1] + U[5] * U[5] * dg[2] + vol;
+    t6[2] = U[6] * U[6] * dg[0] + U[7] * U[7] * dg[1] + U[8] * U[8] * dg[2] + vol;
+    t6[3] = U[0] * U[3] * dg[0] + U[1] * U[4] * dg[1] + U[2] * U[5] * dg[2];
+    t6[4] = U[0] * U[6] * dg[0] + U[1] * U[7] * dg[1] + U[2] * U[8] * dg[2];
+    t6[5] = U[3] * U[6] * dg[0] + U[4] * U[7] * dg[1] + U[5] * U[8] * dg[2];
+}
+
+// H of F' = U diag(1 + t) V^T, written as U diag(t) V^T + (R - I) with
+// R - I = (H V - V diag(s - 1)) diag(1/s) V^T (the rotation of the polar
+// decomposition), so that H' keeps its precision near the rest shape.
+__device__ __forceinline__ void rebuild_h(const SVDH& d, const float* H, const float* t, float* Hout)
+{
+    if (d.inverted || d.s[2] < 0.25f) {
+        // far from the rest shape: F' - I directly
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Hout[3 * r + c] = d.U[3 * r] * (1.0f + t[0]) * d.V[3 * c] + d.U[3 * r + 1] * (1.0f + t[1]) * d.V[3 * c + 1] +
+                                  d.U[3 * r + 2] * (1.0f + t[2]) * d.V[3 * c + 2] - (r == c ? 1.0f : 0.0f);
         return;
     }
-    float U[9], s[3], V[9], d[3];
-    svd3(F, U, s, V);
+    float Wm[9];   // (H V - V diag(s - 1)) diag(1/s), so that R - I = Wm V^T
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float hv = H[3 * r] * d.V[k] + H[3 * r + 1] * d.V[3 + k] + H[3 * r + 2] * d.V[6 + k];
+            Wm[3 * r + k] = (hv - d.V[3 * r + k] * d.sm1[k]) / d.s[k];
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                acc += (d.U[3 * r + k] * t[k] + Wm[3 * r + k]) * d.V[3 * c + k];
+            Hout[3 * r + c] = acc;
+        }
+}
+
+// Fluid pressure term: tau = -p J I, p = K (J^-gamma - 1), from jm1 = J - 1.
+__device__ __forceinline__ void fluid_tau6(const MatParams& m, float jm1, float* t6)
+{
+    float Jg_m1 = expm1f(-m.gamma * log1pf(jm1));   // J^-gamma - 1
+    float pj = m.K * Jg_m1 * (1.0f + jm1);
+    t6[0] = t6[1] = t6[2] = -pj;
+    t6[3] = t6[4] = t6[5] = 0.0f;
+}
+
+// Hencky strain of a singular value (floored at 1e-4 for collapsed or
+// inverted directions).
+__device__ __forceinline__ float hencky(float s, float sm1)
+{
+    return s > 1e-4f ? log1pf(sm1) : logf(1e-4f);
+}
+
+// Kirchhoff stress of a stored state (no return map): used when the stress
+// channels must be rebuilt from (H, Jp - 1), e.g. after mpm_write_state.
+//   fixed-corotated: tau = U diag(2 mu (s - 1) s) U^T + lambda J (J - 1) I,
+//     mu, lambda scaled by exp(xi (1 - Jp)) for snow [Stomakhin 2013];
+//   sand: tau = U diag(2 mu e + lambda tr e) U^T, e = ln s [Klar 2016];
+//   fluid: tau = -p J I, p = K (J^-gamma - 1) [Tampubolon 2017].
+__device__ __forceinline__ void stress_h(const MatParams& m, const float* H, float jm1, float* t6)
+{
+    if (m.kind == MPM_FLUID) {
+        fluid_tau6(m, jm1, t6);
+        return;
+    }
+    SVDH d;
+    svd_h(H, d);
+    float dg[3];
     if (m.kind == MPM_SAND) {
-        float e0 = __logf(fmaxf(s[0], 1e-4f)), e1 = __logf(fmaxf(s[1], 1e-4f)), e2 = __logf(fmaxf(s[2], 1e-4f));
-        float tr = e0 + e1 + e2;
-        d[0] = 2.0f * m.mu * e0 + m.la * tr;
-        d[1] = 2.0f * m.mu * e1 + m.la * tr;
-        d[2] = 2.0f * m.mu * e2 + m.la * tr;
-        udwt(U, d, U, tau);
+        float e[3] = {hencky(d.s[0], d.sm1[0]), hencky(d.s[1], d.sm1[1]), hencky(d.s[2], d.sm1[2])};
+        float tr = e[0] + e[1] + e[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dg[k] = 2.0f * m.mu * e[k] + m.la * tr;
+        tau6(d.U, dg, 0.0f, t6);
         return;
     }
     float mu = m.mu, la = m.la;
     if (m.kind == MPM_SNOW) {
-        float h = __expf(m.xi * (1.0f - Jp));
+        float h = __expf(-m.xi * jm1);
         mu *= h;
         la *= h;
     }
-    float J = s[0] * s[1] * s[2];
-    d[0] = 2.0f * mu * (s[0] - 1.0f) * s[0];
-    d[1] = 2.0f * mu * (s[1] - 1.0f) * s[1];
-    d[2] = 2.0f * mu * (s[2] - 1.0f) * s[2];
-    udwt(U, d, U, tau);
-    float vol = la * J * (J - 1.0f);
-    tau[0] += vol;
-    tau[4] += vol;
-    tau[8] += vol;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        dg[k] = 2.0f * mu * d.sm1[k] * d.s[k];
+    tau6(d.U, dg, la * (1.0f + d.Jm1) * d.Jm1, t6);
 }
 
-// Return mapping on the trial F at the end of G2P: snow singular-value clamp
-// with the Jp update [Stomakhin 2013]; Drucker-Prager projection (cases I-III)
-// [Klar 2016].  Elastic and fluid: nothing to do here.
-__device__ __forceinline__ void plasticity(const MatParams& m, float* F, float& Jp)
-{
-    if (m.kind != MPM_SNOW && m.kind != MPM_SAND)
-        return;
-    float U[9], s[3], V[9], t[3];
-    svd3(F, U, s, V);
-    if (m.kind == MPM_SNOW) {
-        t[0] = fminf(fmaxf(s[0], m.lo), m.hi);
-        t[1] = fminf(fmaxf(s[1], m.lo), m.hi);
-        t[2] = fminf(fmaxf(s[2], m.lo), m.hi);
-        Jp *= (s[0] * s[1] * s[2]) / (t[0] * t[1] * t[2]);
-        udwt(U, t, V, F);
-        return;
-    }
-    float e0 = __logf(fmaxf(s[0], 1e-4f)), e1 = __logf(fmaxf(s[1], 1e-4f)), e2 = __logf(fmaxf(s[2], 1e-4f));
-    float tr = e0 + e1 + e2;
-    if (tr >= 0.0f) {
-        t[0] = t[1] = t[2] = 1.0f;
-        udwt(U, t, V, F);
-        return;
-    }
-    float third = tr * (1.0f / 3.0f);
-    float d0 = e0 - third, d1 = e1 - third, d2 = e2 - third;
-    float nd = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    float dg = nd + m.dp_coef * tr * m.alpha;
-    if (dg <= 0.0f)
-        return;
-    float k = dg / nd;
-    t[0] = __expf(e0 - k * d0);
-    t[1] = __expf(e1 - k * d1);
-    t[2] = __expf(e2 - k * d2);
-    udwt(U, t, V, F);
-}
-
-// End-of-G2P constitutive update with a single SVD (Sec. 4.1 merges "SVD,
+// End-of-G2P constitutive update with one SVD (Sec. 4.1 merges "SVD,
 // plasticity projection, stress computation"): the return map on the trial
-// F (snow clamp + Jp, Drucker-Prager projection), then the Kirchhoff stress
-// of the projected state, which the next P2G needs.  Output t6 = (xx, yy, zz,
-// xy, xz, yz) of the symmetric tau = U diag(d) U^T + vol I.
-__device__ __forceinline__ void constitutive_update(const MatParams& m, float* F, float& Jp, float* t6)
+// state H (snow singular-value clamp with the Jp update [Stomakhin 2013];
+// Drucker-Prager cases I-III [Klar 2016]), then the stress of the projected
+// state for the next P2G.  jm1 is Jp - 1 (snow) or J - 1 (fluid, already
+// advanced by the caller).
+__device__ __forceinline__ void constitutive_update(const MatParams& m, float* H, float& jm1, float* t6)
 {
     if (m.kind == MPM_FLUID) {
-        float p = m.K * (__powf(Jp, -m.gamma) - 1.0f);
-        t6[0] = t6[1] = t6[2] = -p * Jp;
-        t6[3] = t6[4] = t6[5] = 0.0f;
+        fluid_tau6(m, jm1, t6);
         return;
     }
-    float U[9], s[3], V[9], d[3];
-    float vol = 0.0f;
-    svd3(F, U, s, V);
+    SVDH d;
+    svd_h(H, d);
+    float dg[3];
     if (m.kind == MPM_SNOW) {
         float t[3];
-        t[0] = fminf(fmaxf(s[0], m.lo), m.hi);
-        t[1] = fminf(fmaxf(s[1], m.lo), m.hi);
-        t[2] = fminf(fmaxf(s[2], m.lo), m.hi);
-        Jp *= (s[0] * s[1] * s[2]) / (t[0] * t[1] * t[2]);
-        udwt(U, t, V, F);
-        float h = __expf(m.xi * (1.0f - Jp));
+        bool changed = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            t[k] = fminf(fmaxf(d.sm1[k], m.lo_m1), m.hi_m1);
+            changed = changed || t[k] != d.sm1[k];
+        }
+        if (changed) {
+            float P = prod_m1(d.sm1), Ph = prod_m1(t);
+            float r_m1 = (P - Ph) / (1.0f + Ph);           // det(F)/det(F_clamped) - 1
+            jm1 = jm1 * (1.0f + r_m1) + r_m1;              // Jp <- Jp det(F) / det(F_clamped)
+            float Hn[9];
+            rebuild_h(d, H, t, Hn);
+#pragma unroll
+            for (int e = 0; e < 9; ++e)
+                H[e] = Hn[e];
+        }
+        float h = __expf(-m.xi * jm1);
         float mu = m.mu * h, la = m.la * h;
-        float J = t[0] * t[1] * t[2];
+        float Jm1 = changed ? prod_m1(t) : d.Jm1;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            d[k] = 2.0f * mu * (t[k] - 1.0f) * t[k];
-        vol = la * J * (J - 1.0f);
-    } else if (m.kind == MPM_SAND) {
-        float e[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            e[k] = __logf(fmaxf(s[k], 1e-4f));
+            dg[k] = 2.0f * mu * t[k] * (1.0f + t[k]);
+        tau6(d.U, dg, la * (1.0f + Jm1) * Jm1, t6);
+        return;
+    }
+    if (m.kind == MPM_SAND) {
+        float e[3] = {hencky(d.s[0], d.sm1[0]), hencky(d.s[1], d.sm1[1]), hencky(d.s[2], d.sm1[2])};
         float tr = e[0] + e[1] + e[2];
         if (tr >= 0.0f) {
-            float one[3] = {1.0f, 1.0f, 1.0f};
-            udwt(U, one, V, F);
+            // case II: expansion, project to the cone tip (sigma = 1)
+            const float zero[3] = {0.0f, 0.0f, 0.0f};
+            float Hn[9];
+            rebuild_h(d, H, zero, Hn);
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                H[q] = Hn[q];
             e[0] = e[1] = e[2] = 0.0f;
         } else {
             float third = tr * (1.0f / 3.0f);
             float d0 = e[0] - third, d1 = e[1] - third, d2 = e[2] - third;
             float nd = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            float dg = nd + m.dp_coef * tr * m.alpha;
-            if (dg > 0.0f) {
-                float k = dg / nd;
+            float dgm = nd + m.dp_coef * tr * m.alpha;
+            if (dgm > 0.0f) {
+                // case III: radial return onto the cone surface
+                float k = dgm / nd;
                 e[0] -= k * d0;
                 e[1] -= k * d1;
                 e[2] -= k * d2;
-                float t[3] = {__expf(e[0]), __expf(e[1]), __expf(e[2])};
-                udwt(U, t, V, F);
+                float t[3] = {expm1f(e[0]), expm1f(e[1]), expm1f(e[2])};
+                float Hn[9];
+                rebuild_h(d, H, t, Hn);
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    H[q] = Hn[q];
             }
         }
         float tr2 = e[0] + e[1] + e[2];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            d[k] = 2.0f * m.mu * e[k] + m.la * tr2;
-    } else {
-        float J = s[0] * s[1] * s[2];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            d[k] = 2.0f * m.mu * (s[k] - 1.0f) * s[k];
-        vol = m.la * J * (J - 1.0f);
+            dg[k] = 2.0f * m.mu * e[k] + m.la * tr2;
+        tau6(d.U, dg, 0.0f, t6);
+        return;
     }
-    t6[0] = U[0] * U[0] * d[0] + U[1] * U[1] * d[1] + U[2] * U[2] * d[2] + vol;
-    t6[1] = U[3] * U[3] * d[0] + U[4] * U[4] * d[1] + U[5] * U[5] * d[2] + vol;
-    t6[2] = U[6] * U[6] * d[0] + U[7] * U[7] * d[1] + U[8] * U[8] * d[2] + vol;
-    t6[3] = U[0] * U[3] * d[0] + U[1] * U[4] * d[1] + U[2] * U[5] * d[2];
-    t6[4] = U[0] * U[6] * d[0] + U[1] * U[7] * d[1] + U[2] * U[8] * d[2];
-    t6[5] = U[3] * U[6] * d[0] + U[4] * U[7] * d[1] + U[5] * U[8] * d[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        dg[k] = 2.0f * m.mu * d.sm1[k] * d.s[k];
+    tau6(d.U, dg, m.la * (1.0f + d.Jm1) * d.Jm1, t6);
 }
 
 }  // namespace mpm

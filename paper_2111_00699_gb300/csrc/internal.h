@@ -14,8 +14,8 @@ enum Channel : int {
     CH_X = 0,    // x, y, z
     CH_V = 3,    // velocity
     CH_C = 6,    // affine velocity C (row-major 3x3)
-    CH_F = 15,   // deformation gradient F (row-major 3x3)
-    CH_JP = 24,  // snow Jp / fluid J
+    CH_F = 15,   // displacement gradient H = F - I (row-major 3x3)
+    CH_JP = 24,  // snow Jp - 1 / fluid J - 1 (0 for the other models)
     CH_VOL = 25, // rest volume
     CH_TAU = 26, // Kirchhoff stress of the current F: xx, yy, zz, xy, xz, yz
     kChannels = 32
@@ -36,7 +36,9 @@ enum G2PVariant : int {
     G2P_DIRECT = 0,   // thread per particle, 27 gathers
     G2P_CHUNK4 = 1,   // thread walks 4 consecutive particles, node velocities cached per base cell
     G2P_CHUNK8 = 2,   // same with 8 particles per thread
-    kG2PVariants = 3
+    G2P_TILE = 3,     // CTA stages its grid tile in shared memory, gathers from there
+    G2P_OCC = 4,      // thread per particle capped at 64 registers (occupancy)
+    kG2PVariants = 5
 };
 
 // Device status word bits.
@@ -52,7 +54,7 @@ struct MatParams {
     int kind;
     float mu, la, rho;
     float K, gamma;          // fluid
-    float lo, hi, xi;        // snow clamp bounds, hardening
+    float lo_m1, hi_m1, xi;  // snow clamp bounds of sigma - 1 (-theta_c, theta_s), hardening
     float alpha, dp_coef;    // sand: cone slope, (3 la + 2 mu) / (2 mu)
 };
 

@@ -117,9 +117,9 @@ __global__ void k_append(PartView pv, int64_t n0, int64_t n, const float* __rest
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
         pv.ch(CH_C + e)[p] = 0.0f;
-        pv.ch(CH_F + e)[p] = (e % 4 == 0) ? 1.0f : 0.0f;
+        pv.ch(CH_F + e)[p] = 0.0f;   // F - I
     }
-    pv.ch(CH_JP)[p] = 1.0f;
+    pv.ch(CH_JP)[p] = 0.0f;          // Jp - 1 (J - 1 for fluids)
     pv.ch(CH_VOL)[p] = vol ? vol[i] : default_vol;
 #pragma unroll
     for (int e = 0; e < 6; ++e)
@@ -129,24 +129,32 @@ __global__ void k_append(PartView pv, int64_t n0, int64_t n, const float* __rest
 }
 
 // out[id[i] * width + e] = channel(first + e)[i]: storage order -> insertion order.
-__global__ void k_gather_out(PartView pv, int64_t n, int first, int width, float* __restrict__ out)
+// F and Jp are held as F - I and Jp - 1 (J - 1 for fluids): the fields
+// with a unit bias add it on the way out and remove it on the way in.
+// bias_step: 4 for F (diagonal entries 0, 4, 8), 1 for Jp, 0 for none.
+__device__ __forceinline__ float unit_bias(int e, int bias_step)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n)
-        return;
-    int64_t q = pv.id[i];
-    for (int e = 0; e < width; ++e)
-        out[q * width + e] = pv.ch(first + e)[i];
+    return (bias_step && e % bias_step == 0) ? 1.0f : 0.0f;
 }
 
-__global__ void k_scatter_in(PartView pv, int64_t n, int first, int width, const float* __restrict__ in)
+__global__ void k_gather_out(PartView pv, int64_t n, int first, int width, int bias_step, float* __restrict__ out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
     int64_t q = pv.id[i];
     for (int e = 0; e < width; ++e)
-        pv.ch(first + e)[i] = in[q * width + e];
+        out[q * width + e] = pv.ch(first + e)[i] + unit_bias(e, bias_step);
+}
+
+__global__ void k_scatter_in(PartView pv, int64_t n, int first, int width, int bias_step, const float* __restrict__ in)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t q = pv.id[i];
+    for (int e = 0; e < width; ++e)
+        pv.ch(first + e)[i] = in[q * width + e] - unit_bias(e, bias_step);
 }
 
 __global__ void k_grid_to_dense(SimParams sp, const float4* __restrict__ grid, const int32_t* __restrict__ pslot,
@@ -205,28 +213,30 @@ void launch_append(const PartView& pv, int64_t n0, int64_t n, const float* x, co
 }
 
 // field: 0 x, 1 v, 2 C, 3 F, 4 Jp
-static void field_range(int field, int& first, int& width)
+static void field_range(int field, int& first, int& width, int& bias_step)
 {
     static const int F0[5] = {CH_X, CH_V, CH_C, CH_F, CH_JP};
     static const int W[5] = {3, 3, 9, 9, 1};
+    static const int B[5] = {0, 0, 0, 4, 1};
     first = F0[field];
     width = W[field];
+    bias_step = B[field];
 }
 
 void launch_gather_out(const PartView& pv, int64_t n, int field, float* out, cudaStream_t s)
 {
-    int first, width;
-    field_range(field, first, width);
+    int first, width, bias_step;
+    field_range(field, first, width, bias_step);
     if (n > 0)
-        k_gather_out<<<blocks_for(n), kBlock, 0, s>>>(pv, n, first, width, out);
+        k_gather_out<<<blocks_for(n), kBlock, 0, s>>>(pv, n, first, width, bias_step, out);
 }
 
 void launch_scatter_in(const PartView& pv, int64_t n, int field, const float* in, cudaStream_t s)
 {
-    int first, width;
-    field_range(field, first, width);
+    int first, width, bias_step;
+    field_range(field, first, width, bias_step);
     if (n > 0)
-        k_scatter_in<<<blocks_for(n), kBlock, 0, s>>>(pv, n, first, width, in);
+        k_scatter_in<<<blocks_for(n), kBlock, 0, s>>>(pv, n, first, width, bias_step, in);
 }
 
 void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t* pslot, int32_t n_pblocks,

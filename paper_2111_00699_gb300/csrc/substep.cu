@@ -369,20 +369,19 @@ __global__ void __launch_bounds__(kTransferThreads) k_p2g_chunk(SimParams sp, Pa
         acc_flush(gv, acc, cb, err);
 }
 
-// Kirchhoff stress of the stored F and Jp, for states P2G has not seen yet
-// (after mpm_write_state).
+// Kirchhoff stress of the stored H = F - I and Jp - 1, for states P2G has
+// not seen yet (after mpm_write_state).
 __global__ void k_prepare_stress(SimParams sp, PartView pv, int64_t n)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
     const MatParams m = sp.mat[pv.mat[p]];
-    float F[9], tau[9];
+    float H[9], t6[6];
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        F[e] = pv.ch(CH_F + e)[p];
-    kirchhoff(m, F, pv.ch(CH_JP)[p], tau);
-    const float t6[6] = {tau[0], tau[4], tau[8], tau[1], tau[2], tau[5]};
+        H[e] = pv.ch(CH_F + e)[p];
+    stress_h(m, H, pv.ch(CH_JP)[p], t6);
 #pragma unroll
     for (int e = 0; e < 6; ++e)
         pv.ch(CH_TAU + e)[p] = t6[e];
@@ -524,30 +523,33 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
         pv.ch(CH_V + a)[p] = vp[a];
     }
     const MatParams m = sp.mat[pv.mat[p]];
-    float Jp = pv.ch(CH_JP)[p];
+    float jm1 = pv.ch(CH_JP)[p];
     float t6[6];
     if (m.kind == MPM_FLUID) {
-        Jp *= 1.0f + dt * (C[0] + C[4] + C[8]);
-        pv.ch(CH_JP)[p] = Jp;
-        float Fdummy[9];
-        constitutive_update(m, Fdummy, Jp, t6);
+        // J <- (1 + dt tr C) J, held as J - 1
+        jm1 += dt * (C[0] + C[4] + C[8]) * (1.0f + jm1);
+        pv.ch(CH_JP)[p] = jm1;
+        float Hdummy[9];
+        constitutive_update(m, Hdummy, jm1, t6);
     } else {
-        float F[9], Fn[9];
+        // F <- (I + dt C) F, i.e. H <- H + dt (C + C H)
+        float H[9], Hn[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e)
-            F[e] = pv.ch(CH_F + e)[p];
+            H[e] = pv.ch(CH_F + e)[p];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                Fn[3 * r + c] = F[3 * r + c] + dt * (C[3 * r] * F[c] + C[3 * r + 1] * F[3 + c] + C[3 * r + 2] * F[6 + c]);
-        float Jn = Jp;
-        constitutive_update(m, Fn, Jn, t6);
+                Hn[3 * r + c] = H[3 * r + c] + dt * (C[3 * r + c] + C[3 * r] * H[c] + C[3 * r + 1] * H[3 + c] +
+                                                     C[3 * r + 2] * H[6 + c]);
+        float jn = jm1;
+        constitutive_update(m, Hn, jn, t6);
 #pragma unroll
         for (int e = 0; e < 9; ++e)
-            pv.ch(CH_F + e)[p] = Fn[e];
+            pv.ch(CH_F + e)[p] = Hn[e];
         if (m.kind == MPM_SNOW)
-            pv.ch(CH_JP)[p] = Jn;
+            pv.ch(CH_JP)[p] = jn;
     }
     if (kFused) {
         // the fused kernel scatters the new state at once: tau is not stored
@@ -635,6 +637,121 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
         float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
         return make_float3(g.x, g.y, g.z);
     }, vp, Bm);
+    g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+}
+
+// G2P_OCC: the thread-per-particle G2P capped at 64 registers (8 CTAs of 128
+// per SM) to trade register pressure for occupancy.
+__global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_occ(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                float dt, uint32_t* __restrict__ flags,
+                                                                uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float x[3], f[3], w[3][3];
+    int b[3];
+    if (!g2p_weights(sp, pv, p, x, b, f, w, err))
+        return;
+    int pb[8];
+    if (!stencil_blocks(gv, b, pb)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+    const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
+    float vp[3], Bm[9];
+    g2p_accumulate(f, w, [&](int i, int j, int k) {
+        int nx = bx + i, ny = by + j, nz = bz + k;
+        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+        return make_float3(g.x, g.y, g.z);
+    }, vp, Bm);
+    g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+}
+
+// G2P_TILE: shared-memory staging of the block-local grid tile.  The CTA's
+// 128 consecutive (cell-sorted) particles span a small box of nodes; the CTA
+// loads that box once, coalesced, into shared memory, and each particle then
+// gathers its 27 nodes from shared memory (tens of cycles) instead of L2
+// (hundreds).  A CTA whose box exceeds the tile gathers from global memory.
+constexpr int kG2PTileNodes = 1024;   // 16 KB of float4
+
+__global__ void __launch_bounds__(kTransferThreads) k_g2p_tile(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                               float dt, uint32_t* __restrict__ flags,
+                                                               uint32_t* __restrict__ err)
+{
+    __shared__ float4 tile[kG2PTileNodes];
+    __shared__ int box[6];
+    __shared__ int tile_ok;
+    const int tid = threadIdx.x;
+    if (tid < 3) {
+        box[tid] = 0x7fffffff;
+        box[3 + tid] = -0x7fffffff;
+    }
+    if (tid == 0)
+        tile_ok = 1;
+    __syncthreads();
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + tid;
+    float x[3], f[3], w[3][3];
+    int b[3];
+    bool ok = p < n && g2p_weights(sp, pv, p, x, b, f, w, err);
+    if (ok) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&box[a], b[a]);
+            atomicMax(&box[3 + a], b[a]);
+        }
+    }
+    __syncthreads();
+    const int lo0 = box[0], lo1 = box[1], lo2 = box[2];
+    const int d0 = box[3] - lo0 + 3, d1 = box[4] - lo1 + 3, d2 = box[5] - lo2 + 3;
+    const bool empty = box[3] < lo0;
+    const int nodes = empty ? 0 : d0 * d1 * d2;
+    const bool use_tile = nodes > 0 && nodes <= kG2PTileNodes;   // uniform across the CTA
+    if (use_tile) {
+        for (int i = tid; i < nodes; i += kTransferThreads) {
+            int xx = lo0 + i % d0, yy = lo1 + (i / d0) % d1, zz = lo2 + i / (d0 * d1);
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (xx < sp.res[0] && yy < sp.res[1] && zz < sp.res[2]) {
+                int blk = __ldg(&gv.table[morton3((uint32_t)xx >> 2, (uint32_t)yy >> 2, (uint32_t)zz >> 2)]);
+                if (blk >= 0)
+                    g = gv.cur[(int64_t)blk * 64 + (xx & 3) + 4 * (yy & 3) + 16 * (zz & 3)];
+                else
+                    tile_ok = 0;   // a node no particle should need is unmapped: checked per particle below
+            }
+            tile[i] = g;
+        }
+        __syncthreads();
+    }
+    if (!ok)
+        return;
+    float vp[3], Bm[9];
+    if (use_tile) {
+        // the particle's own stencil must be mapped (the tile holds zeros elsewhere)
+        int pb[8];
+        if (!tile_ok && !stencil_blocks(gv, b, pb)) {
+            atomicOr(err, ST_MISSED);
+            return;
+        }
+        const int o0 = b[0] - lo0, o1 = b[1] - lo1, o2 = b[2] - lo2;
+        g2p_accumulate(f, w, [&](int i, int j, int k) {
+            float4 g = tile[(o0 + i) + d0 * ((o1 + j) + d1 * (o2 + k))];
+            return make_float3(g.x, g.y, g.z);
+        }, vp, Bm);
+    } else {
+        int pb[8];
+        if (!stencil_blocks(gv, b, pb)) {
+            atomicOr(err, ST_MISSED);
+            return;
+        }
+        const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
+        g2p_accumulate(f, w, [&](int i, int j, int k) {
+            int nx = bx + i, ny = by + j, nz = bz + k;
+            int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
+            float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+            return make_float3(g.x, g.y, g.z);
+        }, vp, Bm);
+    }
     g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
 }
 
@@ -751,23 +868,26 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartVi
     scatter_to(gv, gv.nxt, q, err);
 }
 
+// Debug kernels take F and Jp (or fluid J) as a user holds them and run the
+// product's H = F - I formulation on them.
 __global__ void k_debug_svd(const float* __restrict__ F, float* U, float* sig, float* V, int64_t n)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
-    float f[9], u[9], s[3], v[9];
+    float h[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        f[e] = F[9 * p + e];
-    svd3(f, u, s, v);
+        h[e] = F[9 * p + e] - ((e % 4 == 0) ? 1.0f : 0.0f);
+    SVDH d;
+    svd_h(h, d);
     for (int e = 0; e < 9; ++e) {
-        if (U) U[9 * p + e] = u[e];
-        if (V) V[9 * p + e] = v[e];
+        if (U) U[9 * p + e] = d.U[e];
+        if (V) V[9 * p + e] = d.V[e];
     }
     if (sig)
         for (int e = 0; e < 3; ++e)
-            sig[3 * p + e] = s[e];
+            sig[3 * p + e] = d.s[e];
 }
 
 __global__ void k_debug_stress(MatParams m, const float* __restrict__ F, const float* __restrict__ Jp,
@@ -776,14 +896,15 @@ __global__ void k_debug_stress(MatParams m, const float* __restrict__ F, const f
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
-    float f[9], t[9];
+    float h[9], t[6];
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        f[e] = F[9 * p + e];
-    kirchhoff(m, f, Jp ? Jp[p] : 1.0f, t);
+        h[e] = F[9 * p + e] - ((e % 4 == 0) ? 1.0f : 0.0f);
+    stress_h(m, h, Jp ? Jp[p] - 1.0f : 0.0f, t);
+    const float full[9] = {t[0], t[3], t[4], t[3], t[1], t[5], t[4], t[5], t[2]};
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        tau[9 * p + e] = t[e];
+        tau[9 * p + e] = full[e];
 }
 
 __global__ void k_debug_plasticity(MatParams m, float* __restrict__ F, float* __restrict__ Jp, int64_t n)
@@ -791,17 +912,18 @@ __global__ void k_debug_plasticity(MatParams m, float* __restrict__ F, float* __
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
         return;
-    float f[9];
+    float h[9], t[6];
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        f[e] = F[9 * p + e];
-    float j = Jp ? Jp[p] : 1.0f;
-    plasticity(m, f, j);
+        h[e] = F[9 * p + e] - ((e % 4 == 0) ? 1.0f : 0.0f);
+    float jm1 = Jp ? Jp[p] - 1.0f : 0.0f;
+    if (m.kind == MPM_SNOW || m.kind == MPM_SAND)
+        constitutive_update(m, h, jm1, t);
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        F[9 * p + e] = f[e];
+        F[9 * p + e] = h[e] + ((e % 4 == 0) ? 1.0f : 0.0f);
     if (Jp)
-        Jp[p] = j;
+        Jp[p] = 1.0f + jm1;
 }
 
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
@@ -818,8 +940,8 @@ MatParams make_mat_params(const mpm_material& m)
     q.la = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
     q.K = m.E;
     q.gamma = m.gamma;
-    q.lo = 1.0f - m.theta_c;
-    q.hi = 1.0f + m.theta_s;
+    q.lo_m1 = -m.theta_c;
+    q.hi_m1 = m.theta_s;
     q.xi = m.hardening;
     double sphi = sin((double)m.friction_deg * 3.14159265358979323846 / 180.0);
     q.alpha = (float)(sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
@@ -861,7 +983,11 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n > 0)
     {
-        if (variant == G2P_CHUNK8)
+        if (variant == G2P_TILE)
+            k_g2p_tile<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+        else if (variant == G2P_OCC)
+            k_g2p_occ<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+        else if (variant == G2P_CHUNK8)
             k_g2p_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
                                                                                                  flags, err);
         else if (variant == G2P_CHUNK4)

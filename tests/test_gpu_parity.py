@@ -99,6 +99,26 @@ def test_stress_matches_oracle(M, kind):
     assert linf(tau, ref) <= 1e-4 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("kind", ["elastic", "snow", "sand"])
+def test_stress_small_strain_matches_oracle(M, kind):
+    """Strains of 1e-4: the stress is proportional to sigma - 1, which an SVD
+    of F itself resolves only to ~1e-7 / 1e-4 = 1e-3 relative.  The kernels
+    hold H = F - I and get sigma - 1 from F^T F - I = H + H^T + H^T H, so
+    they must match the oracle to 1e-4 here too (both sides see the same
+    FP32-rounded F, for which F - I is exact)."""
+    rng = np.random.default_rng(11)
+    n = 2048
+    kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2), snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, hardening=10.0),
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3))[kind]
+    k = kw.pop("kind")
+    gm, om = M.material(k, **kw), orc.material(k, **kw)
+    F = (np.eye(3) + 1e-4 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    Jp = np.ones(n, np.float32)
+    tau = M.debug_stress(gm, torch.from_numpy(F).cuda(), torch.from_numpy(Jp).cuda()).double().cpu().numpy()
+    ref = np.stack([orc.kirchhoff(om, F[i].astype(np.float64), 1.0) for i in range(n)])
+    assert linf(tau, ref) <= 1e-4 * np.abs(ref).max()
+
+
 def test_plasticity_matches_oracle(M):
     rng = np.random.default_rng(2)
     n = 1024
@@ -416,7 +436,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
         res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1)
         assert res["best"] in range(5) and all(v > 0 for v in res["ms"].values())
         res = tune.tune_g2p(sim, 1e-4, steps=2, rounds=1)
-        assert res["best"] in range(3) and all(v > 0 for v in res["ms"].values())
+        assert res["best"] in range(5) and all(v > 0 for v in res["ms"].values())
         ran = sim.stats()["substeps"]
         s = orc.State(x.astype(np.float64), vol=vol)
         for _ in range(ran):
@@ -426,7 +446,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0)])
+@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
