@@ -320,9 +320,15 @@ def _variant_name(kind, v):
 
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
-                        "chunk4": "k_p2g_chunk<4>", "chunk8": "k_p2g_chunk<8>"},
+                        "chunk4": "k_p2g_chunk<4>", "chunk8": "k_p2g_chunk<8>", "stage4": "k_p2g_stage<4>",
+                        "stage8": "k_p2g_stage<8>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         "occ": "k_g2p_occ"}}
+
+
+FUSED_SCATTER_VARIANTS = (0, 3, 4)
+FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chunk<4>", 4: "k_g2p2g_chunk<8>",
+                      5: "k_g2p2g_chunk<4>", 6: "k_g2p2g_chunk<8>"}
 
 
 def _traffic_for(kernel, src_hash):
@@ -346,7 +352,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the batched / fountain / sand sections")
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
-                    help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8); -1 = autotune")
+                    help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
+                         "6 stage8); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ); -1 = autotune")
     ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
@@ -402,17 +409,30 @@ def main():
         warm -= 120
     else:
         sim.set_g2p_variant(args.g2p_variant)
-    # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene
-    fused_ms = {}
-    for on in (False, True, False, True):
-        sim.set_g2p2g(on)
+    # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene;
+    # the fused kernel's scatter follows the P2G variant (direct, chunk4, chunk8)
+    fused_ms, fused_scatter_ms = {}, {}
+    p2g_separate = tuned["best"] if tuned["best"] >= 0 else 3
+    for _ in range(2):
+        sim.set_g2p2g(False)
+        sim.set_p2g_variant(p2g_separate)
         sim.run(3, DT)
-        fused_ms.setdefault("g2p2g" if on else "separate", []).append(
-            _events_time(stream, lambda: sim.run(20, DT)) / 20)
+        fused_ms.setdefault("separate", []).append(_events_time(stream, lambda: sim.run(20, DT)) / 20)
         warm -= 23
-    fused_ms = {k: min(v) for k, v in fused_ms.items()}
+        for v in FUSED_SCATTER_VARIANTS:
+            sim.set_p2g_variant(v)
+            sim.set_g2p2g(True)
+            sim.run(3, DT)
+            fused_scatter_ms.setdefault(_variant_name("P2G", v), []).append(
+                _events_time(stream, lambda: sim.run(20, DT)) / 20)
+            warm -= 23
+    fused_scatter_ms = {k: min(v) for k, v in fused_scatter_ms.items()}
+    fused_best = min(FUSED_SCATTER_VARIANTS, key=lambda v: fused_scatter_ms[_variant_name("P2G", v)])
+    fused_ms = {"separate": min(fused_ms["separate"]), "g2p2g": fused_scatter_ms[_variant_name("P2G", fused_best)]}
     use_fused = args.g2p2g if args.g2p2g is not None else fused_ms["g2p2g"] < fused_ms["separate"]
+    p2g_final = fused_best if use_fused else p2g_separate
     sim.set_g2p2g(bool(use_fused))
+    sim.set_p2g_variant(p2g_final)
     warm = max(3, warm)
     sim.run(warm, DT)
     sim.sync()
@@ -470,7 +490,8 @@ def main():
         # per substep: grid update + k_g2p2g (reads x F Jp vol mat 57 B, writes x v C F Jp 100 B)
         algo["g2p"] = 157 * n_now
     kernel_name = {"p2g": KERNEL_NAMES["P2G"][tuned["best_name"]],
-                   "g2p": "k_g2p2g" if use_fused else KERNEL_NAMES["G2P"][tuned_g["best_name"]],
+                   "g2p": (FUSED_KERNEL_NAMES[p2g_final] if use_fused
+                           else KERNEL_NAMES["G2P"][tuned_g["best_name"]]),
                    "grid": "k_grid"}[dom]
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_note,
@@ -482,7 +503,7 @@ def main():
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if args.e2e_frames > 0:
-        sim = fresh_sim(tuned["best"], tuned_g["best"])
+        sim = fresh_sim(p2g_final, tuned_g["best"])
         sim.set_g2p2g(bool(use_fused))
         host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
                 for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
@@ -535,7 +556,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
             "clocks": clk.summary(), "p2g_variant": tuned, "g2p_variant": tuned_g,
-            "transfer": {"mode": "g2p2g" if use_fused else "separate", "ms_per_substep": fused_ms}, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
+            "transfer": {"mode": "g2p2g" if use_fused else "separate", "ms_per_substep": fused_ms,
+                         "g2p2g_scatter_ms": fused_scatter_ms, "p2g_variant_used": _variant_name("P2G", p2g_final)}, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu, "workloads": workloads}
     print(json.dumps(line))
     if world > 1:

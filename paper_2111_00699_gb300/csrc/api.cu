@@ -59,6 +59,7 @@ struct mpm_ctx {
     int32_t* ranks = nullptr;
     int32_t* table = nullptr;
     int32_t* pslot = nullptr;
+    uint8_t* interior = nullptr;   // per physical block, n_slots bytes
     void* scan_scr = nullptr;
     size_t scan_scr_bytes = 0;
     int32_t n_pblocks = 0;
@@ -238,6 +239,8 @@ mpm_status device_error(mpm_ctx* ctx)
         return fail(ctx, MPM_EDOMAIN, "a particle stencil left the grid");
     if (e & ST_MISSED)
         return fail(ctx, MPM_EDOMAIN, "a particle outran its mapped blocks (moved more than one cell per substep)");
+    if (e & ST_TIMEOUT)
+        return fail(ctx, MPM_ETIMEOUT, "an asynchronous copy into shared memory did not complete in time");
     return MPM_OK;
 }
 
@@ -249,9 +252,9 @@ mpm_status ensure_particle_capacity(mpm_ctx* ctx, int64_t need)
                          (ctx->cfg.max_particles > 0 && ctx->cap >= ctx->cfg.max_particles && need <= ctx->cap)))
         return MPM_OK;
     // Sec. 3.1: grow to 4x the requested size once more than half full.
-    int64_t ncap = round_up(4 * need, 256);
+    int64_t ncap = round_up(4 * need, kCapQuantum);
     if (ctx->cfg.max_particles > 0 && ncap > ctx->cfg.max_particles)
-        ncap = round_up(ctx->cfg.max_particles, 256);
+        ncap = round_up(ctx->cfg.max_particles, kCapQuantum);
     if (ncap > (int64_t)0x7fffff00)
         return fail(ctx, MPM_ECAPACITY, "particle count exceeds 2^31");
     size_t nb = part_bytes(ncap);
@@ -309,6 +312,7 @@ GridView grid_view(mpm_ctx* ctx)
     g.nxt = ctx->grid[1 - ctx->gcur];
     g.table = ctx->table;
     g.pslot = ctx->pslot;
+    g.interior = ctx->interior;
     g.n_pblocks = ctx->n_pblocks;
     return g;
 }
@@ -347,6 +351,8 @@ mpm_status rebuild(mpm_ctx* ctx)
     CK(cudaGetLastError());
     int32_t npb = (int32_t)ctx->hstat[kRing + 1];
     ctx->n_pblocks = npb;
+    launch_interior(sp, ctx->table, ctx->pslot, npb, ctx->interior, s);
+    ctx->launches += 1;
     if ((int64_t)npb > ctx->grid_cap / 2 || !ctx->grid[0]) {
         int64_t gcap = 4 * (int64_t)npb;
         if (gcap > ctx->n_slots)
@@ -444,12 +450,13 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
     ctx->n_slots = (int64_t)1 << (3 * L);
 
     mpm_status st = MPM_OK;
-    size_t b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0;
+    size_t b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0, b5 = 0;
     size_t sb = (size_t)ctx->n_slots * 4;
     if ((st = realloc_buf(ctx, ctx->flags, b0, sb)) != MPM_OK ||
         (st = realloc_buf(ctx, ctx->ranks, b1, sb)) != MPM_OK ||
         (st = realloc_buf(ctx, ctx->table, b2, sb)) != MPM_OK ||
         (st = realloc_buf(ctx, ctx->pslot, b3, sb)) != MPM_OK ||
+        (st = realloc_buf(ctx, ctx->interior, b5, (size_t)ctx->n_slots)) != MPM_OK ||
         (st = realloc_buf(ctx, ctx->dstat, b4, 256)) != MPM_OK ||
         (st = realloc_buf(ctx, ctx->scan_scr, ctx->scan_scr_bytes, scan_scratch_bytes(ctx->n_slots))) != MPM_OK) {
         mpm_destroy(ctx);
@@ -504,6 +511,7 @@ void mpm_destroy(mpm_ctx* ctx)
     dfree(ctx, ctx->ranks, sb);
     dfree(ctx, ctx->table, sb);
     dfree(ctx, ctx->pslot, sb);
+    dfree(ctx, ctx->interior, (size_t)ctx->n_slots);
     dfree(ctx, ctx->scan_scr, ctx->scan_scr_bytes);
     dfree(ctx, ctx->grid[0], (size_t)ctx->grid_cap * 1024);
     dfree(ctx, ctx->grid[1], (size_t)ctx->grid_cap * 1024);
@@ -629,7 +637,7 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
     launch_grid_update(ctx->sp, gv, dt, s);
     prof_end(ctx, 2, e1);
     prof_begin(ctx, e2);
-    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, s);
+    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.p2g_variant, s);
     prof_end(ctx, 3, e2);
     ctx->launches += 2;
     CK(cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s));

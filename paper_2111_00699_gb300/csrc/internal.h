@@ -28,8 +28,14 @@ enum P2GVariant : int {
     P2G_TILE = 2,     // CTA accumulates its 256 particles into a shared-memory node tile, one flush
     P2G_CHUNK4 = 3,   // thread walks 4 consecutive particles, register accumulation per base-cell run
     P2G_CHUNK8 = 4,   // same with 8 particles per thread
-    kP2GVariants = 5
+    P2G_STAGE4 = 5,   // CHUNK4 reading a CTA's 512 particles from shared memory, staged by bulk async copies
+    P2G_STAGE8 = 6,   // same with 8 particles per thread (1024 per CTA)
+    kP2GVariants = 7
 };
+
+// Particle capacity is a multiple of this, so that a staged tile of
+// particles never reads past the end of a channel array.
+constexpr int64_t kCapQuantum = 1024;
 
 // G2P gather variants (tuning knob mpm_config.g2p_variant).
 enum G2PVariant : int {
@@ -48,6 +54,7 @@ enum : uint32_t {
     ST_EDOMAIN = 4u,       // a stencil left the grid
     ST_ENONFINITE = 8u,    // a position became non-finite
     ST_MISSED = 16u,       // P2G/G2P found an unmapped block (CFL violated)
+    ST_TIMEOUT = 32u,      // an asynchronous copy did not complete within its wait limit
 };
 
 struct MatParams {
@@ -81,6 +88,7 @@ struct GridView {
     float4* nxt;          // buffer for the next substep (cleared by the grid update)
     const int32_t* table; // Morton slot -> physical block index, or -1
     const int32_t* pslot; // physical block index -> Morton slot
+    const uint8_t* interior; // physical block index -> 1 if its 26 neighbours (in the grid) are mapped
     int32_t n_pblocks;
 };
 
@@ -101,6 +109,8 @@ void launch_mark_pblocks(const uint32_t* skeys, int64_t n, int L, int32_t* flags
 void launch_build_table(const int32_t* flags, const int32_t* ranks, int64_t n_slots, int32_t* table,
                         int32_t* pslot, int32_t* n_pblocks, cudaStream_t s);
 void launch_permute(const PartView& src, const PartView& dst, const int32_t* perm, int64_t n, cudaStream_t s);
+void launch_interior(const SimParams& sp, const int32_t* table, const int32_t* pslot, int32_t n_pblocks,
+                     uint8_t* interior, cudaStream_t s);
 void launch_append(const PartView& pv, int64_t n0, int64_t n, const float* x, const float* v,
                    const float* vol, float default_vol, int material, cudaStream_t s);
 void launch_gather_out(const PartView& pv, int64_t n, int field, float* out, cudaStream_t s);
@@ -113,7 +123,7 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
                 uint32_t* err, int variant, cudaStream_t s);
 void launch_prepare_stress(const SimParams& sp, const PartView& pv, int64_t n, cudaStream_t s);
 void launch_g2p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
-                  uint32_t* flags, uint32_t* err, cudaStream_t s);
+                  uint32_t* flags, uint32_t* err, int p2g_variant, cudaStream_t s);
 void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaStream_t s);
 void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                 uint32_t* flags, uint32_t* err, int variant, cudaStream_t s);

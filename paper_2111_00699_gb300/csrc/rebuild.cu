@@ -88,6 +88,32 @@ __global__ void k_table(const int32_t* __restrict__ flags, const int32_t* __rest
         *n_pblocks = r + f;
 }
 
+// Interior blocks: a physical block whose 26 neighbours that lie in the grid
+// are all mapped.  A base cell in an interior block keeps the particle's
+// stencil, widened by up to 4 cells per side, inside mapped blocks.
+__global__ void k_interior(SimParams sp, const int32_t* __restrict__ table, const int32_t* __restrict__ pslot,
+                           int32_t n_pblocks, uint8_t* __restrict__ interior)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pblocks)
+        return;
+    uint32_t s = (uint32_t)pslot[r];
+    int B[3] = {(int)compact3(s), (int)compact3(s >> 1), (int)compact3(s >> 2)};
+    bool ok = true;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int N[3] = {B[0] + dx, B[1] + dy, B[2] + dz};
+                bool in = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    in = in && N[a] >= 0 && N[a] <= (sp.res[a] - 1) >> 2;
+                if (in)
+                    ok = ok && table[morton3((uint32_t)N[0], (uint32_t)N[1], (uint32_t)N[2])] >= 0;
+            }
+    interior[r] = ok ? 1 : 0;
+}
+
 // dst[i] = src[perm[i]] for every channel, the material and the id.
 __global__ void k_permute(PartView src, PartView dst, const int32_t* __restrict__ perm, int64_t n)
 {
@@ -203,6 +229,13 @@ void launch_permute(const PartView& src, const PartView& dst, const int32_t* per
 {
     if (n > 0)
         k_permute<<<blocks_for(n), kBlock, 0, s>>>(src, dst, perm, n);
+}
+
+void launch_interior(const SimParams& sp, const int32_t* table, const int32_t* pslot, int32_t n_pblocks,
+                     uint8_t* interior, cudaStream_t s)
+{
+    if (n_pblocks > 0)
+        k_interior<<<blocks_for(n_pblocks), kBlock, 0, s>>>(sp, table, pslot, n_pblocks, interior);
 }
 
 void launch_append(const PartView& pv, int64_t n0, int64_t n, const float* x, const float* v, const float* vol,

@@ -14,6 +14,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
+#include "async_copy.cuh"
 #include "device_math.cuh"
 #include "internal.h"
 
@@ -31,12 +34,15 @@ __device__ __forceinline__ bool stencil_blocks(const GridView& gv, const int* b,
 {
     uint32_t sx[2], sy[2], sz[2];
     int B0 = b[0] >> 2, B1 = b[1] >> 2, B2 = b[2] >> 2;
+    // Morton codes of B and B + 1 per axis; the +1 is done on the dilated
+    // bits directly (fill the other axes' bits with ones, add, mask).
+    constexpr uint32_t kMx = 0x09249249u, kMy = kMx << 1, kMz = kMx << 2;
     sx[0] = spread3((uint32_t)B0);
-    sx[1] = spread3((uint32_t)B0 + 1u);
+    sx[1] = ((sx[0] | ~kMx) + 1u) & kMx;
     sy[0] = spread3((uint32_t)B1) << 1;
-    sy[1] = spread3((uint32_t)B1 + 1u) << 1;
+    sy[1] = ((sy[0] | ~kMy) + 1u) & kMy;
     sz[0] = spread3((uint32_t)B2) << 2;
-    sz[1] = spread3((uint32_t)B2 + 1u) << 2;
+    sz[1] = ((sz[0] | ~kMz) + 1u) & kMz;
     int cx = (b[0] & 3) >= 2, cy = (b[1] & 3) >= 2, cz = (b[2] & 3) >= 2;
     bool ok = true;
 #pragma unroll
@@ -52,6 +58,39 @@ __device__ __forceinline__ bool stencil_blocks(const GridView& gv, const int* b,
                 }
                 pb[dx + 2 * dy + 4 * dz] = v;
             }
+    return ok;
+}
+
+// Grid index of the 27 nodes of a stencil at base b, from the (up to) 8
+// blocks stencil_blocks returned.  Node (i, j, k) lies in candidate block
+// (dx, dy, dz) with dx = ((b_x & 3) + i) >> 2 and so on; the block is picked
+// by one select per axis (z, then y, then x), so that after unrolling a row
+// of 3 nodes costs 2 selects and each node 1 more.
+struct StencilIndex {
+    int pb64[8];   // candidate block slot * 64 (0 where unused)
+    int bx, by, bz;
+
+    __device__ __forceinline__ int operator()(int i, int j, int k) const
+    {
+        const int nx = bx + i, ny = by + j, nz = bz + k;
+        const bool dz = nz >= 4, dy = ny >= 4, dx = nx >= 4;
+        const int q0 = dz ? pb64[4] : pb64[0], q1 = dz ? pb64[5] : pb64[1];
+        const int q2 = dz ? pb64[6] : pb64[2], q3 = dz ? pb64[7] : pb64[3];
+        const int r0 = dy ? q2 : q0, r1 = dy ? q3 : q1;
+        return (dx ? r1 : r0) + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
+    }
+};
+
+__device__ __forceinline__ bool stencil_index(const GridView& gv, const int* b, StencilIndex& si)
+{
+    int pb[8];
+    bool ok = stencil_blocks(gv, b, pb);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        si.pb64[c] = pb[c] * 64;
+    si.bx = b[0] & 3;
+    si.by = b[1] & 3;
+    si.bz = b[2] & 3;
     return ok;
 }
 
@@ -74,13 +113,15 @@ struct P2GParticle {
     float mp, mv[3], A[9];
 };
 
-__device__ __forceinline__ bool load_p2g_particle(const SimParams& sp, const PartView& pv, int64_t p, float dt,
-                                                  P2GParticle& q, uint32_t* err)
+// get(c) returns channel c of the particle (global channel numbering).
+template <class Get>
+__device__ __forceinline__ bool make_p2g_particle(const SimParams& sp, Get get, int mat, float dt, P2GParticle& q,
+                                                  uint32_t* err)
 {
     float x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        x[a] = pv.ch(CH_X + a)[p];
+        x[a] = get(CH_X + a);
         q.b[a] = base_of(x[a], sp.inv_dx);
         q.f[a] = __fmul_rn(x[a], sp.inv_dx) - (float)q.b[a];
         bspline(q.f[a], q.w[a]);
@@ -89,23 +130,29 @@ __device__ __forceinline__ bool load_p2g_particle(const SimParams& sp, const Par
         atomicOr(err, ST_EDOMAIN);
         return false;
     }
-    const float rho = sp.mat[pv.mat[p]].rho;
-    float vol = pv.ch(CH_VOL)[p];
+    const float rho = sp.mat[mat].rho;
+    float vol = get(CH_VOL);
     q.mp = rho * vol;
     float kst = 4.0f * dt * vol * sp.inv_dx * sp.inv_dx;
     float t[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e)
-        t[e] = kst * pv.ch(CH_TAU + e)[p];
+        t[e] = kst * get(CH_TAU + e);
     // symmetric tau: (xx, yy, zz, xy, xz, yz)
     const float tm[9] = {t[0], t[3], t[4], t[3], t[1], t[5], t[4], t[5], t[2]};
 #pragma unroll
     for (int e = 0; e < 9; ++e)
-        q.A[e] = (q.mp * pv.ch(CH_C + e)[p] - tm[e]) * sp.dx;
+        q.A[e] = (q.mp * get(CH_C + e) - tm[e]) * sp.dx;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-        q.mv[a] = q.mp * pv.ch(CH_V + a)[p];
+        q.mv[a] = q.mp * get(CH_V + a);
     return true;
+}
+
+__device__ __forceinline__ bool load_p2g_particle(const SimParams& sp, const PartView& pv, int64_t p, float dt,
+                                                  P2GParticle& q, uint32_t* err)
+{
+    return make_p2g_particle(sp, [&](int c) { return pv.ch(c)[p]; }, pv.mat[p], dt, q, err);
 }
 
 __device__ __forceinline__ float4 node_contribution(const P2GParticle& q, int i, int j, int k)
@@ -124,26 +171,18 @@ __device__ __forceinline__ float4 node_contribution(const P2GParticle& q, int i,
 // (a grid buffer with the mapping of gv).
 __device__ __forceinline__ void scatter_to(const GridView& gv, float4* target, const P2GParticle& q, uint32_t* err)
 {
-    int pb[8];
-    if (!stencil_blocks(gv, q.b, pb)) {
+    StencilIndex si;
+    if (!stencil_index(gv, q.b, si)) {
         atomicOr(err, ST_MISSED);
         return;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int nz = (q.b[2] & 3) + k;
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            int ny = (q.b[1] & 3) + j;
+        for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                int nx = (q.b[0] & 3) + i;
-                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
-                atomicAdd(&target[(int64_t)blk * 64 + local], node_contribution(q, i, j, k));
-            }
-        }
-    }
+            for (int i = 0; i < 3; ++i)
+                atomicAdd(&target[si(i, j, k)], node_contribution(q, i, j, k));
 }
 
 __device__ __forceinline__ void scatter_global(const GridView& gv, const P2GParticle& q, uint32_t* err)
@@ -309,28 +348,21 @@ __device__ __forceinline__ void acc_add(NodeAcc& acc, const P2GParticle& q)
         }
 }
 
-__device__ __forceinline__ void acc_flush(const GridView& gv, const NodeAcc& acc, const int* b, uint32_t* err)
+__device__ __forceinline__ void acc_flush(const GridView& gv, float4* target, const NodeAcc& acc, const int* b,
+                                          uint32_t* err)
 {
-    int pb[8];
-    if (!stencil_blocks(gv, b, pb)) {
+    StencilIndex si;
+    if (!stencil_index(gv, b, si)) {
         atomicOr(err, ST_MISSED);
         return;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int nz = (b[2] & 3) + k;
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            int ny = (b[1] & 3) + j;
+        for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                int nx = (b[0] & 3) + i;
-                int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-                int local = (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
-                atomicAdd(&gv.cur[(int64_t)blk * 64 + local], acc.a[i + 3 * j + 9 * k]);
-            }
-        }
-    }
+            for (int i = 0; i < 3; ++i)
+                atomicAdd(&target[si(i, j, k)], acc.a[i + 3 * j + 9 * k]);
 }
 
 template <int K>
@@ -353,7 +385,7 @@ __global__ void __launch_bounds__(kTransferThreads) k_p2g_chunk(SimParams sp, Pa
         if (!load_p2g_particle(sp, pv, p, dt, q, err))
             continue;
         if (open && (q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2])) {
-            acc_flush(gv, acc, cb, err);
+            acc_flush(gv, gv.cur, acc, cb, err);
             acc_zero(acc);
             open = false;
         }
@@ -366,7 +398,102 @@ __global__ void __launch_bounds__(kTransferThreads) k_p2g_chunk(SimParams sp, Pa
         acc_add(acc, q);
     }
     if (open)
-        acc_flush(gv, acc, cb, err);
+        acc_flush(gv, gv.cur, acc, cb, err);
+}
+
+// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the
+// CTA's 128 K consecutive particles brought into shared memory first by one
+// bulk asynchronous copy per channel (the TMA engine's 1-D form), issued by
+// one thread and completed on an mbarrier.  The channel arrays are read
+// once, fully coalesced and with all copies in flight together, and the
+// per-particle loop then reads shared memory only.
+constexpr int kStageThreads = 128;
+constexpr int kStageCh = 22;   // x 3, v 3, C 9 (channels 0..14), vol, tau 6 (channels 25..31)
+constexpr int kStageWaitIter = 1 << 16;
+
+__host__ __device__ constexpr int stage_slot(int c) { return c < 15 ? c : c - 10; }
+__host__ __device__ constexpr int stage_channel(int i) { return i < 15 ? i : i + 10; }
+
+template <int K>
+constexpr size_t stage_smem_bytes() { return (size_t)kStageThreads * K * (kStageCh * 4 + 1); }
+
+template <int K>
+__global__ void __launch_bounds__(kStageThreads) k_p2g_stage(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                             float dt, uint32_t* __restrict__ err)
+{
+    static_assert(stage_slot(CH_VOL) == 15 && stage_slot(CH_TAU) == 16 && stage_channel(21) == CH_TAU + 5, "slots");
+    constexpr int T = kStageThreads * K;
+    extern __shared__ __align__(128) float sm[];   // kStageCh x T floats, then T material bytes
+    __shared__ __align__(8) uint64_t bar;
+    uint8_t* smat = reinterpret_cast<uint8_t*>(sm + kStageCh * T);
+    const int tid = threadIdx.x;
+    const int64_t p0 = (int64_t)blockIdx.x * T;
+    if (tid == 0)
+        mbar_init(&bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        // p0 + T <= cap (the capacity is a multiple of kCapQuantum): every
+        // copy stays inside its channel array; entries past n are not used.
+        mbar_arrive_expect_tx(&bar, (uint32_t)(T * (kStageCh * 4 + 1)));
+#pragma unroll 1
+        for (int i = 0; i < kStageCh; ++i)
+            bulk_copy_g2s(sm + i * T, pv.ch(stage_channel(i)) + p0, T * 4, &bar);
+        bulk_copy_g2s(smat, pv.mat + p0, T, &bar);
+    }
+    if (!mbar_wait(&bar, 0, kStageWaitIter)) {
+        if (tid == 0)
+            atomicOr(err, ST_TIMEOUT);
+        mbar_wait(&bar, 0, kStageWaitIter);   // let copies still in flight land before the CTA exits
+        return;
+    }
+    const int l0 = tid * K;
+    if (p0 + l0 >= n)
+        return;
+    NodeAcc acc;
+    acc_zero(acc);
+    int cb[3] = {0, 0, 0};
+    bool open = false;
+#pragma unroll 1
+    for (int j = 0; j < K; ++j) {
+        const int l = l0 + j;
+        if (p0 + l >= n)
+            break;
+        P2GParticle q;
+        if (!make_p2g_particle(sp, [&](int c) { return sm[stage_slot(c) * T + l]; }, smat[l], dt, q, err))
+            continue;
+        if (open && (q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2])) {
+            acc_flush(gv, gv.cur, acc, cb, err);
+            acc_zero(acc);
+            open = false;
+        }
+        if (!open) {
+            cb[0] = q.b[0];
+            cb[1] = q.b[1];
+            cb[2] = q.b[2];
+            open = true;
+        }
+        acc_add(acc, q);
+    }
+    if (open)
+        acc_flush(gv, gv.cur, acc, cb, err);
+}
+
+template <int K>
+void launch_p2g_stage(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
+                      uint32_t* err, cudaStream_t s)
+{
+    // the dynamic shared-memory opt-in is set once per device
+    static std::atomic<uint64_t> attr_set{0};
+    constexpr size_t bytes = stage_smem_bytes<K>();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        cudaFuncSetAttribute(k_p2g_stage<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        attr_set.fetch_or(bit);
+    }
+    constexpr int T = kStageThreads * K;
+    k_p2g_stage<K><<<(unsigned)((n + T - 1) / T), kStageThreads, bytes, s>>>(sp, pv, gv, n, dt, err);
 }
 
 // Kirchhoff stress of the stored H = F - I and Jp - 1, for states P2G has
@@ -462,36 +589,53 @@ __device__ __forceinline__ bool g2p_weights(const SimParams& sp, const PartView&
 }
 
 // vp = sum w v_i, Bm = sum w v_i (node - f)^T over the 27 stencil nodes,
-// node velocities given by vel(i, j, k) -> float3.
+// node velocities given by vel(i, j, k) -> float3.  With centred offsets
+// e = (i, j, k) - 1 in {-1, 0, 1}, sum w v (node - f)^T = sum w v e^T - vp (f - 1)^T,
+// and both weighted sums factor axis by axis: each row of 3 nodes along x is
+// reduced first (its sum and its e_x moment), then the rows along y, then z.
 template <class Vel>
 __device__ __forceinline__ void g2p_accumulate(const float* f, const float (*w)[3], Vel vel, float* vp, float* Bm)
 {
-    vp[0] = vp[1] = vp[2] = 0.0f;
+    float M[3][3];   // M[a][d] = sum w v_a e_d
 #pragma unroll
-    for (int e = 0; e < 9; ++e)
-        Bm[e] = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        vp[a] = 0.0f;
+        M[a][0] = M[a][1] = M[a][2] = 0.0f;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float dz = (float)k - f[2];
+        float s[3] = {0.f, 0.f, 0.f}, sx[3] = {0.f, 0.f, 0.f}, sy[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float dy = (float)j - f[1];
-            float wyz = w[1][j] * w[2][k];
+            const float3 g0 = vel(0, j, k), g1 = vel(1, j, k), g2 = vel(2, j, k);
+            const float a0[3] = {w[0][0] * g0.x, w[0][0] * g0.y, w[0][0] * g0.z};
+            const float a2[3] = {w[0][2] * g2.x, w[0][2] * g2.y, w[0][2] * g2.z};
+            const float g1v[3] = {g1.x, g1.y, g1.z};
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float dxo = (float)i - f[0];
-                float wt = w[0][i] * wyz;
-                float3 g = vel(i, j, k);
-                float gx = wt * g.x, gy = wt * g.y, gz = wt * g.z;
-                vp[0] += gx;
-                vp[1] += gy;
-                vp[2] += gz;
-                Bm[0] += gx * dxo; Bm[1] += gx * dy; Bm[2] += gx * dz;
-                Bm[3] += gy * dxo; Bm[4] += gy * dy; Bm[5] += gy * dz;
-                Bm[6] += gz * dxo; Bm[7] += gz * dy; Bm[8] += gz * dz;
+            for (int a = 0; a < 3; ++a) {
+                const float r = a0[a] + w[0][1] * g1v[a] + a2[a];   // row sum
+                const float rx = a2[a] - a0[a];                       // row e_x moment
+                s[a] += w[1][j] * r;
+                sx[a] += w[1][j] * rx;
+                if (j == 0) sy[a] -= w[1][0] * r;
+                if (j == 2) sy[a] += w[1][2] * r;
             }
         }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            vp[a] += w[2][k] * s[a];
+            M[a][0] += w[2][k] * sx[a];
+            M[a][1] += w[2][k] * sy[a];
+            if (k == 0) M[a][2] -= w[2][0] * s[a];
+            if (k == 2) M[a][2] += w[2][2] * s[a];
+        }
     }
+    const float fm[3] = {f[0] - 1.0f, f[1] - 1.0f, f[2] - 1.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            Bm[3 * a + d] = M[a][d] - vp[a] * fm[d];
 }
 
 // Everything after the gather: C, x, v, the F update with the return map and
@@ -504,8 +648,9 @@ struct G2POut {
 
 template <bool kFused>
 __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
-                                             const float* x, const int* b, const float* vp, const float* Bm, float dt,
-                                             uint32_t* __restrict__ flags, uint32_t* __restrict__ err, G2POut* out)
+                                             const float* x, const int* b, int own_rank, const float* vp,
+                                             const float* Bm, float dt, uint32_t* __restrict__ flags,
+                                             uint32_t* __restrict__ err, G2POut* out)
 {
     // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
     float C[9];
@@ -574,7 +719,10 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
     // checks the stencil widened by kM cells per side; failing that asks for
     // a rebuild before the substep after next.  kM = 1 when the next P2G is
     // a separate launch (one substep of travel before it); kM = 2 for the
-    // fused G2P2G, whose scatter already happens at the new position.
+    // fused G2P2G, whose scatter already happens at the new position.  A new
+    // base cell in an interior block (all 26 neighbours mapped) passes at
+    // once; own_rank is the physical index of the old base cell's block
+    // (-1 if the caller does not have it).
     int bn[3];
     bool moved = false, bad = false;
 #pragma unroll
@@ -597,8 +745,12 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
             atomicOr(err, ST_EDOMAIN);
             return false;
         }
+        const bool same_block = (bn[0] >> 2) == (b[0] >> 2) && (bn[1] >> 2) == (b[1] >> 2) && (bn[2] >> 2) == (b[2] >> 2);
+        int rank = same_block ? own_rank : -1;
+        if (rank < 0)
+            rank = __ldg(&gv.table[morton3((uint32_t)bn[0] >> 2, (uint32_t)bn[1] >> 2, (uint32_t)bn[2] >> 2)]);
         int lo[3] = {bn[0] - kM, bn[1] - kM, bn[2] - kM}, hi[3] = {bn[0] + 2 + kM, bn[1] + 2 + kM, bn[2] + 2 + kM};
-        if (!range_mapped(sp, gv, lo, hi)) {
+        if (!(rank >= 0 && __ldg(&gv.interior[rank])) && !range_mapped(sp, gv, lo, hi)) {
             int lo2[3] = {bn[0], bn[1], bn[2]}, hi2[3] = {bn[0] + 2, bn[1] + 2, bn[2] + 2};
             atomicOr(flags, range_mapped(sp, gv, lo2, hi2) ? ST_REBUILD_SOFT : (ST_REBUILD_SOFT | ST_REBUILD_HARD));
         }
@@ -607,10 +759,11 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
 }
 
 __device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
-                                           const float* x, const int* b, const float* vp, const float* Bm, float dt,
-                                           uint32_t* __restrict__ flags, uint32_t* __restrict__ err)
+                                           const float* x, const int* b, int own_rank, const float* vp,
+                                           const float* Bm, float dt, uint32_t* __restrict__ flags,
+                                           uint32_t* __restrict__ err)
 {
-    g2p_finish_t<false>(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err, nullptr);
+    g2p_finish_t<false>(sp, pv, gv, p, x, b, own_rank, vp, Bm, dt, flags, err, nullptr);
 }
 
 __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView pv, GridView gv, int64_t n,
@@ -624,20 +777,17 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
     int b[3];
     if (!g2p_weights(sp, pv, p, x, b, f, w, err))
         return;
-    int pb[8];
-    if (!stencil_blocks(gv, b, pb)) {
+    StencilIndex si;
+    if (!stencil_index(gv, b, si)) {
         atomicOr(err, ST_MISSED);
         return;
     }
-    const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
     float vp[3], Bm[9];
     g2p_accumulate(f, w, [&](int i, int j, int k) {
-        int nx = bx + i, ny = by + j, nz = bz + k;
-        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+        const float4 g = gv.cur[si(i, j, k)];
         return make_float3(g.x, g.y, g.z);
     }, vp, Bm);
-    g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+    g2p_finish(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err);
 }
 
 // G2P_OCC: the thread-per-particle G2P capped at 64 registers (8 CTAs of 128
@@ -653,20 +803,17 @@ __global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_occ(SimParams sp, P
     int b[3];
     if (!g2p_weights(sp, pv, p, x, b, f, w, err))
         return;
-    int pb[8];
-    if (!stencil_blocks(gv, b, pb)) {
+    StencilIndex si;
+    if (!stencil_index(gv, b, si)) {
         atomicOr(err, ST_MISSED);
         return;
     }
-    const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
     float vp[3], Bm[9];
     g2p_accumulate(f, w, [&](int i, int j, int k) {
-        int nx = bx + i, ny = by + j, nz = bz + k;
-        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+        const float4 g = gv.cur[si(i, j, k)];
         return make_float3(g.x, g.y, g.z);
     }, vp, Bm);
-    g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+    g2p_finish(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err);
 }
 
 // G2P_TILE: shared-memory staging of the block-local grid tile.  The CTA's
@@ -739,20 +886,17 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p_tile(SimParams sp, Par
             return make_float3(g.x, g.y, g.z);
         }, vp, Bm);
     } else {
-        int pb[8];
-        if (!stencil_blocks(gv, b, pb)) {
+        StencilIndex si;
+        if (!stencil_index(gv, b, si)) {
             atomicOr(err, ST_MISSED);
             return;
         }
-        const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
         g2p_accumulate(f, w, [&](int i, int j, int k) {
-            int nx = bx + i, ny = by + j, nz = bz + k;
-            int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-            float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+            const float4 g = gv.cur[si(i, j, k)];
             return make_float3(g.x, g.y, g.z);
         }, vp, Bm);
     }
-    g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+    g2p_finish(sp, pv, gv, p, x, b, -1, vp, Bm, dt, flags, err);
 }
 
 // A thread walks K consecutive particles (cell-sorted storage order) and keeps
@@ -769,6 +913,7 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p_chunk(SimParams sp, Pa
         return;
     float3 cache[27];
     int cb[3] = {-1, -1, -1};
+    int own_rank = -1;
     bool have = false;
 #pragma unroll 1
     for (int jj = 0; jj < K; ++jj) {
@@ -780,24 +925,22 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p_chunk(SimParams sp, Pa
         if (!g2p_weights(sp, pv, p, x, b, f, w, err))
             continue;
         if (!have || b[0] != cb[0] || b[1] != cb[1] || b[2] != cb[2]) {
-            int pb[8];
-            if (!stencil_blocks(gv, b, pb)) {
+            StencilIndex si;
+            if (!stencil_index(gv, b, si)) {
                 atomicOr(err, ST_MISSED);
                 have = false;
                 continue;
             }
-            const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        int nx = bx + i, ny = by + j, nz = bz + k;
-                        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-                        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+                        const float4 g = gv.cur[si(i, j, k)];
                         cache[i + 3 * j + 9 * k] = make_float3(g.x, g.y, g.z);
                     }
+            own_rank = si.pb64[0] >> 6;
             cb[0] = b[0];
             cb[1] = b[1];
             cb[2] = b[2];
@@ -805,45 +948,38 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p_chunk(SimParams sp, Pa
         }
         float vp[3], Bm[9];
         g2p_accumulate(f, w, [&](int i, int j, int k) { return cache[i + 3 * j + 9 * k]; }, vp, Bm);
-        g2p_finish(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err);
+        g2p_finish(sp, pv, gv, p, x, b, own_rank, vp, Bm, dt, flags, err);
     }
 }
 
 // Fused G2P2G (Sec. 4.1: G2P of substep n and P2G of substep n + 1 in one
 // kernel, the paper's choice below ~100K particles without particle
 // addition): gather from gv.cur at x_n, update the particle (one SVD for the
-// return map and the stress), write x, v, C, F, Jp, and scatter the new
-// particle's momentum into gv.nxt at x_{n+1}.  gv.nxt must be zero (the grid
-// update of this substep cleared it).
-__global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartView pv, GridView gv, int64_t n,
-                                                            float dt, uint32_t* __restrict__ flags,
-                                                            uint32_t* __restrict__ err)
+// return map and the stress), write x, v, C, F, Jp, and build the new
+// particle's P2G record at x_{n+1} for the scatter into gv.nxt, which must be
+// zero (the grid update of this substep cleared it).
+__device__ __forceinline__ bool g2p2g_particle(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
+                                               float dt, uint32_t* __restrict__ flags, uint32_t* __restrict__ err,
+                                               P2GParticle& q)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
-        return;
     float x[3], f[3], w[3][3];
     int b[3];
     if (!g2p_weights(sp, pv, p, x, b, f, w, err))
-        return;
-    int pb[8];
-    if (!stencil_blocks(gv, b, pb)) {
+        return false;
+    StencilIndex si;
+    if (!stencil_index(gv, b, si)) {
         atomicOr(err, ST_MISSED);
-        return;
+        return false;
     }
-    const int bx = b[0] & 3, by = b[1] & 3, bz = b[2] & 3;
     float vp[3], Bm[9];
     g2p_accumulate(f, w, [&](int i, int j, int k) {
-        int nx = bx + i, ny = by + j, nz = bz + k;
-        int blk = pb[(nx >> 2) + 2 * (ny >> 2) + 4 * (nz >> 2)];
-        float4 g = gv.cur[(int64_t)blk * 64 + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3)];
+        const float4 g = gv.cur[si(i, j, k)];
         return make_float3(g.x, g.y, g.z);
     }, vp, Bm);
     G2POut o;
-    if (!g2p_finish_t<true>(sp, pv, gv, p, x, b, vp, Bm, dt, flags, err, &o))
-        return;
-    // P2G of the new state (same arithmetic as load_p2g_particle)
-    P2GParticle q;
+    if (!g2p_finish_t<true>(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err, &o))
+        return false;
+    // P2G record of the new state (same arithmetic as load_p2g_particle)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         q.b[a] = base_of(o.xn[a], sp.inv_dx);
@@ -852,7 +988,7 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartVi
     }
     if (!in_grid(sp, q.b, o.xn)) {
         atomicOr(err, ST_EDOMAIN);
-        return;
+        return false;
     }
     const float rho = sp.mat[pv.mat[p]].rho;
     float vol = pv.ch(CH_VOL)[p];
@@ -865,7 +1001,62 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartVi
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         q.mv[a] = q.mp * o.vp[a];
-    scatter_to(gv, gv.nxt, q, err);
+    return true;
+}
+
+// Thread per particle, 27 float4 reductions per particle.
+__global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                            float dt, uint32_t* __restrict__ flags,
+                                                            uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    P2GParticle q;
+    if (g2p2g_particle(sp, pv, gv, p, dt, flags, err, q))
+        scatter_to(gv, gv.nxt, q, err);
+}
+
+// The scatter of k_p2g_chunk inside the fused kernel: a thread walks K
+// consecutive particles and accumulates the new particles' contributions in
+// registers while their new base cells agree (particles move less than a
+// cell per substep, so the cell sort still groups them), flushing 27 float4
+// reductions into gv.nxt per run.
+template <int K>
+__global__ void __launch_bounds__(kTransferThreads) k_g2p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                  float dt, uint32_t* __restrict__ flags,
+                                                                  uint32_t* __restrict__ err)
+{
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
+    if (p0 >= n)
+        return;
+    NodeAcc acc;
+    acc_zero(acc);
+    int cb[3] = {0, 0, 0};
+    bool open = false;
+#pragma unroll 1
+    for (int jj = 0; jj < K; ++jj) {
+        int64_t p = p0 + jj;
+        if (p >= n)
+            break;
+        P2GParticle q;
+        if (!g2p2g_particle(sp, pv, gv, p, dt, flags, err, q))
+            continue;
+        if (open && (q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2])) {
+            acc_flush(gv, gv.nxt, acc, cb, err);
+            acc_zero(acc);
+            open = false;
+        }
+        if (!open) {
+            cb[0] = q.b[0];
+            cb[1] = q.b[1];
+            cb[2] = q.b[2];
+            open = true;
+        }
+        acc_add(acc, q);
+    }
+    if (open)
+        acc_flush(gv, gv.nxt, acc, cb, err);
 }
 
 // Debug kernels take F and Jp (or fluid J) as a user holds them and run the
@@ -954,7 +1145,13 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n <= 0)
         return;
-    if (variant == P2G_CHUNK8)
+    if ((variant == P2G_STAGE4 || variant == P2G_STAGE8) && pv.cap % kCapQuantum != 0)
+        variant = variant == P2G_STAGE8 ? P2G_CHUNK8 : P2G_CHUNK4;   // staging needs whole tiles inside the arrays
+    if (variant == P2G_STAGE8)
+        launch_p2g_stage<8>(sp, pv, gv, n, dt, err, s);
+    else if (variant == P2G_STAGE4)
+        launch_p2g_stage<4>(sp, pv, gv, n, dt, err, s);
+    else if (variant == P2G_CHUNK8)
         k_p2g_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_CHUNK4)
         k_p2g_chunk<4><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
@@ -1020,10 +1217,19 @@ void launch_debug_plasticity(const MatParams& mp, float* F, float* Jp, int64_t n
 
 namespace mpm {
 void launch_g2p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* flags,
-                  uint32_t* err, cudaStream_t s)
+                  uint32_t* err, int p2g_variant, cudaStream_t s)
 {
-    if (n > 0)
-        k_g2p2g<<<(unsigned)((n + kTransferThreads - 1) / kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
-                                                                                                     flags, err);
+    if (n <= 0)
+        return;
+    // the scatter follows the P2G variant: register runs of 4 or 8 particles,
+    // else one thread per particle
+    if (p2g_variant == P2G_CHUNK8 || p2g_variant == P2G_STAGE8)
+        k_g2p2g_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                               flags, err);
+    else if (p2g_variant == P2G_CHUNK4 || p2g_variant == P2G_STAGE4)
+        k_g2p2g_chunk<4><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                               flags, err);
+    else
+        k_g2p2g<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
 }
 }  // namespace mpm

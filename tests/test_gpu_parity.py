@@ -209,7 +209,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -234,7 +234,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -434,7 +434,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     with M.Simulator(64, 1 / 64, [gm]) as sim:
         sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
         res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1)
-        assert res["best"] in range(5) and all(v > 0 for v in res["ms"].values())
+        assert res["best"] in range(7) and all(v > 0 for v in res["ms"].values())
         res = tune.tune_g2p(sim, 1e-4, steps=2, rounds=1)
         assert res["best"] in range(5) and all(v > 0 for v in res["ms"].values())
         ran = sim.stats()["substeps"]
@@ -446,7 +446,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4)])
+@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
@@ -522,9 +522,11 @@ def test_sand_blocks_full_size_parity(M):
 
 # ------------------------------------------------------------ fused G2P2G (a6')
 
+@pytest.mark.parametrize("scatter", [0, 3, 4])
 @pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
-def test_g2p2g_matches_oracle(M, kind):
-    """The fused transfer computes the same substeps as the separate phases."""
+def test_g2p2g_matches_oracle(M, kind, scatter):
+    """The fused transfer computes the same substeps as the separate phases,
+    with each scatter form (thread per particle; register runs of 4 and 8)."""
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
               snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
@@ -537,7 +539,7 @@ def test_g2p2g_matches_oracle(M, kind):
     rng = np.random.default_rng(8)
     v = (0.3 * rng.normal(size=(len(x), 3))).astype(np.float32)
     cfg = orc.config(64, 1 / 64, orc.SLIP)
-    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=True) as sim:
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=True, p2g_variant=scatter) as sim:
         sim.add_particles(x, v=v)
         s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
         g = _run_both(M, sim, [om], s, 10, dt, cfg)
