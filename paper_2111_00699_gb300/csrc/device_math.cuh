@@ -303,6 +303,174 @@ __device__ __forceinline__ float hencky(float s, float sm1)
     return s > 1e-4f ? log1pf(sm1) : logf(1e-4f);
 }
 
+// ---- small-strain path without an SVD ----------------------------------------
+// Near the rest shape every quantity the models need is an isotropic function
+// of the left Cauchy-Green tensor B = F F^T = I + G, G = H + H^T + H H^T, and
+// so a power series in G (all such series commute with G and with each other):
+//   fixed-corotated:  (F - R) F^T = B - sqrt(B)
+//                     = G/2 + G^2/8 - G^3/16 + 5 G^4/128 - 7 G^5/256 + ...
+//   Hencky strain:    eps = ln(B)/2 = (G - G^2/2 + G^3/3 - G^4/4 + G^5/5 - G^6/6 + ...)/2
+//   Drucker-Prager:   F' = exp(-X) F (X = eps for case II, the radial return
+//                     of case III for case III), exp(-X) - I by its series.
+// With |G|_F <= 0.1 the first omitted terms are below 1e-6 of the leading
+// one.  Snow takes this path only when no singular value reaches the clamp
+// (G - lo I and hi I - G both positive definite), and no model takes it for
+// an inverted F.  Everything else goes through the SVD below.
+
+struct Sym {   // symmetric 3x3
+    float xx, yy, zz, xy, xz, yz;
+};
+
+// A B for commuting symmetric A, B (then A B is symmetric).
+__device__ __forceinline__ Sym sym_mul(const Sym& a, const Sym& b)
+{
+    Sym r;
+    r.xx = a.xx * b.xx + a.xy * b.xy + a.xz * b.xz;
+    r.yy = a.xy * b.xy + a.yy * b.yy + a.yz * b.yz;
+    r.zz = a.xz * b.xz + a.yz * b.yz + a.zz * b.zz;
+    r.xy = a.xx * b.xy + a.xy * b.yy + a.xz * b.yz;
+    r.xz = a.xx * b.xz + a.xy * b.yz + a.xz * b.zz;
+    r.yz = a.xy * b.xz + a.yy * b.yz + a.yz * b.zz;
+    return r;
+}
+
+__device__ __forceinline__ Sym sym_scale(const Sym& a, float c)
+{
+    return {a.xx * c, a.yy * c, a.zz * c, a.xy * c, a.xz * c, a.yz * c};
+}
+
+__device__ __forceinline__ Sym sym_add_diag(const Sym& a, float c)
+{
+    return {a.xx + c, a.yy + c, a.zz + c, a.xy, a.xz, a.yz};
+}
+
+// sum_{k=1..N} c[k-1] G^k by Horner.
+template <int N>
+__device__ __forceinline__ Sym sym_series(const Sym& g, const float (&c)[N])
+{
+    Sym q = sym_add_diag(sym_scale(g, c[N - 1]), c[N - 2]);
+#pragma unroll
+    for (int k = N - 3; k >= 0; --k)
+        q = sym_add_diag(sym_mul(g, q), c[k]);
+    return sym_mul(g, q);
+}
+
+__device__ __forceinline__ float sym_frob2(const Sym& a)
+{
+    return a.xx * a.xx + a.yy * a.yy + a.zz * a.zz + 2.0f * (a.xy * a.xy + a.xz * a.xz + a.yz * a.yz);
+}
+
+__device__ __forceinline__ float sym_trace(const Sym& a) { return a.xx + a.yy + a.zz; }
+
+// a positive definite (leading principal minors)
+__device__ __forceinline__ bool sym_pd(const Sym& a)
+{
+    float m2 = a.xx * a.yy - a.xy * a.xy;
+    float m3 = a.xx * (a.yy * a.zz - a.yz * a.yz) - a.xy * (a.xy * a.zz - a.yz * a.xz) +
+               a.xz * (a.xy * a.yz - a.yy * a.xz);
+    return a.xx > 0.0f && m2 > 0.0f && m3 > 0.0f;
+}
+
+// G = F F^T - I = H + H^T + H H^T
+__device__ __forceinline__ Sym left_cg_m1(const float* H)
+{
+    Sym g;
+    g.xx = 2.f * H[0] + H[0] * H[0] + H[1] * H[1] + H[2] * H[2];
+    g.yy = 2.f * H[4] + H[3] * H[3] + H[4] * H[4] + H[5] * H[5];
+    g.zz = 2.f * H[8] + H[6] * H[6] + H[7] * H[7] + H[8] * H[8];
+    g.xy = H[1] + H[3] + H[0] * H[3] + H[1] * H[4] + H[2] * H[5];
+    g.xz = H[2] + H[6] + H[0] * H[6] + H[1] * H[7] + H[2] * H[8];
+    g.yz = H[5] + H[7] + H[3] * H[6] + H[4] * H[7] + H[5] * H[8];
+    return g;
+}
+
+constexpr float kSeriesMaxG2 = 0.01f;   // |G|_F^2 bound of the series path
+
+__device__ __forceinline__ void sym_to_t6(const Sym& a, float* t6)
+{
+    t6[0] = a.xx; t6[1] = a.yy; t6[2] = a.zz; t6[3] = a.xy; t6[4] = a.xz; t6[5] = a.yz;
+}
+
+// fixed-corotated: tau = 2 mu (B - sqrt B) + lambda J (J - 1) I
+__device__ __forceinline__ void fc_tau_series(const Sym& g, float mu, float la, float Jm1, float* t6)
+{
+    const float c[5] = {0.5f, 0.125f, -0.0625f, 0.0390625f, -0.02734375f};
+    Sym t = sym_add_diag(sym_scale(sym_series(g, c), 2.0f * mu), la * (1.0f + Jm1) * Jm1);
+    sym_to_t6(t, t6);
+}
+
+// Hencky strain eps = ln(I + G) / 2
+__device__ __forceinline__ Sym hencky_series(const Sym& g)
+{
+    const float c[6] = {0.5f, -0.25f, 1.0f / 6.0f, -0.125f, 0.1f, -1.0f / 12.0f};
+    return sym_series(g, c);
+}
+
+// H <- H + (exp(-X) - I)(I + H), i.e. F <- exp(-X) F
+__device__ __forceinline__ void left_exp_update(const Sym& x, float* H)
+{
+    const float c[5] = {-1.0f, 0.5f, -1.0f / 6.0f, 1.0f / 24.0f, -1.0f / 120.0f};
+    const Sym e = sym_series(x, c);
+    const float E[9] = {e.xx, e.xy, e.xz, e.xy, e.yy, e.yz, e.xz, e.yz, e.zz};
+    float Hn[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2)
+            Hn[3 * r + c2] = H[3 * r + c2] + E[3 * r + c2] + E[3 * r] * H[c2] + E[3 * r + 1] * H[3 + c2] +
+                             E[3 * r + 2] * H[6 + c2];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        H[q] = Hn[q];
+}
+
+// The series path of constitutive_update / stress_h; false if the state is
+// outside its range (the caller then takes the SVD path).  With
+// `project` the return maps run (snow: none needed on this path; sand:
+// cases II and III update H).
+__device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H, float jm1, bool project, float* t6)
+{
+    const Sym g = left_cg_m1(H);
+    const float Jm1 = det_m1(H);
+    if (!(sym_frob2(g) <= kSeriesMaxG2) || !(Jm1 > -1.0f))
+        return false;
+    if (m.kind == MPM_SNOW) {
+        // elastic only if every sigma^2 - 1 (eigenvalue of G) lies strictly inside the clamp
+        if (!sym_pd(sym_add_diag(g, -m.lo_b)) || !sym_pd(sym_add_diag(sym_scale(g, -1.0f), m.hi_b)))
+            return false;
+        const float h = __expf(-m.xi * jm1);
+        fc_tau_series(g, m.mu * h, m.la * h, Jm1, t6);
+        return true;
+    }
+    if (m.kind == MPM_ELASTIC) {
+        fc_tau_series(g, m.mu, m.la, Jm1, t6);
+        return true;
+    }
+    // sand: Hencky strain in the current (left) frame, Drucker-Prager return map
+    Sym eps = hencky_series(g);
+    const float tr = sym_trace(eps);
+    if (project) {
+        if (tr >= 0.0f) {
+            // case II: project to the cone tip, F <- R = exp(-eps) F, tau = 0
+            left_exp_update(eps, H);
+            t6[0] = t6[1] = t6[2] = t6[3] = t6[4] = t6[5] = 0.0f;
+            return true;
+        }
+        const Sym dev = sym_add_diag(eps, -tr * (1.0f / 3.0f));
+        const float nd = sqrtf(sym_frob2(dev));
+        const float dgm = nd + m.dp_coef * tr * m.alpha;
+        if (dgm > 0.0f) {
+            // case III: eps <- eps - dgm dev / |dev|, F <- exp(-X) F with X = dgm dev / |dev|
+            const Sym x = sym_scale(dev, dgm / nd);
+            left_exp_update(x, H);
+            eps = {eps.xx - x.xx, eps.yy - x.yy, eps.zz - x.zz, -x.xy + eps.xy, eps.xz - x.xz, eps.yz - x.yz};
+        }
+    }
+    const Sym t = sym_add_diag(sym_scale(eps, 2.0f * m.mu), m.la * tr);
+    sym_to_t6(t, t6);
+    return true;
+}
+
 // Kirchhoff stress of a stored state (no return map): used when the stress
 // channels must be rebuilt from (H, Jp - 1), e.g. after mpm_write_state.
 //   fixed-corotated: tau = U diag(2 mu (s - 1) s) U^T + lambda J (J - 1) I,
@@ -314,6 +482,14 @@ __device__ __forceinline__ void stress_h(const MatParams& m, const float* H, flo
     if (m.kind == MPM_FLUID) {
         fluid_tau6(m, jm1, t6);
         return;
+    }
+    {
+        float Hc[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            Hc[q] = H[q];
+        if (small_strain_update(m, Hc, jm1, false, t6))
+            return;
     }
     SVDH d;
     svd_h(H, d);
@@ -351,6 +527,8 @@ __device__ __forceinline__ void constitutive_update(const MatParams& m, float* H
         fluid_tau6(m, jm1, t6);
         return;
     }
+    if (small_strain_update(m, H, jm1, true, t6))
+        return;
     SVDH d;
     svd_h(H, d);
     float dg[3];

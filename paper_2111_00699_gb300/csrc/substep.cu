@@ -1133,6 +1133,8 @@ MatParams make_mat_params(const mpm_material& m)
     q.gamma = m.gamma;
     q.lo_m1 = -m.theta_c;
     q.hi_m1 = m.theta_s;
+    q.lo_b = (float)((1.0 - (double)m.theta_c) * (1.0 - (double)m.theta_c) - 1.0);
+    q.hi_b = (float)((1.0 + (double)m.theta_s) * (1.0 + (double)m.theta_s) - 1.0);
     q.xi = m.hardening;
     double sphi = sin((double)m.friction_deg * 3.14159265358979323846 / 180.0);
     q.alpha = (float)(sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
