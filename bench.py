@@ -320,15 +320,16 @@ def _variant_name(kind, v):
 
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
-                        "chunk4": "k_p2g_chunk<4>", "chunk8": "k_p2g_chunk<8>", "stage4": "k_p2g_stage<4>",
-                        "stage8": "k_p2g_stage<8>"},
+                        "chunk4": "k_p2g_chunk<4, false>", "chunk8": "k_p2g_chunk<8, false>", "stage4": "k_p2g_stage<4>",
+                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
-                        "occ": "k_g2p_occ"}}
+                        "occ": "k_g2p_occ", "stage": "k_g2p_stage"}}
 
 
-FUSED_SCATTER_VARIANTS = (0, 3, 4)
-FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chunk<4>", 4: "k_g2p2g_chunk<8>",
-                      5: "k_g2p2g_chunk<4>", 6: "k_g2p2g_chunk<8>"}
+FUSED_SCATTER_VARIANTS = (0, 3, 4, 7)
+FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chunk<4, false>",
+                      4: "k_g2p2g_chunk<8, false>", 5: "k_g2p2g_chunk<4, false>", 6: "k_g2p2g_chunk<8, false>",
+                      7: "k_g2p2g_chunk<4, true>"}
 
 
 def _traffic_for(kernel, src_hash):
@@ -353,9 +354,9 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8); -1 = autotune")
+                         "6 stage8, 7 sacc4); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
-                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ); -1 = autotune")
+                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage); -1 = autotune")
     ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
                     help="1: fused G2P2G transfer, 0: separate phases; default: the faster one")
     args = ap.parse_args()

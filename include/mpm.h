@@ -85,17 +85,20 @@ typedef struct {
     int32_t use_g2p2g;     /* 1: fused G2P2G transfer (Sec. 4.1) -- per substep the grid
                               update and one kernel doing G2P and the next P2G, whose
                               scatter follows p2g_variant (3/4: register runs of 4/8
-                              particles, else one thread per particle);
+                              particles, 7: runs of 4 accumulated in shared memory,
+                              else one thread per particle);
                               0: separate P2G, grid update, G2P */
     int32_t p2g_variant;   /* tuning: 0 direct float4 atomics, 1 cell-strided lanes,
                               2 shared-memory node tile per CTA, 3/4 register
                               accumulation over runs of 4/8 particles, 5/6 the same with
                               each CTA's 512/1024 particles staged in shared memory by
-                              bulk asynchronous copies (see the autotuner) */
+                              bulk asynchronous copies, 7 as 3 with the accumulators in
+                              thread-private shared memory (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64
-                              registers */
+                              registers, 5 the same with each CTA's particle inputs and
+                              2x2x2-block grid tile staged by bulk asynchronous copies */
     int32_t reserved[5];
 } mpm_config;
 

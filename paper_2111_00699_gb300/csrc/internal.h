@@ -30,7 +30,8 @@ enum P2GVariant : int {
     P2G_CHUNK8 = 4,   // same with 8 particles per thread
     P2G_STAGE4 = 5,   // CHUNK4 reading a CTA's 512 particles from shared memory, staged by bulk async copies
     P2G_STAGE8 = 6,   // same with 8 particles per thread (1024 per CTA)
-    kP2GVariants = 7
+    P2G_SACC4 = 7,    // CHUNK4 with the 27 node accumulators in (thread-private) shared memory
+    kP2GVariants = 8
 };
 
 // Particle capacity is a multiple of this, so that a staged tile of
@@ -44,7 +45,8 @@ enum G2PVariant : int {
     G2P_CHUNK8 = 2,   // same with 8 particles per thread
     G2P_TILE = 3,     // CTA stages its grid tile in shared memory, gathers from there
     G2P_OCC = 4,      // thread per particle capped at 64 registers (occupancy)
-    kG2PVariants = 5
+    G2P_STAGE = 5,    // OCC with particle inputs and a 2x2x2-block grid tile staged by bulk async copies
+    kG2PVariants = 6
 };
 
 // Device status word bits.

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "async_copy.cuh"
 #include "device_math.cuh"
@@ -319,7 +320,12 @@ __device__ __forceinline__ void acc_zero(NodeAcc& acc)
 // acc += contributions of particle q (same base cell as the accumulator).
 // The affine term is split per axis: (mv + A d) = (mv + A_y dy + A_z dz) +
 // A_x dx, with the (j, k) part computed once per row.
-__device__ __forceinline__ void acc_add(NodeAcc& acc, const P2GParticle& q)
+// The contributions of particle q to its 27 nodes: add(n, wt, vx, vy, vz, m)
+// for node n = i + 3 j + 9 k receives w (m v + A (node - f)) as wt * (vx, vy,
+// vz) and w m as wt * m.  The affine term is split per axis: (mv + A d) =
+// (mv + A_y dy + A_z dz) + A_x dx, with the (j, k) part computed once per row.
+template <class Add>
+__device__ __forceinline__ void p2g_contributions(const P2GParticle& q, Add add)
 {
     float dxo[3], dyo[3], dzo[3];
 #pragma unroll
@@ -337,16 +343,73 @@ __device__ __forceinline__ void acc_add(NodeAcc& acc, const P2GParticle& q)
             float by = q.mv[1] + q.A[4] * dyo[j] + q.A[5] * dzo[k];
             float bz = q.mv[2] + q.A[7] * dyo[j] + q.A[8] * dzo[k];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float wt = q.w[0][i] * wyz;
-                float4& a = acc.a[i + 3 * j + 9 * k];
-                a.x += wt * (bx + q.A[0] * dxo[i]);
-                a.y += wt * (by + q.A[3] * dxo[i]);
-                a.z += wt * (bz + q.A[6] * dxo[i]);
-                a.w += wt * q.mp;
-            }
+            for (int i = 0; i < 3; ++i)
+                add(i + 3 * j + 9 * k, q.w[0][i] * wyz, bx + q.A[0] * dxo[i], by + q.A[3] * dxo[i],
+                    bz + q.A[6] * dxo[i], q.mp);
         }
 }
+
+// acc += contributions of particle q (same base cell as the accumulator).
+__device__ __forceinline__ void acc_add(NodeAcc& acc, const P2GParticle& q)
+{
+    p2g_contributions(q, [&](int n, float wt, float vx, float vy, float vz, float m) {
+        float4& a = acc.a[n];
+        a.x = fmaf(wt, vx, a.x);
+        a.y = fmaf(wt, vy, a.y);
+        a.z = fmaf(wt, vz, a.z);
+        a.w = fmaf(wt, m, a.w);
+    });
+}
+
+// The same 27 accumulators held in shared memory, private to one thread:
+// node n at base[n * kTransferThreads] (a warp touches 32 consecutive float4
+// per node: no bank conflicts, no atomics).  Frees ~108 registers per thread
+// for occupancy at the cost of a shared load and store per node.
+struct SmemAcc {
+    float4* base;
+};
+
+__device__ __forceinline__ void acc_zero(SmemAcc acc)
+{
+#pragma unroll
+    for (int n = 0; n < 27; ++n)
+        acc.base[n * kTransferThreads] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void acc_add(SmemAcc acc, const P2GParticle& q)
+{
+    p2g_contributions(q, [&](int n, float wt, float vx, float vy, float vz, float m) {
+        float4 a = acc.base[n * kTransferThreads];
+        a.x = fmaf(wt, vx, a.x);
+        a.y = fmaf(wt, vy, a.y);
+        a.z = fmaf(wt, vz, a.z);
+        a.w = fmaf(wt, m, a.w);
+        acc.base[n * kTransferThreads] = a;
+        // one row of 3 nodes at a time: keeps the compiler from hoisting all
+        // 27 shared loads (and their registers) ahead of the arithmetic
+        if (n % 3 == 2)
+            asm volatile("" ::: "memory");
+    });
+}
+
+__device__ __forceinline__ void acc_flush(const GridView& gv, float4* target, SmemAcc acc, const int* b,
+                                          uint32_t* err)
+{
+    StencilIndex si;
+    if (!stencil_index(gv, b, si)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                atomicAdd(&target[si(i, j, k)], acc.base[(i + 3 * j + 9 * k) * kTransferThreads]);
+}
+
+constexpr size_t kSmemAccBytes = (size_t)27 * kTransferThreads * sizeof(float4);
 
 __device__ __forceinline__ void acc_flush(const GridView& gv, float4* target, const NodeAcc& acc, const int* b,
                                           uint32_t* err)
@@ -365,14 +428,17 @@ __device__ __forceinline__ void acc_flush(const GridView& gv, float4* target, co
                 atomicAdd(&target[si(i, j, k)], acc.a[i + 3 * j + 9 * k]);
 }
 
-template <int K>
-__global__ void __launch_bounds__(kTransferThreads) k_p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+template <int K, bool kSmem>
+__global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 1) k_p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
                                                                 float dt, uint32_t* __restrict__ err)
 {
+    extern __shared__ float4 sacc[];
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
     if (p0 >= n)
         return;
-    NodeAcc acc;
+    typename std::conditional<kSmem, SmemAcc, NodeAcc>::type acc;
+    if constexpr (kSmem)
+        acc.base = sacc + threadIdx.x;
     acc_zero(acc);
     int cb[3] = {0, 0, 0};
     bool open = false;
@@ -478,20 +544,27 @@ __global__ void __launch_bounds__(kStageThreads) k_p2g_stage(SimParams sp, PartV
         acc_flush(gv, gv.cur, acc, cb, err);
 }
 
+// Opts kernel `Kernel` into `bytes` of dynamic shared memory, once per
+// kernel and device (the flag set is per instantiation, i.e. per kernel).
+template <auto Kernel>
+void smem_opt_in(size_t bytes)
+{
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+        cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        done.fetch_or(bit);
+    }
+}
+
 template <int K>
 void launch_p2g_stage(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                       uint32_t* err, cudaStream_t s)
 {
-    // the dynamic shared-memory opt-in is set once per device
-    static std::atomic<uint64_t> attr_set{0};
     constexpr size_t bytes = stage_smem_bytes<K>();
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const uint64_t bit = 1ull << (dev & 63);
-    if (!(attr_set.load() & bit)) {
-        cudaFuncSetAttribute(k_p2g_stage<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        attr_set.fetch_or(bit);
-    }
+    smem_opt_in<k_p2g_stage<K>>(bytes);
     constexpr int T = kStageThreads * K;
     k_p2g_stage<K><<<(unsigned)((n + T - 1) / T), kStageThreads, bytes, s>>>(sp, pv, gv, n, dt, err);
 }
@@ -571,12 +644,13 @@ __device__ __forceinline__ bool range_mapped(const SimParams& sp, const GridView
 }
 
 // Weights of one particle for G2P; false if its stencil left the grid.
-__device__ __forceinline__ bool g2p_weights(const SimParams& sp, const PartView& pv, int64_t p, float* x, int* b,
-                                            float* f, float (*w)[3], uint32_t* err)
+template <class Get>
+__device__ __forceinline__ bool g2p_weights_from(const SimParams& sp, Get get, float* x, int* b, float* f,
+                                                 float (*w)[3], uint32_t* err)
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        x[a] = pv.ch(CH_X + a)[p];
+        x[a] = get(CH_X + a);
         b[a] = base_of(x[a], sp.inv_dx);
         f[a] = __fmul_rn(x[a], sp.inv_dx) - (float)b[a];
         bspline(f[a], w[a]);
@@ -586,6 +660,12 @@ __device__ __forceinline__ bool g2p_weights(const SimParams& sp, const PartView&
         return false;
     }
     return true;
+}
+
+__device__ __forceinline__ bool g2p_weights(const SimParams& sp, const PartView& pv, int64_t p, float* x, int* b,
+                                            float* f, float (*w)[3], uint32_t* err)
+{
+    return g2p_weights_from(sp, [&](int c) { return pv.ch(c)[p]; }, x, b, f, w, err);
 }
 
 // vp = sum w v_i, Bm = sum w v_i (node - f)^T over the 27 stencil nodes,
@@ -646,11 +726,13 @@ struct G2POut {
     float xn[3], vp[3], C[9], t6[6];
 };
 
-template <bool kFused>
-__device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
-                                             const float* x, const int* b, int own_rank, const float* vp,
-                                             const float* Bm, float dt, uint32_t* __restrict__ flags,
-                                             uint32_t* __restrict__ err, G2POut* out)
+// get(c) reads input channel c (F - I, Jp - 1) of particle p; mat is its material.
+template <bool kFused, class Get>
+__device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartView& pv, const GridView& gv,
+                                                int64_t p, Get get, int mat, const float* x, const int* b,
+                                                int own_rank, const float* vp, const float* Bm, float dt,
+                                                uint32_t* __restrict__ flags, uint32_t* __restrict__ err,
+                                                G2POut* out)
 {
     // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
     float C[9];
@@ -667,8 +749,8 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
         pv.ch(CH_X + a)[p] = xn[a];
         pv.ch(CH_V + a)[p] = vp[a];
     }
-    const MatParams m = sp.mat[pv.mat[p]];
-    float jm1 = pv.ch(CH_JP)[p];
+    const MatParams m = sp.mat[mat];
+    float jm1 = get(CH_JP);
     float t6[6];
     if (m.kind == MPM_FLUID) {
         // J <- (1 + dt tr C) J, held as J - 1
@@ -681,7 +763,7 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
         float H[9], Hn[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e)
-            H[e] = pv.ch(CH_F + e)[p];
+            H[e] = get(CH_F + e);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -756,6 +838,16 @@ __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView
         }
     }
     return true;
+}
+
+template <bool kFused>
+__device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
+                                             const float* x, const int* b, int own_rank, const float* vp,
+                                             const float* Bm, float dt, uint32_t* __restrict__ flags,
+                                             uint32_t* __restrict__ err, G2POut* out)
+{
+    return g2p_finish_from<kFused>(sp, pv, gv, p, [&](int c) { return pv.ch(c)[p]; }, pv.mat[p], x, b, own_rank, vp,
+                                   Bm, dt, flags, err, out);
 }
 
 __device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
@@ -899,6 +991,146 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p_tile(SimParams sp, Par
     g2p_finish(sp, pv, gv, p, x, b, -1, vp, Bm, dt, flags, err);
 }
 
+// G2P_STAGE: thread per particle, with the CTA's inputs brought into shared
+// memory by bulk asynchronous copies (the TMA engine's 1-D form): the 128
+// particles' x, F - I and Jp - 1 (one copy per channel) and the 2x2x2 grid
+// blocks around the first particle's block (one 1 KB copy per block).  The
+// particles are block-sorted, so most of a CTA gathers its 27 nodes from that
+// tile; a particle whose stencil leaves it gathers from global memory.
+constexpr int kG2PStageIn = 13;   // x (channels 0..2), F - I and Jp - 1 (channels 15..24)
+__host__ __device__ constexpr int g2p_in_slot(int c) { return c < 3 ? c : c - 12; }
+__host__ __device__ constexpr int g2p_in_channel(int i) { return i < 3 ? i : i + 12; }
+
+__global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_stage(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                  float dt, uint32_t* __restrict__ flags,
+                                                                  uint32_t* __restrict__ err)
+{
+    static_assert(g2p_in_slot(CH_F) == 3 && g2p_in_slot(CH_JP) == 12 && g2p_in_channel(12) == CH_JP, "slots");
+    constexpr int T = kTransferThreads;
+    __shared__ __align__(128) float sin[kG2PStageIn * T];
+    __shared__ __align__(128) float4 tile[8 * 64];
+    __shared__ __align__(16) uint8_t smat[T];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int home[3], home_mask, home_slot[8];
+    const int tid = threadIdx.x;
+    const int64_t p0 = (int64_t)blockIdx.x * T;
+    const int64_t p = p0 + tid;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // particles: p0 + T <= cap (capacity is a multiple of kCapQuantum)
+        mbar_arrive_expect_tx(&bar[0], (uint32_t)(T * (kG2PStageIn * 4 + 1)));
+#pragma unroll 1
+        for (int i = 0; i < kG2PStageIn; ++i)
+            bulk_copy_g2s(sin + i * T, pv.ch(g2p_in_channel(i)) + p0, T * 4, &bar[0]);
+        bulk_copy_g2s(smat, pv.mat + p0, T, &bar[0]);
+        // grid tile: the 2x2x2 mapped blocks starting at the first particle's block
+        float x0[3];
+        int b0[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x0[a] = pv.ch(CH_X + a)[p0];
+            b0[a] = base_of(x0[a], sp.inv_dx);
+        }
+        ok = in_grid(sp, b0, x0);
+        int mask = 0;
+        if (ok) {
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                int B[3] = {(b0[0] >> 2) + (c & 1), (b0[1] >> 2) + ((c >> 1) & 1), (b0[2] >> 2) + (c >> 2)};
+                bool in = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    in = in && 4 * B[a] < sp.res[a] && B[a] < (1 << sp.L);
+                int slot = in ? __ldg(&gv.table[morton3((uint32_t)B[0], (uint32_t)B[1], (uint32_t)B[2])]) : -1;
+                home_slot[c] = slot;
+                if (slot >= 0)
+                    mask |= 1 << c;
+            }
+        }
+        home[0] = b0[0] >> 2;
+        home[1] = b0[1] >> 2;
+        home[2] = b0[2] >> 2;
+        home_mask = mask;
+        mbar_arrive_expect_tx(&bar[1], (uint32_t)(__popc(mask) * 1024));
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c)
+            if (mask & (1 << c))
+                bulk_copy_g2s(tile + 64 * c, gv.cur + (int64_t)home_slot[c] * 64, 1024, &bar[1]);
+    }
+    __syncthreads();
+    bool ok = mbar_wait(&bar[0], 0, kStageWaitIter);
+    if (ok && p < n) {
+        const int l = tid;
+        auto get = [&](int c) { return sin[g2p_in_slot(c) * T + l]; };
+        float x[3], f[3], w[3][3];
+        int b[3];
+        if (g2p_weights_from(sp, get, x, b, f, w, err)) {
+            int o[3];
+            bool use_tile = true;
+            int need = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                o[a] = b[a] - 4 * home[a];
+                use_tile = use_tile && o[a] >= 0 && o[a] <= 5;
+            }
+            if (use_tile) {
+                // candidate blocks the stencil touches: per axis o >> 2 .. (o + 2) >> 2
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int d[3] = {c & 1, (c >> 1) & 1, c >> 2};
+                    bool t = true;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        t = t && d[a] >= (o[a] >> 2) && d[a] <= ((o[a] + 2) >> 2);
+                    need |= t ? (1 << c) : 0;
+                }
+                use_tile = (need & ~home_mask) == 0;
+            }
+            float vp[3], Bm[9];
+            int own_rank = -1;
+            bool have = true;
+            if (use_tile && (ok = mbar_wait(&bar[1], 0, kStageWaitIter))) {
+                StencilIndex ti;
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    ti.pb64[c] = 64 * c;
+                ti.bx = o[0];
+                ti.by = o[1];
+                ti.bz = o[2];
+                g2p_accumulate(f, w, [&](int i, int j, int k) {
+                    const float4 g = tile[ti(i, j, k)];
+                    return make_float3(g.x, g.y, g.z);
+                }, vp, Bm);
+                own_rank = home_slot[(o[0] >> 2) + 2 * (o[1] >> 2) + 4 * (o[2] >> 2)];
+            } else if (ok) {
+                StencilIndex si;
+                if (!stencil_index(gv, b, si)) {
+                    atomicOr(err, ST_MISSED);
+                    have = false;
+                } else {
+                    g2p_accumulate(f, w, [&](int i, int j, int k) {
+                        const float4 g = gv.cur[si(i, j, k)];
+                        return make_float3(g.x, g.y, g.z);
+                    }, vp, Bm);
+                    own_rank = si.pb64[0] >> 6;
+                }
+            }
+            if (ok && have)
+                g2p_finish_from<false>(sp, pv, gv, p, get, smat[l], x, b, own_rank, vp, Bm, dt, flags, err, nullptr);
+        }
+    }
+    // no CTA exits with copies into its shared memory still in flight
+    bool done0 = ok || mbar_wait(&bar[0], 0, kStageWaitIter);
+    bool done1 = mbar_wait(&bar[1], 0, kStageWaitIter);
+    if (!(ok && done0 && done1) && tid == 0)
+        atomicOr(err, ST_TIMEOUT);
+}
+
 // A thread walks K consecutive particles (cell-sorted storage order) and keeps
 // the 27 node velocities of the current base cell in registers, loading them
 // again only when the base cell changes (about once per 8 particles after the
@@ -1022,15 +1254,18 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartVi
 // registers while their new base cells agree (particles move less than a
 // cell per substep, so the cell sort still groups them), flushing 27 float4
 // reductions into gv.nxt per run.
-template <int K>
-__global__ void __launch_bounds__(kTransferThreads) k_g2p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+template <int K, bool kSmem>
+__global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 1) k_g2p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
                                                                   float dt, uint32_t* __restrict__ flags,
                                                                   uint32_t* __restrict__ err)
 {
+    extern __shared__ float4 sacc[];
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
     if (p0 >= n)
         return;
-    NodeAcc acc;
+    typename std::conditional<kSmem, SmemAcc, NodeAcc>::type acc;
+    if constexpr (kSmem)
+        acc.base = sacc + threadIdx.x;
     acc_zero(acc);
     int cb[3] = {0, 0, 0};
     bool open = false;
@@ -1153,10 +1388,16 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
         launch_p2g_stage<8>(sp, pv, gv, n, dt, err, s);
     else if (variant == P2G_STAGE4)
         launch_p2g_stage<4>(sp, pv, gv, n, dt, err, s);
-    else if (variant == P2G_CHUNK8)
-        k_p2g_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else if (variant == P2G_SACC4) {
+        smem_opt_in<k_p2g_chunk<4, true>>(kSmemAccBytes);
+        k_p2g_chunk<4, true><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, kSmemAccBytes, s>>>(
+            sp, pv, gv, n, dt, err);
+    } else if (variant == P2G_CHUNK8)
+        k_p2g_chunk<8, false><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                                   err);
     else if (variant == P2G_CHUNK4)
-        k_p2g_chunk<4><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+        k_p2g_chunk<4, false><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
+                                                                                                   err);
     else if (variant == P2G_STRIDED)
         k_p2g_strided<<<blocks_for(n, kTileThreads), kTileThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_TILE)
@@ -1182,7 +1423,9 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n > 0)
     {
-        if (variant == G2P_TILE)
+        if (variant == G2P_STAGE && pv.cap % kCapQuantum == 0)
+            k_g2p_stage<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+        else if (variant == G2P_TILE)
             k_g2p_tile<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
         else if (variant == G2P_OCC)
             k_g2p_occ<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
@@ -1225,12 +1468,16 @@ void launch_g2p2g(const SimParams& sp, const PartView& pv, const GridView& gv, i
         return;
     // the scatter follows the P2G variant: register runs of 4 or 8 particles,
     // else one thread per particle
-    if (p2g_variant == P2G_CHUNK8 || p2g_variant == P2G_STAGE8)
-        k_g2p2g_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
-                                                                                               flags, err);
+    if (p2g_variant == P2G_SACC4) {
+        smem_opt_in<k_g2p2g_chunk<4, true>>(kSmemAccBytes);
+        k_g2p2g_chunk<4, true><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, kSmemAccBytes, s>>>(
+            sp, pv, gv, n, dt, flags, err);
+    } else if (p2g_variant == P2G_CHUNK8 || p2g_variant == P2G_STAGE8)
+        k_g2p2g_chunk<8, false><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(
+            sp, pv, gv, n, dt, flags, err);
     else if (p2g_variant == P2G_CHUNK4 || p2g_variant == P2G_STAGE4)
-        k_g2p2g_chunk<4><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
-                                                                                               flags, err);
+        k_g2p2g_chunk<4, false><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(
+            sp, pv, gv, n, dt, flags, err);
     else
         k_g2p2g<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
 }
