@@ -332,6 +332,18 @@ FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chun
                       7: "k_g2p2g_chunk<4, true>"}
 
 
+KERNEL_SOURCES = ("substep.cu", "device_math.cuh", "async_copy.cuh", "internal.h")
+
+
+def kernel_source_hash():
+    """SHA-1 over the sources the transfer kernels are compiled from: a DRAM
+    traffic figure recorded from an ncu capture is valid only for them."""
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def _traffic_for(kernel, src_hash):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -357,6 +369,9 @@ def main():
                          "6 stage8, 7 sacc4); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage); -1 = autotune")
+    ap.add_argument("--profile-substeps", type=int, default=0,
+                    help="profiler mode: run this many substeps of the snow scene with the given variants "
+                         "(default chunk4 P2G, occ G2P), print one status line and exit; no timing")
     ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
                     help="1: fused G2P2G transfer, 0: separate phases; default: the faster one")
     args = ap.parse_args()
@@ -393,6 +408,23 @@ def main():
                             g2p_variant=gvariant)
         sim.add_particles(xs)
         return sim
+
+    if args.profile_substeps > 0:
+        # a short fixed sequence for ncu captures: the first substep rebuilds,
+        # every later one launches P2G, grid update, G2P (or grid update and
+        # the fused kernel) once
+        pv = args.p2g_variant if args.p2g_variant >= 0 else 3
+        gv = args.g2p_variant if args.g2p_variant >= 0 else 4
+        sim = fresh_sim(pv, gv)
+        sim.set_g2p2g(bool(args.g2p2g))
+        sim.run(args.profile_substeps, DT)
+        sim.sync()
+        if rank == 0:
+            print(json.dumps({"profile_substeps": args.profile_substeps, "p2g_variant": _variant_name("P2G", pv),
+                              "g2p_variant": _variant_name("G2P", gv), "g2p2g": bool(args.g2p2g),
+                              "stats": sim.stats()}))
+        sim.close()
+        return
 
     # ---- device-resident throughput (the `value`) ----
     from paper_2111_00699_gb300 import tune
@@ -486,7 +518,7 @@ def main():
     peak_note = "of measured" if hbm else "of fallback"
     hbm = hbm or 6800.0
     achieved = algo[dom] / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
-    src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", "substep.cu"), "rb").read()).hexdigest()
+    src_hash = kernel_source_hash()
     if use_fused:
         # per substep: grid update + k_g2p2g (reads x F Jp vol mat 57 B, writes x v C F Jp 100 B)
         algo["g2p"] = 157 * n_now

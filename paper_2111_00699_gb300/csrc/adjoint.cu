@@ -6,9 +6,12 @@
 // (mu_p, lambda_p from E_p and a common nu), common density, MLS-MPM
 // transfers with quadratic B-splines, sticky or slip walls.
 //
-// The grid is dense (res0 x res1 x res2 float4 nodes): the differentiable
-// rollouts this serves are small (tens of thousands of particles on 64^3),
-// so mapping and sorting would only add state to differentiate through.
+// The grid is dense (res0 x res1 x res2 nodes): the differentiable rollouts
+// this serves are small (tens of thousands of particles on 64^3), so mapping
+// and sorting would only add state to differentiate through.  The two grid
+// sums (P2G momentum and mass, and the scattered velocity adjoint) are
+// accumulated in FP64 (4 doubles per node): in FP32 their order-dependent
+// rounding made a 200-substep gradient vary by ~1e-3 from run to run.
 //
 // State of one particle: 24 floats x[3] v[3] C[9] H[9], with H = F - I the
 // displacement gradient (row-major).  The
@@ -155,7 +158,7 @@ __device__ __forceinline__ void fc_tau(const DiffParams& dp, float E, const FCDe
 }
 
 __global__ void dk_p2g(DiffParams dp, int64_t n, const float* __restrict__ s, const float* __restrict__ E,
-                       const float* __restrict__ vol, float dt, float4* __restrict__ grid, uint32_t* err)
+                       const float* __restrict__ vol, float dt, double* __restrict__ grid, uint32_t* err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
@@ -189,23 +192,28 @@ __global__ void dk_p2g(DiffParams dp, int64_t n, const float* __restrict__ s, co
                 val.y = wt * (mp * q[4] + A[3] * d0 + A[4] * d1 + A[5] * d2);
                 val.z = wt * (mp * q[5] + A[6] * d0 + A[7] * d1 + A[8] * d2);
                 val.w = wt * mp;
-                atomicAdd(&grid[d_node(dp, S, i, j, kk)], val);
+                double* g = grid + 4 * d_node(dp, S, i, j, kk);
+                atomicAdd(g + 0, (double)val.x);
+                atomicAdd(g + 1, (double)val.y);
+                atomicAdd(g + 2, (double)val.z);
+                atomicAdd(g + 3, (double)val.w);
             }
 }
 
 // v = P / m + dt g with the wall condition; Pm keeps (P, m), vel gets (v, m).
-__global__ void dk_grid(DiffParams dp, int64_t nodes, float dt, const float4* __restrict__ Pm, float4* __restrict__ vel)
+__global__ void dk_grid(DiffParams dp, int64_t nodes, float dt, const double* __restrict__ Pm, float4* __restrict__ vel)
 {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= nodes)
         return;
-    float4 g = Pm[id];
-    float v[3] = {0.f, 0.f, 0.f};
-    if (g.w > 0.0f) {
+    const double2 pa = reinterpret_cast<const double2*>(Pm)[2 * id], pb = reinterpret_cast<const double2*>(Pm)[2 * id + 1];
+    const double P[3] = {pa.x, pa.y, pb.x}, m = pb.y;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (m > 0.0) {
         int c[3] = {(int)(id % dp.res[0]), (int)((id / dp.res[0]) % dp.res[1]), (int)(id / ((int64_t)dp.res[0] * dp.res[1]))};
-        v[0] = g.x / g.w + dt * dp.g[0];
-        v[1] = g.y / g.w + dt * dp.g[1];
-        v[2] = g.z / g.w + dt * dp.g[2];
+        v[0] = P[0] / m + (double)(dt * dp.g[0]);
+        v[1] = P[1] / m + (double)(dt * dp.g[1]);
+        v[2] = P[2] / m + (double)(dt * dp.g[2]);
         if (dp.boundary == MPM_STICKY) {
             bool wall = false;
 #pragma unroll
@@ -223,7 +231,7 @@ __global__ void dk_grid(DiffParams dp, int64_t nodes, float dt, const float4* __
             }
         }
     }
-    vel[id] = make_float4(v[0], v[1], v[2], g.w);
+    vel[id] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)m);
 }
 
 __global__ void dk_g2p(DiffParams dp, int64_t n, const float* __restrict__ s, const float4* __restrict__ vel, float dt,
@@ -286,7 +294,7 @@ __global__ void dk_g2p(DiffParams dp, int64_t n, const float* __restrict__ s, co
 // Reverse of G2P: writes xbar (partial) and Fbar (partial) of the input state
 // and scatters the velocity adjoint to the grid.
 __global__ void dk_g2p_adj(DiffParams dp, int64_t n, const float* __restrict__ s, const float4* __restrict__ vel,
-                           const float* __restrict__ gout, float dt, float* __restrict__ gin, float4* __restrict__ vbar)
+                           const float* __restrict__ gout, float dt, float* __restrict__ gin, double* __restrict__ vbar)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
@@ -375,8 +383,9 @@ __global__ void dk_g2p_adj(DiffParams dp, int64_t n, const float* __restrict__ s
                     vtv += vt[a] * v[a];
                     vCd += v[a] * Cd[a];
                 }
-                atomicAdd(&vbar[id], make_float4(wt * (vt[0] + D * Cd[0]), wt * (vt[1] + D * Cd[1]),
-                                                 wt * (vt[2] + D * Cd[2]), 0.0f));
+                atomicAdd(vbar + 4 * id + 0, (double)(wt * (vt[0] + D * Cd[0])));
+                atomicAdd(vbar + 4 * id + 1, (double)(wt * (vt[1] + D * Cd[1])));
+                atomicAdd(vbar + 4 * id + 2, (double)(wt * (vt[2] + D * Cd[2])));
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
                     xb[a] += gw[a] * (vtv + D * vCd) - D * wt * CtTv[a];
@@ -390,41 +399,41 @@ __global__ void dk_g2p_adj(DiffParams dp, int64_t n, const float* __restrict__ s
 }
 
 // Reverse of the grid update: (Pbar, mbar) from vbar.
-__global__ void dk_grid_adj(DiffParams dp, int64_t nodes, float dt, const float4* __restrict__ Pm,
-                            const float4* __restrict__ vbar, float4* __restrict__ Pmbar)
+__global__ void dk_grid_adj(DiffParams dp, int64_t nodes, float dt, const double* __restrict__ Pm,
+                            const double* __restrict__ vbar, float4* __restrict__ Pmbar)
 {
     int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= nodes)
         return;
-    float4 g = Pm[id];
+    const double2 pa = reinterpret_cast<const double2*>(Pm)[2 * id], pq = reinterpret_cast<const double2*>(Pm)[2 * id + 1];
+    const double P[3] = {pa.x, pa.y, pq.x}, m = pq.y;
     float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g.w > 0.0f) {
-        float4 vb = vbar[id];
+    if (m > 0.0) {
+        const double2 ba = reinterpret_cast<const double2*>(vbar)[2 * id], bb = reinterpret_cast<const double2*>(vbar)[2 * id + 1];
         int c[3] = {(int)(id % dp.res[0]), (int)((id / dp.res[0]) % dp.res[1]), (int)(id / ((int64_t)dp.res[0] * dp.res[1]))};
-        float P[3] = {g.x, g.y, g.z};
-        float b[3] = {vb.x, vb.y, vb.z};
-        float keep[3] = {1.f, 1.f, 1.f};
+        const double b[3] = {ba.x, ba.y, bb.x};
+        double keep[3] = {1.0, 1.0, 1.0};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             bool low = c[a] < dp.wall, high = c[a] >= dp.res[a] - dp.wall;
-            float vfree = P[a] / g.w + dt * dp.g[a];
+            double vfree = P[a] / m + (double)(dt * dp.g[a]);   // as dk_grid computes it
             if (dp.boundary == MPM_STICKY) {
                 if (low || high)
-                    keep[0] = keep[1] = keep[2] = 0.f;
-            } else if ((low && vfree < 0.f) || (high && vfree > 0.f)) {
-                keep[a] = 0.f;
+                    keep[0] = keep[1] = keep[2] = 0.0;
+            } else if ((low && vfree < 0.0) || (high && vfree > 0.0)) {
+                keep[a] = 0.0;
             }
         }
-        float im = 1.0f / g.w;
-        float mb = 0.f;
-        float pb[3];
+        const double im = 1.0 / m;
+        double mb = 0.0;
+        double pb[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float v = keep[a] * b[a];
+            double v = keep[a] * b[a];
             pb[a] = v * im;
             mb -= v * P[a] * im * im;
         }
-        out = make_float4(pb[0], pb[1], pb[2], mb);
+        out = make_float4((float)pb[0], (float)pb[1], (float)pb[2], (float)mb);
     }
     Pmbar[id] = out;
 }
@@ -571,7 +580,8 @@ struct mpm_diff {
     mpm_allocator alloc{};
     bool have_alloc = false;
     float* vol = nullptr;
-    float4 *Pm = nullptr, *vel = nullptr, *vbar = nullptr, *Pmbar = nullptr;
+    double *Pm = nullptr, *vbar = nullptr;   // 4 doubles per node
+    float4 *vel = nullptr, *Pmbar = nullptr;
     uint32_t* err = nullptr;
     int64_t launches = 0;
 };
@@ -597,7 +607,7 @@ static void dd_free(mpm_diff* d, void* p, size_t b)
 static void forward_grid(mpm_diff* d, float dt, const float* E, const float* s)
 {
     cudaStream_t st = d->stream;
-    cudaMemsetAsync(d->Pm, 0, (size_t)d->nodes * 16, st);
+    cudaMemsetAsync(d->Pm, 0, (size_t)d->nodes * 32, st);
     dk_p2g<<<dblk(d->n, kDT), kDT, 0, st>>>(d->dp, d->n, s, E, d->vol, dt, d->Pm, d->err);
     dk_grid<<<dblk(d->nodes, 256), 256, 0, st>>>(d->dp, d->nodes, dt, d->Pm, d->vel);
     d->launches += 2;
@@ -638,9 +648,9 @@ mpm_status mpm_diff_create(const mpm_config* cfg, float nu, float rho, int64_t n
     d->nodes = (int64_t)cfg->res[0] * cfg->res[1] * cfg->res[2];
     size_t gb = (size_t)d->nodes * 16;
     d->vol = (float*)dd_alloc(d, (size_t)n * 4);
-    d->Pm = (float4*)dd_alloc(d, gb);
+    d->Pm = (double*)dd_alloc(d, 2 * gb);
     d->vel = (float4*)dd_alloc(d, gb);
-    d->vbar = (float4*)dd_alloc(d, gb);
+    d->vbar = (double*)dd_alloc(d, 2 * gb);
     d->Pmbar = (float4*)dd_alloc(d, gb);
     d->err = (uint32_t*)dd_alloc(d, 256);
     if (!d->vol || !d->Pm || !d->vel || !d->vbar || !d->Pmbar || !d->err) {
@@ -689,7 +699,7 @@ mpm_status mpm_diff_adjoint(mpm_diff* d, float dt, const float* E, const float* 
         return MPM_EINVAL;
     cudaStream_t st = d->stream;
     forward_grid(d, dt, E, s_in);
-    cudaMemsetAsync(d->vbar, 0, (size_t)d->nodes * 16, st);
+    cudaMemsetAsync(d->vbar, 0, (size_t)d->nodes * 32, st);
     dk_g2p_adj<<<dblk(d->n, kDT), kDT, 0, st>>>(d->dp, d->n, s_in, d->vel, g_out, dt, g_in, d->vbar);
     dk_grid_adj<<<dblk(d->nodes, 256), 256, 0, st>>>(d->dp, d->nodes, dt, d->Pm, d->vbar, d->Pmbar);
     dk_p2g_adj<<<dblk(d->n, kDT), kDT, 0, st>>>(d->dp, d->n, s_in, E, d->vol, dt, d->Pmbar, g_in, gE);
@@ -715,9 +725,9 @@ void mpm_diff_destroy(mpm_diff* d)
     cudaStreamSynchronize(d->stream);
     size_t gb = (size_t)d->nodes * 16;
     dd_free(d, d->vol, (size_t)d->n * 4);
-    dd_free(d, d->Pm, gb);
+    dd_free(d, d->Pm, 2 * gb);
     dd_free(d, d->vel, gb);
-    dd_free(d, d->vbar, gb);
+    dd_free(d, d->vbar, 2 * gb);
     dd_free(d, d->Pmbar, gb);
     dd_free(d, d->err, 256);
     cudaStreamSynchronize(d->stream);

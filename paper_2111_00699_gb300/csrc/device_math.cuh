@@ -161,7 +161,7 @@ __device__ __forceinline__ void svd_h(const float* H, SVDH& d)
     for (int i = 0; i < 9; ++i)
         d.V[i] = (i % 4 == 0) ? 1.0f : 0.0f;
 #pragma unroll
-    for (int sweep = 0; sweep < 4; ++sweep) {
+    for (int sweep = 0; sweep < 3; ++sweep) {
         jacobi_pair(e00, e11, e01, e02, e12, d.V, 0, 1);
         jacobi_pair(e00, e22, e02, e01, e12, d.V, 0, 2);
         jacobi_pair(e11, e22, e12, e01, e02, d.V, 1, 2);

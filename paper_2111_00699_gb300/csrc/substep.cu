@@ -429,7 +429,7 @@ __device__ __forceinline__ void acc_flush(const GridView& gv, float4* target, co
 }
 
 template <int K, bool kSmem>
-__global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 1) k_p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+__global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 3) k_p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
                                                                 float dt, uint32_t* __restrict__ err)
 {
     extern __shared__ float4 sacc[];
@@ -1255,7 +1255,7 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p2g(SimParams sp, PartVi
 // cell per substep, so the cell sort still groups them), flushing 27 float4
 // reductions into gv.nxt per run.
 template <int K, bool kSmem>
-__global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 1) k_g2p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
+__global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 2) k_g2p2g_chunk(SimParams sp, PartView pv, GridView gv, int64_t n,
                                                                   float dt, uint32_t* __restrict__ flags,
                                                                   uint32_t* __restrict__ err)
 {
