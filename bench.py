@@ -258,6 +258,76 @@ def bench_fountain(substeps=3600):
             "ms_per_frame": ms / substeps * frame, "particles_end": n_end, "rebuilds": st["rebuilds"]}
 
 
+def bench_small_elastic(substeps=100, reps=5):
+    """The small elastic case: 8,192 particles uniform in [0.4, 0.6]^3, 64^3,
+    fixed-corotated E 1e4, nu 0.2, rho 1, dt 1e-4, sticky walls, 100
+    substeps.  The whole state fits in L2, so the figure is microseconds per
+    substep (launch and latency bound), for the separate phases and for the
+    fused G2P2G transfer (the paper's choice below ~100K particles)."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x = torch.from_numpy(scenes.cube_uniform(0, 8192, 0.4, 0.6)).cuda()
+    vol = torch.full((8192,), 0.008 / 8192, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {"workload": "small elastic, 8192 particles, 64^3, dt=1e-4, 100 substeps", "unit": "us/substep"}
+    for fused in (False, True):
+        best = None
+        for _ in range(reps):
+            with mpm.Simulator(64, 1 / 64, [mpm.material(mpm.ELASTIC, E=1e4, nu=0.2, rho=1.0)],
+                               stream=stream, p2g_variant=3, g2p_variant=0, g2p2g=fused) as sim:
+                sim.add_particles(x, vol=vol)
+                sim.run(3, 1e-4)
+                ms = _events_time(stream, lambda: sim.run(substeps, 1e-4))
+                sim.sync()
+            best = ms if best is None else min(best, ms)
+        out["g2p2g" if fused else "separate"] = 1e3 * best / substeps
+    out["value"] = min(out["separate"], out["g2p2g"])
+    out["particle_substeps_per_s"] = 8192 / (out["value"] * 1e-6)
+    return out
+
+
+def bench_ablations(substeps=100):
+    """The paper's single-GPU ablations (Sec. 6), on the snow-blocks scene
+    with the particles added in a shuffled order: free-zone rebuilds with a
+    full sort (the default) against a rebuild before every substep, against
+    no sort at all, and the P2G scatter forms (float4 reductions per node,
+    a shared-memory node tile, register runs).  ms per substep over
+    `substeps` substeps after 20 warm-up substeps, fresh context each."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x, _ = scenes.snow_blocks()
+    x = x[np.random.default_rng(11).permutation(len(x))]
+    xs = torch.from_numpy(x).cuda()
+    mat = mpm.material(mpm.SNOW, **SNOW)
+    stream = torch.cuda.Stream()
+
+    def timed(p2g=3, g2p=4, no_sort=False, rebuild_every=False):
+        with mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream, p2g_variant=p2g, g2p_variant=g2p,
+                           no_sort=no_sort) as sim:
+            sim.add_particles(xs)
+
+            def run(k):
+                if not rebuild_every:
+                    return sim.run(k, DT)
+                for _ in range(k):
+                    sim.rebuild()
+                    sim.substep(DT)
+            run(20)
+            ms = _events_time(stream, lambda: run(substeps))
+            sim.sync()
+        return ms / substeps
+
+    out = {"workload": "snow blocks 1340960 particles, shuffled insertion order, %d substeps each" % substeps,
+           "unit": "ms/substep"}
+    out["free_zone_full_sort"] = timed()
+    out["rebuild_every_substep"] = timed(rebuild_every=True)
+    out["no_sort"] = timed(no_sort=True)
+    out["p2g_float4_reductions_per_node"] = timed(p2g=0)
+    out["p2g_shared_memory_node_tile"] = timed(p2g=2)
+    out["p2g_register_runs_of_4"] = out["free_zone_full_sort"]
+    return out
+
+
 def bench_sand(substeps=1000):
     """Drucker-Prager sand (phi = 30 deg), 4 random boxes, ~500K particles at
     8 per cell, 128^3, dt 1e-4."""
@@ -573,7 +643,8 @@ def main():
     if not args.no_workloads and world == 1:
         workloads = {}
         for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand),
-                         ("adjoint", bench_adjoint)):
+                         ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
+                         ("ablations", bench_ablations)):
             try:
                 workloads[name] = fn()
             except Exception as exc:   # report, do not lose the main line

@@ -99,7 +99,11 @@ typedef struct {
                               in shared memory per CTA, 4 thread per particle at 64
                               registers, 5 the same with each CTA's particle inputs and
                               2x2x2-block grid tile staged by bulk asynchronous copies */
-    int32_t reserved[5];
+    int32_t no_sort;       /* ablation (Sec. 6 sorting study): 1 = a rebuild maps the blocks
+                              but leaves the particles in their storage order (no sort, no
+                              permutation; mpm_read_order then returns MPM_EINVAL); results
+                              are the same up to floating-point summation order.  0: sort */
+    int32_t reserved[4];
 } mpm_config;
 
 /* Device memory provider.  alloc returns device memory usable on `stream`

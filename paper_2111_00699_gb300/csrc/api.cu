@@ -325,19 +325,21 @@ mpm_status rebuild(mpm_ctx* ctx)
     cudaStream_t s = ctx->stream;
     int64_t n = ctx->n;
     const SimParams& sp = ctx->sp;
+    const bool sort = !ctx->cfg.no_sort;
     if (n > 0) {
         launch_keys(sp, ctx->pv[ctx->cur], n, ctx->keys, ctx->vals, ctx->dstat, s);
         ctx->launches += 1;
-        CK(radix_sort_pairs(ctx->keys, ctx->vals, ctx->skeys, ctx->svals, n, 3 * sp.L + 6, ctx->sort_scr, s,
-                            &ctx->launches));
+        if (sort)
+            CK(radix_sort_pairs(ctx->keys, ctx->vals, ctx->skeys, ctx->svals, n, 3 * sp.L + 6, ctx->sort_scr, s,
+                                &ctx->launches));
     }
     CK(cudaMemsetAsync(ctx->flags, 0, (size_t)ctx->n_slots * 4, s));
-    launch_mark_pblocks(ctx->skeys, n, sp.L, ctx->flags, s);
+    launch_mark_pblocks(sort ? ctx->skeys : ctx->keys, n, sp.L, ctx->flags, s);
     CK(exclusive_scan(ctx->flags, ctx->ranks, ctx->n_slots, ctx->scan_scr, s, &ctx->launches));
     launch_build_table(ctx->flags, ctx->ranks, ctx->n_slots, ctx->table, ctx->pslot,
                        (int32_t*)&ctx->dstat[1 + kRing], s);
     ctx->launches += 2;
-    if (n > 0) {
+    if (n > 0 && sort) {
         launch_permute(ctx->pv[ctx->cur], ctx->pv[1 - ctx->cur], ctx->svals, n, s);
         ctx->launches += 1;
         ctx->cur = 1 - ctx->cur;
@@ -371,7 +373,7 @@ mpm_status rebuild(mpm_ctx* ctx)
     }
     ctx->gcur = 0;
     ctx->primed = false;
-    ctx->keys_valid = true;
+    ctx->keys_valid = sort;
     ctx->need_rebuild = false;
     ctx->last_rebuild = ctx->step;
     ctx->rebuilds += 1;
@@ -412,6 +414,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         maxres = cfg->res[a] > maxres ? cfg->res[a] : maxres;
     }
     if (cfg->use_g2p2g != 0 && cfg->use_g2p2g != 1)
+        return MPM_EINVAL;
+    if (cfg->no_sort != 0 && cfg->no_sort != 1)
         return MPM_EINVAL;
     if (cfg->p2g_variant < 0 || cfg->p2g_variant >= kP2GVariants)
         return MPM_EINVAL;
@@ -868,6 +872,8 @@ mpm_status mpm_read_order(mpm_ctx* ctx, uint32_t* keys, int32_t* ids, int on_dev
 {
     if (!ctx)
         return MPM_EINVAL;
+    if (ctx->cfg.no_sort)
+        return fail(ctx, MPM_EINVAL, "mpm_read_order: the context does not sort (no_sort = 1)");
     if (!ctx->keys_valid)
         return fail(ctx, MPM_EINVAL, "mpm_read_order: no rebuild since the particles last changed");
     size_t bytes = (size_t)ctx->n * 4;
