@@ -279,6 +279,18 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
  * between substeps (mpm_config.use_g2p2g). */
 mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on);
 
+/* Replay the separate substep (flag clear, P2G, grid update, G2P, flag
+ * copy) from CUDA graphs (on = 1): one graph per flag-ring slot and current
+ * grid buffer, captured on first use and dropped at every rebuild, particle
+ * addition, variant change or change of dt.  Removes the launch gaps between
+ * the phases, which dominate small scenes.  The paper launches kernels
+ * directly; this is a GB300-side choice with the same results.  EINVAL if
+ * the context runs on the legacy default stream (it cannot be captured).
+ * Not used while profiling is on or in fused G2P2G mode.
+ * mpm_graph_launches returns the number of graph replays so far. */
+mpm_status mpm_use_graphs(mpm_ctx* ctx, int on);
+int64_t mpm_graph_launches(const mpm_ctx* ctx);
+
 /* Per-phase timing with CUDA events on the context's stream.  Phase ids:
  * 0 rebuild, 1 P2G, 2 grid update, 3 G2P.  mpm_profile_read syncs and
  * writes total milliseconds and launch counts per phase since the last

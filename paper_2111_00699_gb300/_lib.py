@@ -81,6 +81,8 @@ _PROTOS = {
     "mpm_set_p2g_variant": (I, [P, I]),
     "mpm_set_g2p_variant": (I, [P, I]),
     "mpm_set_g2p2g": (I, [P, I]),
+    "mpm_use_graphs": (I, [P, I]),
+    "mpm_graph_launches": (I64, [P]),
     "mpm_profile_enable": (I, [P, I]),
     "mpm_profile_read": (I, [P, P, P, I]),
     "mpm_radix_sort_pairs": (I, [P, P, P, P, I64, I, P, P, P]),

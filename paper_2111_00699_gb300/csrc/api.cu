@@ -96,6 +96,15 @@ struct mpm_ctx {
     int64_t rebuilds = 0, launches = 0;
     std::string err;
 
+    // CUDA-graph replay of the separate substep (memset, P2G, grid update,
+    // G2P, flag copy): one graph per (flag slot, current grid buffer); every
+    // pointer and size a graph captures is fixed until the next rebuild,
+    // particle addition, variant or dt change, which drop them all
+    bool graphs = false;
+    cudaGraphExec_t gexec[2 * kRing] = {};
+    float graph_dt = 0.0f;
+    int64_t graph_launches = 0;
+
     // host mirror of the block table (refreshed at every rebuild), used to
     // decide on the host whether emitted particles land in mapped blocks
     int32_t* htable = nullptr;
@@ -317,9 +326,40 @@ GridView grid_view(mpm_ctx* ctx)
     return g;
 }
 
+// One separate substep on the context's stream: clear the flag slot, P2G,
+// grid update, G2P, copy the flags to the pinned ring.
+void enqueue_separate(mpm_ctx* ctx, float dt, int slot)
+{
+    cudaStream_t s = ctx->stream;
+    cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s);
+    GridView gv = grid_view(ctx);
+    const PartView& pv = ctx->pv[ctx->cur];
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    prof_begin(ctx, e0);
+    launch_p2g(ctx->sp, pv, gv, ctx->n, dt, ctx->dstat, ctx->cfg.p2g_variant, s);
+    prof_end(ctx, 1, e0);
+    prof_begin(ctx, e1);
+    launch_grid_update(ctx->sp, gv, dt, s);
+    prof_end(ctx, 2, e1);
+    prof_begin(ctx, e2);
+    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.g2p_variant, s);
+    prof_end(ctx, 3, e2);
+    cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s);
+}
+
+void drop_graphs(mpm_ctx* ctx)
+{
+    for (auto& g : ctx->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
 // Rebuild-mapping + full sort (Sec. 4.2.1, Sec. 4.2.2).
 mpm_status rebuild(mpm_ctx* ctx)
 {
+    drop_graphs(ctx);
     cudaEvent_t pa = nullptr;
     prof_begin(ctx, pa);
     cudaStream_t s = ctx->stream;
@@ -497,11 +537,29 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
     return MPM_OK;
 }
 
+mpm_status mpm_use_graphs(mpm_ctx* ctx, int on)
+{
+    if (!ctx || (on != 0 && on != 1))
+        return MPM_EINVAL;
+    if (on && ctx->stream == nullptr)
+        return fail(ctx, MPM_EINVAL, "CUDA graphs need a stream other than the legacy default stream");
+    if (!on)
+        drop_graphs(ctx);
+    ctx->graphs = on != 0;
+    return MPM_OK;
+}
+
+int64_t mpm_graph_launches(const mpm_ctx* ctx)
+{
+    return ctx ? ctx->graph_launches : 0;
+}
+
 void mpm_destroy(mpm_ctx* ctx)
 {
     if (!ctx)
         return;
     cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
     for (auto& r : ctx->prof_recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -582,6 +640,7 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaGetLastError());
     ctx->n += n;
+    drop_graphs(ctx);
     ctx->need_rebuild = true;
     ctx->primed = false;
     ctx->keys_valid = false;
@@ -711,6 +770,7 @@ mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const flo
     ctx->launches += 1;
     CK(cudaGetLastError());
     ctx->n += n;
+    drop_graphs(ctx);
     ctx->emitted += n;
     ctx->keys_valid = false;
     ctx->primed = false;   // the new particles are not in the fused path's momentum
@@ -745,21 +805,27 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     int slot = (int)(ctx->step % kRing);
     if (ctx->cfg.use_g2p2g)
         return substep_fused(ctx, dt, slot);
-    CK(cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s));
-    GridView gv = grid_view(ctx);
-    const PartView& pv = ctx->pv[ctx->cur];
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    prof_begin(ctx, e0);
-    launch_p2g(ctx->sp, pv, gv, ctx->n, dt, ctx->dstat, ctx->cfg.p2g_variant, s);
-    prof_end(ctx, 1, e0);
-    prof_begin(ctx, e1);
-    launch_grid_update(ctx->sp, gv, dt, s);
-    prof_end(ctx, 2, e1);
-    prof_begin(ctx, e2);
-    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.g2p_variant, s);
-    prof_end(ctx, 3, e2);
+    if (ctx->graphs && !ctx->prof) {
+        if (dt != ctx->graph_dt) {
+            drop_graphs(ctx);
+            ctx->graph_dt = dt;
+        }
+        const int gi = 2 * slot + ctx->gcur;
+        if (!ctx->gexec[gi]) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            enqueue_separate(ctx, dt, slot);
+            CK(cudaStreamEndCapture(s, &graph));
+            cudaError_t e = cudaGraphInstantiate(&ctx->gexec[gi], graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e);
+        }
+        CK(cudaGraphLaunch(ctx->gexec[gi], s));
+        ctx->graph_launches += 1;
+    } else {
+        enqueue_separate(ctx, dt, slot);
+    }
     ctx->launches += 3;
-    CK(cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(ctx->ev[slot], s));
     CK(cudaGetLastError());
     ctx->gcur = 1 - ctx->gcur;
@@ -944,6 +1010,7 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant)
     if (!ctx || variant < 0 || variant >= kP2GVariants)
         return MPM_EINVAL;
     ctx->cfg.p2g_variant = variant;
+    drop_graphs(ctx);
     return MPM_OK;
 }
 
@@ -971,6 +1038,7 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant)
     if (!ctx || variant < 0 || variant >= kG2PVariants)
         return MPM_EINVAL;
     ctx->cfg.g2p_variant = variant;
+    drop_graphs(ctx);
     return MPM_OK;
 }
 

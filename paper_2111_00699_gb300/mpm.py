@@ -50,7 +50,7 @@ class Simulator:
     def __init__(self, res, dx, materials, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0),
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
                  device=None, p2g_variant: int = 3, g2p_variant: int = 0, g2p2g: bool = False,
-                 no_sort: bool = False):
+                 no_sort: bool = False, graphs: bool = False):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -96,6 +96,8 @@ class Simulator:
                                 ctypes.byref(self._alloc) if self._alloc is not None else None,
                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._ctx))
         _check(st)
+        if graphs:
+            self.use_graphs(True)
 
     # -- lifecycle --------------------------------------------------------
     def close(self):
@@ -222,6 +224,14 @@ class Simulator:
 
     def set_g2p2g(self, on: bool):
         _check(load().mpm_set_g2p2g(self._ctx, 1 if on else 0), self._ctx)
+
+    def use_graphs(self, on: bool = True):
+        """Replay the separate substep from CUDA graphs (needs a non-default stream)."""
+        _check(load().mpm_use_graphs(self._ctx, 1 if on else 0), self._ctx)
+
+    @property
+    def graph_launches(self) -> int:
+        return int(load().mpm_graph_launches(self._ctx))
 
     def set_g2p_variant(self, variant: int):
         _check(load().mpm_set_g2p_variant(self._ctx, int(variant)), self._ctx)

@@ -530,6 +530,38 @@ def test_sand_blocks_full_size_parity(M):
 
 # ------------------------------------------------------------ fused G2P2G (a6')
 
+def test_graph_replay_matches_oracle(M):
+    """Separate substeps replayed from CUDA graphs: parity through rebuilds
+    (a fast block crosses many cells), a dt change and a particle addition,
+    each of which drops the graphs; replays actually happen."""
+    x = scenes.cube_uniform(4, 3000, 0.3, 0.4)
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    v = np.tile(np.array([30.0, 20.0, 10.0], np.float32), (len(x), 1))
+    vol = (1 / 64) ** 3 / 8
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    stream = torch.cuda.Stream()
+    s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, stream=stream, graphs=True) as sim:
+        sim.add_particles(x, v=v)
+        for steps, dt in ((30, 1e-4), (20, 7e-5)):
+            g = _run_both(M, sim, [om], s, steps, dt, cfg)
+            assert linf(g["x"], s.x) <= 1e-4
+            assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        x2 = scenes.cube_uniform(5, 500, 0.6, 0.65)
+        sim.add_particles(x2)
+        s = orc.State(np.concatenate([s.x, x2.astype(np.float64)]), np.concatenate([s.v, np.zeros((500, 3))]),
+                      np.concatenate([s.C, np.zeros((500, 3, 3))]), np.concatenate([s.F, np.tile(np.eye(3), (500, 1, 1))]),
+                      np.concatenate([s.Jp, np.ones(500)]), np.concatenate([s.vol, np.full(500, vol)]),
+                      np.concatenate([s.mat, np.zeros(500, s.mat.dtype)]))
+        g = _run_both(M, sim, [om], s, 20, 1e-4, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        assert sim.graph_launches >= 50
+        assert sim.stats()["rebuilds"] >= 3
+    with pytest.raises(RuntimeError):
+        M.Simulator(64, 1 / 64, [gm], stream=torch.cuda.default_stream(), graphs=True)
+
+
 def test_no_sort_ablation_matches_oracle(M):
     """With no_sort = 1 the rebuild maps blocks but leaves the particles in
     their (here shuffled) storage order: the substeps are the same up to
