@@ -108,3 +108,28 @@ def test_batched_rejects_bad_input(M):
         with pytest.raises(M.MpmError) as e:
             bsim.substep(1e-4)
         assert e.value.status == 4
+
+
+def test_batched_full_size_sampled_scenes(M):
+    """The full batched workload as bench.py times it (256 scenes, 4.8M
+    particles, seed 4, CUDA graphs, P2G runs of 8), 10 substeps from rest;
+    two scenes per material (the smallest and the largest) are compared with
+    the oracle run on that scene alone."""
+    bs = scenes.batched_scenes(4)
+    assert len(bs) == 256
+    vs = [np.zeros((len(b["x"]), 3), np.float32) for b in bs]
+    out, st, dts = _run_batch(M, bs, vs, 10, True, 8)
+    assert st["graph_launches"] == 10
+    _, om = _mats(M)
+    picks = []
+    for mat in range(4):
+        ids = [i for i, b in enumerate(bs) if b["material"] == mat]
+        ids.sort(key=lambda i: len(bs[i]["x"]))
+        picks += [ids[0], ids[-1]]
+    for i in picks:
+        b = bs[i]
+        s = _oracle_run(b, b["x"], vs[i], om[b["material"]], float(dts[i]), 10)
+        g = out[i]
+        assert np.abs(g["x"] - s.x).max() <= 1e-4, i
+        assert np.abs(g["v"] - s.v).max() <= 1e-4 * np.abs(s.v).max(), i
+        assert np.abs(g["Jp"] - s.Jp).max() <= 1e-4, i

@@ -309,21 +309,28 @@ def test_substeps_materials(M, kind):
     assert linf(g["Jp"], s.Jp) <= 1e-4
 
 
-def test_one_substep_snow_full_size(M):
+def test_ten_substeps_snow_full_size_bench_configuration(M):
+    """The 1.34M-particle snow scene in the launch configuration bench.py
+    times (register-run P2G, 64-register G2P, CUDA-graph replay on a side
+    stream): x and v after 10 substeps within 1e-4 of the FP64 oracle."""
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
     gm, om = mats_pair(M, M.SNOW, E=1.4e5, nu=0.2, rho=400.0)
     cfg = orc.config(256, 1 / 256, orc.SLIP)
     rng = np.random.default_rng(9)
     v = (0.2 * rng.normal(size=(len(x), 3))).astype(np.float32)
-    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP) as sim:
+    stream = torch.cuda.Stream()
+    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP, stream=stream, p2g_variant=3, g2p_variant=4,
+                     graphs=True) as sim:
         sim.add_particles(torch.from_numpy(x).cuda(), v=torch.from_numpy(v).cuda())
         s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
-        g = _run_both(M, sim, [om], s, 1, 5e-5, cfg)
+        g = _run_both(M, sim, [om], s, 10, 5e-5, cfg)
+        assert sim.graph_launches >= 8
     assert linf(g["x"], s.x) <= 1e-4
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
     assert linf(g["C"], s.C) <= 1e-4 * np.abs(s.C).max()
     assert linf(g["F"], s.F) <= 1e-5
+    assert linf(g["Jp"], s.Jp) <= 1e-5
 
 
 def test_rebuild_is_triggered_and_parity_holds(M):
@@ -507,6 +514,39 @@ def test_fountain_emission_parity(M):
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
     assert linf(g["Jp"], s.Jp) <= 1e-4
     assert stats["rebuilds"] <= steps // 4, stats
+
+
+def test_fountain_full_budget_properties(M):
+    """The whole fountain run bench.py times (3,600 emitting substeps up to
+    144,000 particles, 128^3): too long for the oracle, so properties that
+    hold at any size -- every emitted particle is there, in insertion order,
+    finite and inside the walls, and P2G of the final state conserves mass
+    to 1e-6."""
+    res, dt, steps = 128, 1e-4, 3600
+    vol = (1 / res) ** 3 / 8
+    gm = M.material(M.FLUID, E=1e4, gamma=7.0, rho=1000.0)
+    first = None
+    total = 0
+    stream = torch.cuda.Stream()
+    with M.Simulator(res, 1 / res, [gm], boundary=M.SLIP, stream=stream) as sim:
+        for k in range(steps):
+            xe, ve = scenes.fountain_batch(2, k, dt, vol)
+            if first is None:
+                first = xe.copy()
+            total += len(xe)
+            sim.emit_particles(xe, v=ve)
+            sim.substep(dt)
+        st = sim.read_state()
+        g = sim.debug_p2g(dt).double()
+        n = sim.n
+    assert n == total == 144000
+    x = st["x"].double().cpu().numpy()
+    assert np.isfinite(x).all() and np.isfinite(st["v"].cpu().numpy()).all()
+    assert x.min() > 3 / res and x.max() < 1 - 3 / res
+    # insertion order: the first batch rose from the inlet, still above it
+    assert np.abs(x[: len(first), [0, 2]] - 0.5).max() < 0.45
+    mass = 1000.0 * vol * n
+    assert abs(float(g[..., 0].sum()) - mass) <= 1e-6 * mass
 
 
 def test_sand_blocks_full_size_parity(M):
