@@ -186,7 +186,7 @@ typedef struct {
 } mpm_scene_desc;
 
 /* n_scenes <= 65535 scenes and n_mats <= 255 materials are copied.  Fails
- * with MPM_ECAPACITY if the scenes' block slots need more than 26 bits. */
+ * with MPM_ECAPACITY if the scenes' block slots need more than 25 bits. */
 mpm_status mpm_batch_create(int n_scenes, const mpm_scene_desc* scenes, const mpm_material* mats, int n_mats,
                             const mpm_allocator* allocator, void* cuda_stream, mpm_batch** out);
 /* Host arrays (x, v: n x 3; vol0: n, NULL = dx^3/8; v NULL = 0), before the

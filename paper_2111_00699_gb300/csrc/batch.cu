@@ -80,6 +80,26 @@ __device__ __forceinline__ int64_t node_addr(const SceneParams& sc, int x, int y
     return (int64_t)slot * 64 + (x & 3) + 4 * (y & 3) + 16 * (z & 3);
 }
 
+// Node indices of the stencil at base b in a scene's slot range: the 8
+// candidate blocks B + {0,1}^3 (B = b >> 2) sit at slot_base + Morton(B + d);
+// the +1 per axis is done on the dilated Morton bits.
+__device__ __forceinline__ StencilIndex scene_stencil_index(const SceneParams& sc, const int* b)
+{
+    constexpr uint32_t kMx = 0x09249249u, kMy = kMx << 1, kMz = kMx << 2;
+    const uint32_t sx0 = spread3((uint32_t)b[0] >> 2), sy0 = spread3((uint32_t)b[1] >> 2) << 1,
+                   sz0 = spread3((uint32_t)b[2] >> 2) << 2;
+    const uint32_t sx[2] = {sx0, ((sx0 | ~kMx) + 1u) & kMx}, sy[2] = {sy0, ((sy0 | ~kMy) + 1u) & kMy},
+                   sz[2] = {sz0, ((sz0 | ~kMz) + 1u) & kMz};
+    StencilIndex si;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        si.pb64[c] = (int)((sc.slot_base + (sx[c & 1] | sy[(c >> 1) & 1] | sz[c >> 2])) * 64u);
+    si.bx = b[0] & 3;
+    si.by = b[1] & 3;
+    si.bz = b[2] & 3;
+    return si;
+}
+
 __device__ __forceinline__ bool b_stencil_mapped(const SceneParams& sc, const BatchView& bv, const int* lo,
                                                  const int* hi)
 {
@@ -396,7 +416,7 @@ __global__ void bk_active_scene(const SceneParams* __restrict__ scenes, int n_sc
     ascene[i] = lo;
 }
 
-__global__ void __launch_bounds__(kT) bk_g2p(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ flags,
+__global__ void __launch_bounds__(kT, 8) bk_g2p(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ flags,
                                               uint32_t* __restrict__ err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -422,29 +442,12 @@ __global__ void __launch_bounds__(kT) bk_g2p(BatchView bv, PartView pv, int64_t 
         atomicOr(err, ST_MISSED);
         return;
     }
-    float vp[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float dz = (float)k - f[2];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float dy = (float)j - f[1];
-            float wyz = w[1][j] * w[2][k];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float dxo = (float)i - f[0];
-                float wt = w[0][i] * wyz;
-                float4 g = bv.cur[node_addr(sc, b[0] + i, b[1] + j, b[2] + k)];
-                float gx = wt * g.x, gy = wt * g.y, gz = wt * g.z;
-                vp[0] += gx;
-                vp[1] += gy;
-                vp[2] += gz;
-                Bm[0] += gx * dxo; Bm[1] += gx * dy; Bm[2] += gx * dz;
-                Bm[3] += gy * dxo; Bm[4] += gy * dy; Bm[5] += gy * dz;
-                Bm[6] += gz * dxo; Bm[7] += gz * dy; Bm[8] += gz * dz;
-            }
-        }
-    }
+    const StencilIndex si = scene_stencil_index(sc, b);
+    float vp[3], Bm[9];
+    g2p_accumulate(f, w, [&](int i, int j, int k) {
+        const float4 g = bv.cur[si(i, j, k)];
+        return make_float3(g.x, g.y, g.z);
+    }, vp, Bm);
     float C[9];
     const float c4 = 4.0f * sc.inv_dx;
     const float dt = sc.dt;
@@ -819,7 +822,7 @@ mpm_status mpm_batch_create(int n_scenes, const mpm_scene_desc* scenes, const mp
     int bits = 0;
     while (((uint64_t)1 << bits) < slots)
         ++bits;
-    if (bits + 6 > 32) {
+    if (bits + 6 > 31) {   // sort keys (slot << 6 | cell) and node indices (slot * 64) stay below 2^31
         delete b;
         return MPM_ECAPACITY;
     }

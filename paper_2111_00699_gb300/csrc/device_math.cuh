@@ -54,6 +54,77 @@ __device__ __forceinline__ void bspline(float f, float w[3])
     w[2] = 0.5f * c * c;
 }
 
+// ---- stencil addressing and the G2P gather ------------------------------------
+// Grid index of the 27 nodes of a stencil at base b, from the (up to) 8
+// blocks stencil_blocks returned.  Node (i, j, k) lies in candidate block
+// (dx, dy, dz) with dx = ((b_x & 3) + i) >> 2 and so on; the block is picked
+// by one select per axis (z, then y, then x), so that after unrolling a row
+// of 3 nodes costs 2 selects and each node 1 more.
+struct StencilIndex {
+    int pb64[8];   // candidate block slot * 64 (0 where unused)
+    int bx, by, bz;
+
+    __device__ __forceinline__ int operator()(int i, int j, int k) const
+    {
+        const int nx = bx + i, ny = by + j, nz = bz + k;
+        const bool dz = nz >= 4, dy = ny >= 4, dx = nx >= 4;
+        const int q0 = dz ? pb64[4] : pb64[0], q1 = dz ? pb64[5] : pb64[1];
+        const int q2 = dz ? pb64[6] : pb64[2], q3 = dz ? pb64[7] : pb64[3];
+        const int r0 = dy ? q2 : q0, r1 = dy ? q3 : q1;
+        return (dx ? r1 : r0) + (nx & 3) + 4 * (ny & 3) + 16 * (nz & 3);
+    }
+};
+
+// vp = sum w v_i, Bm = sum w v_i (node - f)^T over the 27 stencil nodes,
+// node velocities given by vel(i, j, k) -> float3.  With centred offsets
+// e = (i, j, k) - 1 in {-1, 0, 1}, sum w v (node - f)^T = sum w v e^T - vp (f - 1)^T,
+// and both weighted sums factor axis by axis: each row of 3 nodes along x is
+// reduced first (its sum and its e_x moment), then the rows along y, then z.
+template <class Vel>
+__device__ __forceinline__ void g2p_accumulate(const float* f, const float (*w)[3], Vel vel, float* vp, float* Bm)
+{
+    float M[3][3];   // M[a][d] = sum w v_a e_d
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        vp[a] = 0.0f;
+        M[a][0] = M[a][1] = M[a][2] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float s[3] = {0.f, 0.f, 0.f}, sx[3] = {0.f, 0.f, 0.f}, sy[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float3 g0 = vel(0, j, k), g1 = vel(1, j, k), g2 = vel(2, j, k);
+            const float a0[3] = {w[0][0] * g0.x, w[0][0] * g0.y, w[0][0] * g0.z};
+            const float a2[3] = {w[0][2] * g2.x, w[0][2] * g2.y, w[0][2] * g2.z};
+            const float g1v[3] = {g1.x, g1.y, g1.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float r = a0[a] + w[0][1] * g1v[a] + a2[a];   // row sum
+                const float rx = a2[a] - a0[a];                       // row e_x moment
+                s[a] += w[1][j] * r;
+                sx[a] += w[1][j] * rx;
+                if (j == 0) sy[a] -= w[1][0] * r;
+                if (j == 2) sy[a] += w[1][2] * r;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            vp[a] += w[2][k] * s[a];
+            M[a][0] += w[2][k] * sx[a];
+            M[a][1] += w[2][k] * sy[a];
+            if (k == 0) M[a][2] -= w[2][0] * s[a];
+            if (k == 2) M[a][2] += w[2][2] * s[a];
+        }
+    }
+    const float fm[3] = {f[0] - 1.0f, f[1] - 1.0f, f[2] - 1.0f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            Bm[3 * a + d] = M[a][d] - vp[a] * fm[d];
+}
+
 // ---- 3x3 SVD helpers -------------------------------------------------------------
 // The SVD (svd_h below) diagonalises the symmetric F^T F - I by cyclic Jacobi
 // rotations with exact angles (V and the singular values), as in McAdams et
