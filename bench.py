@@ -38,6 +38,7 @@ UNIT = "particle-substeps/s"
 RES = 256
 DX = 1.0 / RES
 DT = 5e-5
+RESORT_INTERVAL = 64   # window re-sort every 64 substeps (measured: 0.1825 -> 0.1789 ms/substep; 8: 0.193)
 FRAME = 1.0 / 60.0
 SUBSTEPS_PER_FRAME = FRAME / DT            # 333.33
 SNOW = dict(E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0)
@@ -476,7 +477,7 @@ def main():
 
     def fresh_sim(variant=4, gvariant=2):
         sim = mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream, p2g_variant=variant,
-                            g2p_variant=gvariant, graphs=True)
+                            g2p_variant=gvariant, graphs=True, resort_interval=RESORT_INTERVAL)
         sim.add_particles(xs)
         return sim
 

@@ -103,7 +103,12 @@ typedef struct {
                               but leaves the particles in their storage order (no sort, no
                               permutation; mpm_read_order then returns MPM_EINVAL); results
                               are the same up to floating-point summation order.  0: sort */
-    int32_t reserved[4];
+    int32_t resort_interval; /* > 0: every this many substeps between rebuilds, re-order the
+                              particles of each window of 1024 storage slots by their current
+                              (block, cell) key, so that P2G keeps merging runs of particles
+                              in one cell; 0: only the sort at rebuild (Sec. 4.2.2).  Same
+                              results up to floating-point summation order. */
+    int32_t reserved[3];
 } mpm_config;
 
 /* Device memory provider.  alloc returns device memory usable on `stream`

@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
     _fields_ = [("res", ctypes.c_int32 * 3), ("dx", ctypes.c_float), ("boundary", ctypes.c_int32),
                 ("wall", ctypes.c_int32), ("gravity", ctypes.c_float * 3), ("max_particles", ctypes.c_int64),
                 ("use_g2p2g", ctypes.c_int32), ("p2g_variant", ctypes.c_int32), ("g2p_variant", ctypes.c_int32),
-                ("no_sort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("no_sort", ctypes.c_int32), ("resort_interval", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

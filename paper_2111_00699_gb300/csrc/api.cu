@@ -86,7 +86,7 @@ struct mpm_ctx {
     uint32_t* dstat = nullptr;
     uint32_t* hstat = nullptr;  // pinned mirror
     cudaEvent_t ev[kRing] = {};
-    int64_t step = 0, last_rebuild = -1;
+    int64_t step = 0, last_rebuild = -1, last_resort = -1;
     bool need_rebuild = true;
     // fused G2P2G mode: grid[gcur] holds the momentum of the current state
     // (primed); the stress channels are stale after fused substeps
@@ -101,7 +101,7 @@ struct mpm_ctx {
     // pointer and size a graph captures is fixed until the next rebuild,
     // particle addition, variant or dt change, which drop them all
     bool graphs = false;
-    cudaGraphExec_t gexec[2 * kRing] = {};
+    cudaGraphExec_t gexec[4 * kRing] = {};   // by flag slot, current grid buffer, current particle buffer
     float graph_dt = 0.0f;
     int64_t graph_launches = 0;
 
@@ -457,6 +457,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         return MPM_EINVAL;
     if (cfg->no_sort != 0 && cfg->no_sort != 1)
         return MPM_EINVAL;
+    if (cfg->resort_interval < 0)
+        return MPM_EINVAL;
     if (cfg->p2g_variant < 0 || cfg->p2g_variant >= kP2GVariants)
         return MPM_EINVAL;
     if (cfg->g2p_variant < 0 || cfg->g2p_variant >= kG2PVariants)
@@ -803,6 +805,14 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     }
     cudaStream_t s = ctx->stream;
     int slot = (int)(ctx->step % kRing);
+    const int64_t since = ctx->step - (ctx->last_resort > ctx->last_rebuild ? ctx->last_resort : ctx->last_rebuild);
+    if (ctx->cfg.resort_interval > 0 && !ctx->cfg.no_sort && since >= ctx->cfg.resort_interval) {
+        launch_resort_window(ctx->sp, ctx->pv[ctx->cur], ctx->pv[1 - ctx->cur], ctx->n, s);
+        ctx->cur = 1 - ctx->cur;
+        ctx->launches += 1;
+        ctx->keys_valid = false;
+        ctx->last_resort = ctx->step;
+    }
     if (ctx->cfg.use_g2p2g)
         return substep_fused(ctx, dt, slot);
     if (ctx->graphs && !ctx->prof) {
@@ -810,7 +820,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
             drop_graphs(ctx);
             ctx->graph_dt = dt;
         }
-        const int gi = 2 * slot + ctx->gcur;
+        const int gi = 4 * slot + 2 * ctx->gcur + ctx->cur;
         if (!ctx->gexec[gi]) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

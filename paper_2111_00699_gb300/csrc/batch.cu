@@ -74,12 +74,6 @@ __device__ __forceinline__ bool b_in_grid(const SceneParams& sc, const int* b, c
     return ok;
 }
 
-__device__ __forceinline__ int64_t node_addr(const SceneParams& sc, int x, int y, int z)
-{
-    uint32_t slot = sc.slot_base + morton3((uint32_t)x >> 2, (uint32_t)y >> 2, (uint32_t)z >> 2);
-    return (int64_t)slot * 64 + (x & 3) + 4 * (y & 3) + 16 * (z & 3);
-}
-
 // Node indices of the stencil at base b in a scene's slot range: the 8
 // candidate blocks B + {0,1}^3 (B = b >> 2) sit at slot_base + Morton(B + d);
 // the +1 per axis is done on the dilated Morton bits.
@@ -292,13 +286,14 @@ __global__ void __launch_bounds__(kT) bk_p2g(BatchView bv, PartView pv, int64_t 
         if (change) {
             int lo[3] = {cb[0], cb[1], cb[2]}, hi[3] = {cb[0] + 2, cb[1] + 2, cb[2] + 2};
             if (b_stencil_mapped(sc, bv, lo, hi)) {
+                const StencilIndex si = scene_stencil_index(sc, cb);
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
 #pragma unroll
                     for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
                         for (int i = 0; i < 3; ++i)
-                            atomicAdd(&bv.cur[node_addr(sc, cb[0] + i, cb[1] + jj, cb[2] + k)], acc[i + 3 * jj + 9 * k]);
+                            atomicAdd(&bv.cur[si(i, jj, k)], acc[i + 3 * jj + 9 * k]);
             } else {
                 atomicOr(err, ST_MISSED);
             }
@@ -340,13 +335,14 @@ __global__ void __launch_bounds__(kT) bk_p2g(BatchView bv, PartView pv, int64_t 
     if (cs >= 0) {
         int lo[3] = {cb[0], cb[1], cb[2]}, hi[3] = {cb[0] + 2, cb[1] + 2, cb[2] + 2};
         if (b_stencil_mapped(sc, bv, lo, hi)) {
+            const StencilIndex si = scene_stencil_index(sc, cb);
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
-                        atomicAdd(&bv.cur[node_addr(sc, cb[0] + i, cb[1] + jj, cb[2] + k)], acc[i + 3 * jj + 9 * k]);
+                        atomicAdd(&bv.cur[si(i, jj, k)], acc[i + 3 * jj + 9 * k]);
         } else {
             atomicOr(err, ST_MISSED);
         }

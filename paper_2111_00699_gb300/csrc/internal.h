@@ -112,6 +112,8 @@ void launch_mark_pblocks(const uint32_t* skeys, int64_t n, int L, int32_t* flags
 void launch_build_table(const int32_t* flags, const int32_t* ranks, int64_t n_slots, int32_t* table,
                         int32_t* pslot, int32_t* n_pblocks, cudaStream_t s);
 void launch_permute(const PartView& src, const PartView& dst, const int32_t* perm, int64_t n, cudaStream_t s);
+constexpr int kResortWindow = 1024;
+void launch_resort_window(const SimParams& sp, const PartView& src, const PartView& dst, int64_t n, cudaStream_t s);
 void launch_interior(const SimParams& sp, const int32_t* table, const int32_t* pslot, int32_t n_pblocks,
                      uint8_t* interior, cudaStream_t s);
 void launch_append(const PartView& pv, int64_t n0, int64_t n, const float* x, const float* v,

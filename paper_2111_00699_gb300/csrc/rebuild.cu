@@ -22,12 +22,9 @@ inline unsigned blocks_for(int64_t n, int per = kBlock) { return (unsigned)((n +
 
 // Particle code (Sec. 4): base node per axis with the -dx/2 shift of the
 // particle blocks; key = Morton(block) << 6 | Morton(cell within block).
-__global__ void k_keys(SimParams sp, PartView pv, int64_t n, uint32_t* __restrict__ keys,
-                       int32_t* __restrict__ vals, uint32_t* __restrict__ err)
+// Key of particle p (0xffffffff if its stencil leaves the grid or the table).
+__device__ __forceinline__ uint32_t particle_key(const SimParams& sp, const PartView& pv, int64_t p)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
-        return;
     int b[3];
     bool ok = true;
 #pragma unroll
@@ -36,16 +33,83 @@ __global__ void k_keys(SimParams sp, PartView pv, int64_t n, uint32_t* __restric
         b[a] = base_of(x, sp.inv_dx);
         ok = ok && isfinite(x) && b[a] >= 0 && b[a] + 2 < sp.res[a] && (b[a] >> 2) < (1 << sp.L);
     }
-    uint32_t key = 0xffffffffu;
-    if (ok) {
-        uint32_t blk = morton3((uint32_t)b[0] >> 2, (uint32_t)b[1] >> 2, (uint32_t)b[2] >> 2);
-        uint32_t cell = morton3((uint32_t)b[0] & 3u, (uint32_t)b[1] & 3u, (uint32_t)b[2] & 3u);
-        key = (blk << 6) | cell;
-    } else {
+    if (!ok)
+        return 0xffffffffu;
+    uint32_t blk = morton3((uint32_t)b[0] >> 2, (uint32_t)b[1] >> 2, (uint32_t)b[2] >> 2);
+    uint32_t cell = morton3((uint32_t)b[0] & 3u, (uint32_t)b[1] & 3u, (uint32_t)b[2] & 3u);
+    return (blk << 6) | cell;
+}
+
+__global__ void k_keys(SimParams sp, PartView pv, int64_t n, uint32_t* __restrict__ keys,
+                       int32_t* __restrict__ vals, uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    const uint32_t key = particle_key(sp, pv, p);
+    if (key == 0xffffffffu)
         atomicOr(err, ST_EDOMAIN);
-    }
     keys[p] = key;
     vals[p] = (int32_t)p;
+}
+
+// Window re-sort between rebuilds: the particles of each window of
+// kResortWindow consecutive storage slots are ordered by their current key
+// (block code, cell code) and copied, permuted, to the other particle
+// buffer.  Particles drift across cell faces long before they leave the
+// mapped blocks, and P2G merges only runs of consecutive particles in one
+// cell; this restores the runs without a global sort or a host round trip.
+// Ties keep no particular order (bitonic sort), which changes only the
+// order of floating-point sums.
+constexpr int kResortThreads = 256;
+
+__global__ void __launch_bounds__(kResortThreads) k_resort_window(SimParams sp, PartView src, PartView dst, int64_t n)
+{
+    __shared__ uint32_t key[kResortWindow];
+    __shared__ uint16_t idx[kResortWindow];
+    const int tid = threadIdx.x;
+    const int64_t p0 = (int64_t)blockIdx.x * kResortWindow;
+    for (int i = tid; i < kResortWindow; i += kResortThreads) {
+        const int64_t p = p0 + i;
+        uint32_t k = 0xffffffffu;                       // padding past n sorts last
+        if (p < n)
+            k = min(particle_key(sp, src, p), 0xfffffffeu);
+        key[i] = k;
+        idx[i] = (uint16_t)i;
+    }
+    __syncthreads();
+    // bitonic sort of (key, idx), ascending
+    for (int size = 2; size <= kResortWindow; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < kResortWindow / 2; t += kResortThreads) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint32_t a = key[lo], b = key[hi];
+                const bool swap = up ? (a > b || (a == b && idx[lo] > idx[hi]))
+                                     : (a < b || (a == b && idx[lo] < idx[hi]));
+                if (swap) {
+                    key[lo] = b;
+                    key[hi] = a;
+                    const uint16_t t2 = idx[lo];
+                    idx[lo] = idx[hi];
+                    idx[hi] = t2;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int m = (int)min((int64_t)kResortWindow, n - p0);
+    for (int c = 0; c < kChannels; ++c) {
+        const float* in = src.ch(c) + p0;
+        float* out = dst.ch(c) + p0;
+        for (int i = tid; i < m; i += kResortThreads)
+            out[i] = in[idx[i]];
+    }
+    for (int i = tid; i < m; i += kResortThreads) {
+        dst.mat[p0 + i] = src.mat[p0 + idx[i]];
+        dst.id[p0 + i] = src.id[p0 + idx[i]];
+    }
 }
 
 // Mark the 3x3x3 neighbourhood of every gblock (the first particle of each
@@ -229,6 +293,12 @@ void launch_permute(const PartView& src, const PartView& dst, const int32_t* per
 {
     if (n > 0)
         k_permute<<<blocks_for(n), kBlock, 0, s>>>(src, dst, perm, n);
+}
+
+void launch_resort_window(const SimParams& sp, const PartView& src, const PartView& dst, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        k_resort_window<<<(unsigned)((n + kResortWindow - 1) / kResortWindow), kResortThreads, 0, s>>>(sp, src, dst, n);
 }
 
 void launch_interior(const SimParams& sp, const int32_t* table, const int32_t* pslot, int32_t n_pblocks,

@@ -50,7 +50,7 @@ class Simulator:
     def __init__(self, res, dx, materials, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0),
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
                  device=None, p2g_variant: int = 3, g2p_variant: int = 0, g2p2g: bool = False,
-                 no_sort: bool = False, graphs: bool = False):
+                 no_sort: bool = False, graphs: bool = False, resort_interval: int = 0):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -71,6 +71,7 @@ class Simulator:
         cfg.p2g_variant = int(p2g_variant)
         cfg.g2p_variant = int(g2p_variant)
         cfg.no_sort = 1 if no_sort else 0
+        cfg.resort_interval = int(resort_interval)
         mats = (_lib.Material * len(self.materials))(*self.materials)
         self._alloc = None
         if torch_allocator:

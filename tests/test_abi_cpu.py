@@ -65,6 +65,9 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     bad.use_g2p2g = 2
     assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad = _lib.Config.from_buffer_copy(cfg)
+    bad.resort_interval = -1
+    assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
+    bad = _lib.Config.from_buffer_copy(cfg)
     bad.no_sort = 2
     assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad = _lib.Config.from_buffer_copy(cfg)
