@@ -330,6 +330,38 @@ def bench_ablations(substeps=100):
     return out
 
 
+def _snow_ms_per_substep(steps=400, warm=300):
+    """ms per substep of the snow scene in the bench launch configuration
+    (used by the fast-math ablation in a child process)."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x, _ = scenes.snow_blocks()
+    stream = torch.cuda.Stream()
+    with mpm.Simulator(RES, DX, [mpm.material(mpm.SNOW, **SNOW)], boundary=mpm.SLIP, stream=stream, p2g_variant=4,
+                       g2p_variant=4, graphs=True, resort_interval=RESORT_INTERVAL) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        sim.run(warm, DT)
+        ms = _events_time(stream, lambda: sim.run(steps, DT))
+        sim.sync()
+    return ms / steps
+
+
+def bench_fast_math():
+    """Sec. 6 fast-math ablation: the same snow run with the library built
+    with and without -use_fast_math (each in a child process, since one
+    process loads one build)."""
+    from paper_2111_00699_gb300 import build
+    build.build(ieee=True)
+    out = {"workload": "snow blocks 1340960 particles, 400 substeps after 300", "unit": "ms/substep"}
+    for name, env in (("fast_math", {}), ("ieee", {"MPM_LIBRARY": "ieee"})):
+        r = subprocess.run([sys.executable, "-c", "import bench, json; print(json.dumps(bench._snow_ms_per_substep()))"],
+                           cwd=ROOT, env=dict(os.environ, **env), capture_output=True, text=True)
+        out[name] = json.loads(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else "failed: " + r.stderr[-300:]
+    if isinstance(out["fast_math"], float) and isinstance(out["ieee"], float):
+        out["ieee_over_fast_math"] = out["ieee"] / out["fast_math"]
+    return out
+
+
 def bench_sand(substeps=1000):
     """Drucker-Prager sand (phi = 30 deg), 4 random boxes, ~500K particles at
     8 per cell, 128^3, dt 1e-4."""
@@ -646,7 +678,7 @@ def main():
         workloads = {}
         for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand),
                          ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
-                         ("ablations", bench_ablations)):
+                         ("ablations", bench_ablations), ("fast_math", bench_fast_math)):
             try:
                 workloads[name] = fn()
             except Exception as exc:   # report, do not lose the main line

@@ -11,7 +11,9 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmpm.so")
+# MPM_LIBRARY=ieee selects the build without fast-math intrinsics (the
+# fast-math ablation); the default is the fast-math build
+LIB_PATH = os.path.join(HERE, "libmpm_ieee.so" if os.environ.get("MPM_LIBRARY") == "ieee" else "libmpm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "mpm.h")
 
 MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECAPACITY, MPM_EDOMAIN, MPM_ENONFINITE, MPM_ETIMEOUT, MPM_ECUDA, MPM_ENOTSUP = range(9)

@@ -9,6 +9,8 @@ Tolerances (stated per check):
     substeps: |dv|_inf <= 1e-4 |v|_inf;
   * total grid mass vs total particle mass: 1e-6 relative.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -715,3 +717,38 @@ def test_g2p2g_with_emission(M):
         g = {k: v.double().cpu().numpy() for k, v in sim.read_state().items()}
     assert linf(g["x"], s.x) <= 1e-4
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+
+
+def test_ieee_build_matches_oracle():
+    """The library built without fast-math intrinsics (the fast-math ablation)
+    computes the same substeps: the small elastic and a snow case, in a child
+    process that loads that build."""
+    import subprocess
+    import sys
+    from paper_2111_00699_gb300 import build
+    build.build(ieee=True)
+    code = r"""
+import numpy as np, torch, oracle as orc
+from paper_2111_00699_gb300 import mpm, scenes, _lib
+assert _lib.LIB_PATH.endswith("libmpm_ieee.so")
+orc.build()
+x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
+for kind, kw, dt in ((mpm.ELASTIC, dict(E=1e4, nu=0.2, rho=1.0), 1e-4),
+                     (mpm.SNOW, dict(E=1.4e5, nu=0.2, rho=400.0), 5e-5)):
+    rng = np.random.default_rng(3)
+    v = (0.3 * rng.normal(size=x.shape)).astype(np.float32)
+    with mpm.Simulator(64, 1 / 64, [mpm.material(kind, **kw)]) as sim:
+        sim.add_particles(x, v=v, vol=np.full(len(x), 0.008 / 8192, np.float32))
+        sim.run(10, dt)
+        g = {k: t.double().cpu().numpy() for k, t in sim.read_state().items()}
+    s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=0.008 / 8192)
+    for _ in range(10):
+        assert orc.substep(orc.config(64, 1 / 64, orc.STICKY), [orc.material(kind, **kw)], s, dt) == 0
+    assert np.abs(g["x"] - s.x).max() <= 1e-4
+    assert np.abs(g["v"] - s.v).max() <= 1e-4 * np.abs(s.v).max()
+print("ok")
+"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=dict(os.environ, MPM_LIBRARY="ieee"),
+                       capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
