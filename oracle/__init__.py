@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRCS = ["bspline.c", "svd.c", "material.c", "transfer.c", "keys.c", "adjoint.c"]
 
-ELASTIC, FLUID, SNOW, SAND = 0, 1, 2, 3
+ELASTIC, FLUID, SNOW, SAND, NACC = 0, 1, 2, 3, 4
 STICKY, SLIP = 0, 1
 
 
@@ -46,7 +46,8 @@ class Material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("E", ctypes.c_double), ("nu", ctypes.c_double),
                 ("rho", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("theta_c", ctypes.c_double), ("theta_s", ctypes.c_double),
-                ("hardening", ctypes.c_double), ("friction_deg", ctypes.c_double)]
+                ("hardening", ctypes.c_double), ("friction_deg", ctypes.c_double),
+                ("friction_M", ctypes.c_double), ("cohesion", ctypes.c_double), ("alpha0", ctypes.c_double)]
 
 
 class Config(ctypes.Structure):
@@ -109,8 +110,9 @@ def _f64(a, shape=None):
 
 
 def material(kind, E=1e4, nu=0.2, rho=1.0, gamma=7.0, theta_c=2.5e-2, theta_s=7.5e-3,
-             hardening=10.0, friction_deg=30.0) -> Material:
-    return Material(int(kind), E, nu, rho, gamma, theta_c, theta_s, hardening, friction_deg)
+             hardening=10.0, friction_deg=30.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01) -> Material:
+    return Material(int(kind), E, nu, rho, gamma, theta_c, theta_s, hardening, friction_deg, friction_M, cohesion,
+                    alpha0)
 
 
 def config(res, dx, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0)) -> Config:

@@ -16,6 +16,18 @@
  *   sand:             tau = U (2 mu eps + lambda tr(eps) I) U^T with the
  *                     Hencky strain eps = ln(sigma), and the Drucker-Prager
  *                     return map of Klar et al. 2016 (cases I-III).
+ *   NACC snow:        the non-associative Cam-Clay model the paper uses for
+ *                     its snow scene (Sec. 6.5, parameters kappa, nu, M, beta,
+ *                     xi in the notation of Wolper et al. 2019): the same
+ *                     Hencky elasticity with mu, lambda from the bulk modulus
+ *                     kappa and nu; with p = -tr(tau)/3 and
+ *                     q = sqrt(3/2) |dev tau|, the yield surface
+ *                     y = (1 + 2 beta) q^2 + M^2 (p + beta p0)(p - p0) = 0,
+ *                     p0 = kappa sinh(xi max(-alpha, 0)), alpha = alpha0 + ln Jp;
+ *                     the return map keeps p and scales q onto the surface
+ *                     (non-associative), or moves to the tips (p0, 0) and
+ *                     (-beta p0, 0) beyond them; Jp absorbs the volume the
+ *                     projection removes.
  * Readings of points the sources leave open (log of non-positive singular
  * values, tie cases) are listed in the design doc.
  */
@@ -86,6 +98,50 @@ static void hencky(const double sig[3], double eps[3])
         eps[i] = log(sig[i] > 1e-4 ? sig[i] : 1e-4);
 }
 
+/* Lame parameters from the bulk modulus kappa and Poisson ratio nu. */
+static void nacc_lame(double kappa, double nu, double* mu, double* la)
+{
+    *mu = 3.0 * kappa * (1.0 - 2.0 * nu) / (2.0 * (1.0 + nu));
+    *la = kappa - 2.0 * *mu / 3.0;
+}
+
+/* NACC return map on the principal Hencky strains eps (in place).  Returns
+ * the change of ln det F (trial minus projected); see the file comment. */
+static double nacc_project(const orc_material* mat, double Jp, double eps[3])
+{
+    double mu, la;
+    nacc_lame(mat->E, mat->nu, &mu, &la);
+    const double kappa = mat->E, M = mat->friction_M, beta = mat->cohesion;
+    double tr = eps[0] + eps[1] + eps[2];
+    double dev[3], nd = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        dev[i] = eps[i] - tr / 3.0;
+        nd += dev[i] * dev[i];
+    }
+    nd = sqrt(nd);
+    double p = -kappa * tr;                       /* -tr(tau) / 3 with tr(tau) = 3 kappa tr(eps) */
+    double q = sqrt(1.5) * 2.0 * mu * nd;         /* sqrt(3/2) |dev tau|, dev tau = 2 mu dev eps */
+    double alpha = mat->alpha0 + log(Jp);
+    double p0 = kappa * sinh(mat->hardening * (alpha < 0.0 ? -alpha : 0.0));
+    double pn = p, qn = q;
+    if (p > p0) {
+        pn = p0;
+        qn = 0.0;
+    } else if (p < -beta * p0) {
+        pn = -beta * p0;
+        qn = 0.0;
+    } else {
+        double y = (1.0 + 2.0 * beta) * q * q + M * M * (p + beta * p0) * (p - p0);
+        if (y > 0.0)
+            qn = sqrt(M * M * (p + beta * p0) * (p0 - p) / (1.0 + 2.0 * beta));
+    }
+    double trn = -pn / kappa;
+    double s = q > 0.0 ? qn / q : 0.0;
+    for (int i = 0; i < 3; ++i)
+        eps[i] = trn / 3.0 + s * dev[i];
+    return tr - trn;
+}
+
 void orc_kirchhoff(const orc_material* mat, const double F[9], double Jp, double tau[9])
 {
     double mu, la;
@@ -108,8 +164,12 @@ void orc_kirchhoff(const orc_material* mat, const double F[9], double Jp, double
             AT(tau, i, i) = -p * J;
         break;
     }
+    case ORC_NACC:
     case ORC_SAND: {
-        orc_lame(mat->E, mat->nu, &mu, &la);
+        if (mat->kind == ORC_NACC)
+            nacc_lame(mat->E, mat->nu, &mu, &la);
+        else
+            orc_lame(mat->E, mat->nu, &mu, &la);
         double U[9], sig[3], V[9], eps[3], d[3];
         orc_svd3(F, U, sig, V);
         hencky(sig, eps);
@@ -126,6 +186,17 @@ void orc_kirchhoff(const orc_material* mat, const double F[9], double Jp, double
 
 void orc_plasticity(const orc_material* mat, double F[9], double* Jp)
 {
+    if (mat->kind == ORC_NACC) {
+        double U[9], sig[3], V[9], eps[3], s[3];
+        orc_svd3(F, U, sig, V);
+        hencky(sig, eps);
+        double dlnJ = nacc_project(mat, *Jp, eps);
+        for (int i = 0; i < 3; ++i)
+            s[i] = exp(eps[i]);
+        udwt(U, s, V, F);
+        *Jp *= exp(dlnJ);
+        return;
+    }
     if (mat->kind == ORC_SNOW) {
         double U[9], sig[3], V[9], cl[3];
         orc_svd3(F, U, sig, V);

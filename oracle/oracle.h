@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-enum { ORC_ELASTIC = 0, ORC_FLUID = 1, ORC_SNOW = 2, ORC_SAND = 3 };
+enum { ORC_ELASTIC = 0, ORC_FLUID = 1, ORC_SNOW = 2, ORC_SAND = 3, ORC_NACC = 4 };
 enum { ORC_STICKY = 0, ORC_SLIP = 1 };
 enum { ORC_OK = 0, ORC_EDOMAIN = 4, ORC_EINVAL = 1 };
 
@@ -52,6 +52,9 @@ typedef struct {
     double theta_s;    /* snow critical stretch */
     double hardening;  /* snow hardening coefficient xi */
     double friction_deg; /* sand friction angle phi in degrees */
+    double friction_M; /* NACC: slope M of the critical state line */
+    double cohesion;   /* NACC: cohesion beta */
+    double alpha0;     /* NACC: initial hardening state alpha (ln of the plastic volume ratio) */
 } orc_material;
 
 typedef struct {
@@ -79,8 +82,9 @@ void orc_svd3(const double F[9], double U[9], double sig[3], double V[9]);
 /* Lame parameters from (E, nu). */
 void orc_lame(double E, double nu, double* mu, double* la);
 
-/* Kirchhoff stress tau = P F^T of one particle.  Jp is the snow plastic
- * volume ratio, or the fluid J; ignored for elastic and sand. */
+/* Kirchhoff stress tau = P F^T of one particle.  Jp is the snow (and NACC)
+ * plastic volume ratio, or the fluid J; ignored for elastic and sand.
+ * ORC_NACC: E is the bulk modulus kappa, hardening is xi. */
 void orc_kirchhoff(const orc_material* mat, const double F[9], double Jp, double tau[9]);
 
 /* Return mapping applied to the trial F at the end of G2P (snow clamp,

@@ -203,6 +203,83 @@ def test_drucker_prager_cases(orc):
     np.testing.assert_allclose(dev2 / np.linalg.norm(dev2), np.sort(dev)[::-1] / np.linalg.norm(dev), atol=1e-9)
 
 
+def _nacc_pq(F, kappa, nu):
+    """p = -tr(tau)/3 and q = sqrt(3/2)|dev tau| of the Hencky St. Venant-
+    Kirchhoff stress of F, from numpy's SVD (independent of the oracle)."""
+    mu = 3 * kappa * (1 - 2 * nu) / (2 * (1 + nu))
+    e = np.log(np.linalg.svd(F, compute_uv=False))
+    dev = e - e.mean()
+    return -kappa * e.sum(), np.sqrt(1.5) * 2 * mu * np.linalg.norm(dev), e, dev
+
+
+def test_nacc_cam_clay_return_map(orc):
+    """NACC (Cam-Clay, non-associative): inside the ellipse nothing changes;
+    beyond it q shrinks onto the surface at the same p with the deviatoric
+    direction kept; beyond the tips the state moves to (p0, 0) or
+    (-beta p0, 0) and Jp absorbs the removed volume; the stress is Hencky
+    St. Venant-Kirchhoff with the bulk modulus kappa."""
+    kappa, nu, M, beta, xi, a0 = 5e5, 0.3, 0.8, 0.9, 5.0, -0.01
+    mat = orc.material(orc.NACC, E=kappa, nu=nu, hardening=xi, friction_M=M, cohesion=beta, alpha0=a0)
+    mu = 3 * kappa * (1 - 2 * nu) / (2 * (1 + nu))
+    la = kappa - 2 * mu / 3
+    p0 = kappa * np.sinh(xi * 0.01)                   # Jp = 1: alpha = alpha0
+    y = lambda p, q: (1 + 2 * beta) * q * q + M * M * (p + beta * p0) * (p - p0)
+    rng = np.random.default_rng(21)
+    R1, R2 = _rand_rot(rng), _rand_rot(rng)
+    # stress
+    Fs = R1 @ np.diag([1.01, 0.995, 0.98]) @ R2.T
+    tau = orc.kirchhoff(mat, Fs, 1.0)
+    e = np.log([1.01, 0.995, 0.98])
+    ref = R1 @ np.diag(2 * mu * e + la * e.sum()) @ R1.T
+    np.testing.assert_allclose(tau, ref, atol=1e-9 * np.abs(ref).max())
+    assert abs(np.trace(tau) - 3 * kappa * e.sum()) < 1e-9 * kappa
+    # inside: mild compression, little shear
+    Fi = R1 @ np.diag([0.9999, 0.9998, 0.9997]) @ R2.T
+    p, q, _, _ = _nacc_pq(Fi, kappa, nu)
+    assert 0 < p < p0 and y(p, q) < 0
+    F, Jp = orc.plasticity(mat, Fi, 1.0)
+    np.testing.assert_allclose(F, Fi, atol=1e-13)
+    assert Jp == 1.0
+    # sheared: projected onto the ellipse at the same p, direction kept, no volume change
+    Fo = R1 @ np.diag([1.03, 0.997, 0.975]) @ R2.T
+    p, q, e, dev = _nacc_pq(Fo, kappa, nu)
+    assert -beta * p0 < p < p0 and y(p, q) > 0
+    F, Jp = orc.plasticity(mat, Fo, 1.0)
+    p2, q2, e2, dev2 = _nacc_pq(F, kappa, nu)
+    assert abs(p2 - p) < 1e-9 * kappa and abs(y(p2, q2)) < 1e-9 * (M * p0) ** 2
+    np.testing.assert_allclose(dev2 / np.linalg.norm(dev2), np.sort(dev)[::-1] / np.linalg.norm(dev), atol=1e-9)
+    assert abs(Jp - 1.0) < 1e-12
+    # compressed past the cap: to (p0, 0); Jp takes the removed volume
+    Fc = R1 @ np.diag([0.985, 0.98, 0.975]) @ R2.T
+    p, q, e, _ = _nacc_pq(Fc, kappa, nu)
+    assert p > p0
+    F, Jp = orc.plasticity(mat, Fc, 1.0)
+    p2, q2, e2, _ = _nacc_pq(F, kappa, nu)
+    assert abs(p2 - p0) < 1e-9 * kappa and q2 < 1e-6 * kappa
+    assert abs(Jp * np.linalg.det(F) - np.linalg.det(Fc)) < 1e-12
+    # stretched past the cohesion tip: to (-beta p0, 0)
+    Ft = R1 @ np.diag([1.016, 1.018, 1.015]) @ R2.T
+    p, q, _, _ = _nacc_pq(Ft, kappa, nu)
+    assert p < -beta * p0
+    F, Jp = orc.plasticity(mat, Ft, 1.0)
+    p2, q2, _, _ = _nacc_pq(F, kappa, nu)
+    assert abs(p2 + beta * p0) < 1e-9 * kappa and q2 < 1e-6 * kappa
+    assert abs(Jp * np.linalg.det(F) - np.linalg.det(Ft)) < 1e-12
+    # no hardening (alpha >= 0): p0 = 0, every state returns to the stress-free one
+    soft = orc.material(orc.NACC, E=kappa, nu=nu, hardening=xi, friction_M=M, cohesion=beta, alpha0=0.0)
+    F, Jp = orc.plasticity(soft, Fo, 1.0)
+    np.testing.assert_allclose(np.linalg.svd(F, compute_uv=False), 1.0, atol=1e-12)
+    np.testing.assert_allclose(orc.kirchhoff(soft, F, Jp), 0.0, atol=1e-6)
+    # hardening: compaction (Jp < 1, alpha = -0.03) raises p0 to kappa sinh(0.15), so the
+    # state that was past the cap is now inside the ellipse and stays
+    p, q, _, _ = _nacc_pq(Fc, kappa, nu)
+    p0h = kappa * np.sinh(xi * 0.03)
+    assert p < p0h and (1 + 2 * beta) * q * q + M * M * (p + beta * p0h) * (p - p0h) < 0
+    F, Jp = orc.plasticity(mat, Fc, np.exp(-0.02))
+    np.testing.assert_allclose(F, Fc, atol=1e-13)
+    assert Jp == np.exp(-0.02)
+
+
 # --------------------------------------------------------------- transfers
 
 def _random_state(orc, rng, n, lo, hi, dx, F_noise=0.05, C_scale=1.0, v_scale=1.0):
