@@ -53,21 +53,29 @@ typedef enum {
     MPM_ENOTSUP = 8     /* the request is valid but not supported by this build */
 } mpm_status;
 
-typedef enum { MPM_ELASTIC = 0, MPM_FLUID = 1, MPM_SNOW = 2, MPM_SAND = 3 } mpm_kind;
+typedef enum { MPM_ELASTIC = 0, MPM_FLUID = 1, MPM_SNOW = 2, MPM_SAND = 3, MPM_NACC = 4 } mpm_kind;
 typedef enum { MPM_STICKY = 0, MPM_SLIP = 1 } mpm_boundary;
 
-/* One material.  E is Young's modulus (for MPM_FLUID: the bulk modulus K).
- * Fixed-corotated elastic [Stomakhin 2012]; snow = fixed-corotated on F_E
- * with exp(hardening (1 - Jp)) and singular values clamped to
+/* One material.  E is Young's modulus (for MPM_FLUID and MPM_NACC: the bulk
+ * modulus).  Fixed-corotated elastic [Stomakhin 2012]; snow = fixed-corotated
+ * on F_E with exp(hardening (1 - Jp)) and singular values clamped to
  * [1 - theta_c, 1 + theta_s] [Stomakhin 2013]; fluid p = K (J^-gamma - 1)
  * [Tampubolon 2017]; sand = Hencky-strain St. Venant-Kirchhoff with the
- * Drucker-Prager return map for friction angle friction_deg [Klar 2016]. */
+ * Drucker-Prager return map for friction angle friction_deg [Klar 2016];
+ * NACC snow (the paper's snow model, Sec. 6.5, after Wolper et al. 2019) =
+ * the same Hencky elasticity from the bulk modulus E and nu, the Cam-Clay
+ * yield ellipse (1 + 2 beta) q^2 + M^2 (p + beta p0)(p - p0) <= 0 with
+ * p0 = E sinh(hardening * max(-alpha, 0)), alpha = alpha0 + ln Jp, and a
+ * non-associative return map (q scaled at fixed p, or the tips). */
 typedef struct {
     int32_t kind;          /* mpm_kind */
     float E, nu, rho;
     float gamma;           /* fluid exponent */
     float theta_c, theta_s, hardening;
     float friction_deg;
+    float friction_M;      /* NACC: slope M of the critical state line */
+    float cohesion;        /* NACC: cohesion beta */
+    float alpha0;          /* NACC: initial alpha (< 0 gives the material strength at rest) */
 } mpm_material;
 
 /* Grid and scene.  Nodes i = 0..res[a]-1 sit at i * dx.  Nodes with

@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mpm.h")
 MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECAPACITY, MPM_EDOMAIN, MPM_ENONFINITE, MPM_ETIMEOUT, MPM_ECUDA, MPM_ENOTSUP = range(9)
 STATUS_NAMES = ["MPM_OK", "MPM_EINVAL", "MPM_ENOMEM", "MPM_ECAPACITY", "MPM_EDOMAIN", "MPM_ENONFINITE",
                 "MPM_ETIMEOUT", "MPM_ECUDA", "MPM_ENOTSUP"]
-ELASTIC, FLUID, SNOW, SAND = 0, 1, 2, 3
+ELASTIC, FLUID, SNOW, SAND, NACC = 0, 1, 2, 3, 4
 STICKY, SLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
@@ -30,7 +30,8 @@ G2P_VARIANTS = ("direct", "chunk4", "chunk8", "tile", "occ", "stage")
 class Material(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("E", ctypes.c_float), ("nu", ctypes.c_float), ("rho", ctypes.c_float),
                 ("gamma", ctypes.c_float), ("theta_c", ctypes.c_float), ("theta_s", ctypes.c_float),
-                ("hardening", ctypes.c_float), ("friction_deg", ctypes.c_float)]
+                ("hardening", ctypes.c_float), ("friction_deg", ctypes.c_float),
+                ("friction_M", ctypes.c_float), ("cohesion", ctypes.c_float), ("alpha0", ctypes.c_float)]
 
 
 class Config(ctypes.Structure):
@@ -147,5 +148,6 @@ class MpmError(RuntimeError):
 
 
 def material(kind=ELASTIC, E=1e4, nu=0.2, rho=1.0, gamma=7.0, theta_c=2.5e-2, theta_s=7.5e-3,
-             hardening=10.0, friction_deg=30.0) -> Material:
-    return Material(int(kind), E, nu, rho, gamma, theta_c, theta_s, hardening, friction_deg)
+             hardening=10.0, friction_deg=30.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01) -> Material:
+    return Material(int(kind), E, nu, rho, gamma, theta_c, theta_s, hardening, friction_deg, friction_M, cohesion,
+                    alpha0)

@@ -423,7 +423,9 @@ mpm_status rebuild(mpm_ctx* ctx)
 
 bool valid_material(const mpm_material& m)
 {
-    if (m.kind < MPM_ELASTIC || m.kind > MPM_SAND)
+    if (m.kind < MPM_ELASTIC || m.kind > MPM_NACC)
+        return false;
+    if (m.kind == MPM_NACC && !(m.friction_M > 0.f && m.cohesion >= 0.f && m.hardening >= 0.f))
         return false;
     if (!(m.rho > 0.f) || !(m.E > 0.f))
         return false;

@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kT, 8) bk_g2p(BatchView bv, PartView pv, int64
 #pragma unroll
         for (int e = 0; e < 9; ++e)
             pv.ch(CH_F + e)[p] = Hn[e];
-        if (m.kind == MPM_SNOW)
+        if (m.kind == MPM_SNOW || m.kind == MPM_NACC)
             pv.ch(CH_JP)[p] = jn;
     }
 #pragma unroll
@@ -769,7 +769,7 @@ mpm_status mpm_batch_create(int n_scenes, const mpm_scene_desc* scenes, const mp
         return MPM_EINVAL;
     for (int i = 0; i < n_mats; ++i) {
         const mpm_material& m = mats[i];
-        if (m.kind < MPM_ELASTIC || m.kind > MPM_SAND || !(m.rho > 0.f) || !(m.E > 0.f) ||
+        if (m.kind < MPM_ELASTIC || m.kind > MPM_NACC || !(m.rho > 0.f) || !(m.E > 0.f) ||
             (m.kind != MPM_FLUID && !(m.nu > -1.f && m.nu < 0.5f)))
             return MPM_EINVAL;
     }

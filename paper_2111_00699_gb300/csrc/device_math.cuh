@@ -499,7 +499,39 @@ __device__ __forceinline__ void left_exp_update(const Sym& x, float* H)
 // outside its range (the caller then takes the SVD path).  With
 // `project` the return maps run (snow: none needed on this path; sand:
 // cases II and III update H).
-__device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H, float jm1, bool project, float* t6)
+// NACC return map on the Hencky strain, given its trace tr and the norm nd
+// of its deviator: with p = -kappa tr and q = sqrt(3/2) 2 mu nd, a state
+// outside the ellipse (1 + 2 beta) q^2 + M^2 (p + beta p0)(p - p0) <= 0,
+// p0 = kappa sinh(xi max(-alpha, 0)), alpha = alpha0 + ln Jp, keeps p and
+// takes the q on the ellipse, or moves to a tip beyond p0 or -beta p0.
+// Returns false if the state is inside; else the new trace trn and the
+// factor s on the deviator.
+__device__ __forceinline__ bool nacc_return(const MatParams& m, float jm1, float tr, float nd, float& trn, float& s)
+{
+    const float kappa = m.K;
+    const float p = -kappa * tr;
+    const float q = 1.22474487f * 2.0f * m.mu * nd;   // sqrt(3/2) |dev tau|
+    const float alpha = m.alpha0 + log1pf(jm1);
+    const float p0 = kappa * sinhf(m.xi * fmaxf(-alpha, 0.0f));
+    float pn = p, qn = q;
+    if (p > p0) {
+        pn = p0;
+        qn = 0.0f;
+    } else if (p < -m.beta * p0) {
+        pn = -m.beta * p0;
+        qn = 0.0f;
+    } else {
+        const float y = (1.0f + 2.0f * m.beta) * q * q + m.M2 * (p + m.beta * p0) * (p - p0);
+        if (!(y > 0.0f))
+            return false;
+        qn = sqrtf(m.M2 * (p + m.beta * p0) * (p0 - p) / (1.0f + 2.0f * m.beta));
+    }
+    trn = -pn / kappa;
+    s = q > 0.0f ? qn / q : 0.0f;
+    return true;
+}
+
+__device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H, float& jm1, bool project, float* t6)
 {
     const Sym g = left_cg_m1(H);
     const float Jm1 = det_m1(H);
@@ -517,9 +549,26 @@ __device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H
         fc_tau_series(g, m.mu, m.la, Jm1, t6);
         return true;
     }
-    // sand: Hencky strain in the current (left) frame, Drucker-Prager return map
+    // sand and NACC: Hencky strain in the current (left) frame
     Sym eps = hencky_series(g);
     const float tr = sym_trace(eps);
+    if (project && m.kind == MPM_NACC) {
+        const Sym dev = sym_add_diag(eps, -tr * (1.0f / 3.0f));
+        float trn, sc;
+        if (nacc_return(m, jm1, tr, sqrtf(sym_frob2(dev)), trn, sc)) {
+            // eps <- trn/3 I + sc dev, F <- exp(eps_new - eps) F, Jp <- Jp exp(tr - trn)
+            const Sym en = sym_add_diag(sym_scale(dev, sc), trn * (1.0f / 3.0f));
+            const Sym x = {eps.xx - en.xx, eps.yy - en.yy, eps.zz - en.zz, eps.xy - en.xy, eps.xz - en.xz,
+                           eps.yz - en.yz};
+            left_exp_update(x, H);
+            const float r = expm1f(tr - trn);
+            jm1 = jm1 * (1.0f + r) + r;
+            eps = en;
+        }
+        const Sym t = sym_add_diag(sym_scale(eps, 2.0f * m.mu), m.la * sym_trace(eps));
+        sym_to_t6(t, t6);
+        return true;
+    }
     if (project) {
         if (tr >= 0.0f) {
             // case II: project to the cone tip, F <- R = exp(-eps) F, tau = 0
@@ -559,13 +608,14 @@ __device__ __forceinline__ void stress_h(const MatParams& m, const float* H, flo
 #pragma unroll
         for (int q = 0; q < 9; ++q)
             Hc[q] = H[q];
-        if (small_strain_update(m, Hc, jm1, false, t6))
+        float jc = jm1;
+        if (small_strain_update(m, Hc, jc, false, t6))
             return;
     }
     SVDH d;
     svd_h(H, d);
     float dg[3];
-    if (m.kind == MPM_SAND) {
+    if (m.kind == MPM_SAND || m.kind == MPM_NACC) {
         float e[3] = {hencky(d.s[0], d.sm1[0]), hencky(d.s[1], d.sm1[1]), hencky(d.s[2], d.sm1[2])};
         float tr = e[0] + e[1] + e[2];
 #pragma unroll
@@ -628,6 +678,33 @@ __device__ __forceinline__ void constitutive_update(const MatParams& m, float* H
         for (int k = 0; k < 3; ++k)
             dg[k] = 2.0f * mu * t[k] * (1.0f + t[k]);
         tau6(d.U, dg, la * (1.0f + Jm1) * Jm1, t6);
+        return;
+    }
+    if (m.kind == MPM_NACC) {
+        float e[3] = {hencky(d.s[0], d.sm1[0]), hencky(d.s[1], d.sm1[1]), hencky(d.s[2], d.sm1[2])};
+        const float tr = e[0] + e[1] + e[2];
+        const float dv[3] = {e[0] - tr * (1.0f / 3.0f), e[1] - tr * (1.0f / 3.0f), e[2] - tr * (1.0f / 3.0f)};
+        float trn, sc;
+        if (nacc_return(m, jm1, tr, sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]), trn, sc)) {
+            float t[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                e[k] = trn * (1.0f / 3.0f) + sc * dv[k];
+                t[k] = expm1f(e[k]);
+            }
+            float Hn[9];
+            rebuild_h(d, H, t, Hn);
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                H[q] = Hn[q];
+            const float r = expm1f(tr - trn);
+            jm1 = jm1 * (1.0f + r) + r;
+        }
+        const float tr2 = e[0] + e[1] + e[2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dg[k] = 2.0f * m.mu * e[k] + m.la * tr2;
+        tau6(d.U, dg, 0.0f, t6);
         return;
     }
     if (m.kind == MPM_SAND) {

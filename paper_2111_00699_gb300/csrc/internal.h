@@ -65,6 +65,7 @@ struct MatParams {
     float K, gamma;          // fluid
     float lo_m1, hi_m1, xi;  // snow clamp bounds of sigma - 1 (-theta_c, theta_s), hardening
     float lo_b, hi_b;        // the same bounds on sigma^2 - 1: (1 - theta_c)^2 - 1, (1 + theta_s)^2 - 1
+    float M2, beta, alpha0;  // NACC: M^2, cohesion, initial alpha (K holds the bulk modulus, xi the hardening)
     float alpha, dp_coef;    // sand: cone slope, (3 la + 2 mu) / (2 mu)
 };
 

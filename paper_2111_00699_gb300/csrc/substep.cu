@@ -705,7 +705,7 @@ __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartV
 #pragma unroll
         for (int e = 0; e < 9; ++e)
             pv.ch(CH_F + e)[p] = Hn[e];
-        if (m.kind == MPM_SNOW)
+        if (m.kind == MPM_SNOW || m.kind == MPM_NACC)
             pv.ch(CH_JP)[p] = jn;
     }
     if (kFused) {
@@ -1273,7 +1273,7 @@ __global__ void k_debug_plasticity(MatParams m, float* __restrict__ F, float* __
     for (int e = 0; e < 9; ++e)
         h[e] = F[9 * p + e] - ((e % 4 == 0) ? 1.0f : 0.0f);
     float jm1 = Jp ? Jp[p] - 1.0f : 0.0f;
-    if (m.kind == MPM_SNOW || m.kind == MPM_SAND)
+    if (m.kind == MPM_SNOW || m.kind == MPM_SAND || m.kind == MPM_NACC)
         constitutive_update(m, h, jm1, t);
 #pragma unroll
     for (int e = 0; e < 9; ++e)
@@ -1294,6 +1294,15 @@ MatParams make_mat_params(const mpm_material& m)
     double E = m.E, nu = m.nu;
     q.mu = (float)(E / (2.0 * (1.0 + nu)));
     q.la = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    if (m.kind == MPM_NACC) {
+        // E is the bulk modulus kappa
+        const double mu = 3.0 * E * (1.0 - 2.0 * nu) / (2.0 * (1.0 + nu));
+        q.mu = (float)mu;
+        q.la = (float)(E - 2.0 * mu / 3.0);
+        q.M2 = m.friction_M * m.friction_M;
+        q.beta = m.cohesion;
+        q.alpha0 = m.alpha0;
+    }
     q.K = m.E;
     q.gamma = m.gamma;
     q.lo_m1 = -m.theta_c;

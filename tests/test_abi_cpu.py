@@ -35,7 +35,7 @@ def test_exports_are_c_symbols(lib):
 
 def test_struct_layouts_match_header(lib):
     from paper_2111_00699_gb300 import _lib
-    assert ctypes.sizeof(_lib.Material) == 4 * 9
+    assert ctypes.sizeof(_lib.Material) == 4 * 12
     assert ctypes.sizeof(_lib.Config) == 12 + 4 + 4 + 4 + 12 + 4 + 8 + 4 + 28   # with alignment padding
     assert ctypes.sizeof(_lib.Stats) == 6 * 8
 
@@ -76,6 +76,10 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     bad_mat = (_lib.Material * 1)(_lib.material(7))
     assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad_mat = (_lib.Material * 1)(_lib.material(_lib.ELASTIC, nu=0.5))
+    assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
+    bad_mat = (_lib.Material * 1)(_lib.material(_lib.NACC, E=5e4, nu=0.3, friction_M=0.0))
+    assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
+    bad_mat = (_lib.Material * 1)(_lib.material(5))
     assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     assert not ctx.value
 

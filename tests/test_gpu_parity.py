@@ -87,14 +87,15 @@ def test_svd_matches_numpy(M):
 
 
 @pytest.mark.parametrize("scale", [0.05, 0.01])
-@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc"])
 def test_stress_matches_oracle(M, kind, scale):
     """Stress of stored states, on the SVD path (5 % strain) and on the
     small-strain series path (1 %)."""
     rng = np.random.default_rng(1)
     n = 2048
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2), snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, hardening=10.0),
-              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0), sand=dict(kind=M.SAND, E=3.5e5, nu=0.3))[kind]
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0), sand=dict(kind=M.SAND, E=3.5e5, nu=0.3),
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, hardening=5.0))[kind]
     k = kw.pop("kind")
     gm, om = M.material(k, **kw), orc.material(k, **kw)
     F = (np.eye(3) + scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
@@ -133,7 +134,8 @@ def test_plasticity_matches_oracle(M, scale):
     rng = np.random.default_rng(2)
     n = 1024
     for kind, kw in ((M.SNOW, dict(E=1.4e5, nu=0.2, theta_c=2.5e-2, theta_s=7.5e-3)),
-                     (M.SAND, dict(E=3.5e5, nu=0.3, friction_deg=30.0))):
+                     (M.SAND, dict(E=3.5e5, nu=0.3, friction_deg=30.0)),
+                     (M.NACC, dict(E=5e4, nu=0.3, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01))):
         gm, om = M.material(kind, **kw), orc.material(kind, **kw)
         F = (np.eye(3) + scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
         Jp = rng.uniform(0.9, 1.1, n).astype(np.float32)
@@ -282,12 +284,13 @@ def test_substeps_small_elastic(M):
         assert linf(g["v"], s.v) <= 1e-3 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc"])
 def test_substeps_materials(M, kind):
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
               snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
-              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0),
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01))[kind]
     k = kw.pop("kind")
     gm, om = mats_pair(M, k, **kw)
     dt = 5e-5 if k == M.SNOW else 1e-4
