@@ -362,6 +362,28 @@ def bench_fast_math():
     return out
 
 
+def bench_nacc_snow(substeps=400):
+    """The snow-blocks scene with the paper's own snow model, NACC (Sec. 6.5:
+    bulk modulus 5e5 dyne/cm^2 = 5e4 Pa, nu 0.3, M 0.8, beta 0.9, xi 5;
+    alpha0 = -0.01), 256^3, dt 5e-5, in the bench launch configuration."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x, _ = scenes.snow_blocks()
+    stream = torch.cuda.Stream()
+    mat = mpm.material(mpm.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01)
+    with mpm.Simulator(RES, DX, [mat], boundary=mpm.SLIP, stream=stream, p2g_variant=3, g2p_variant=4, graphs=True,
+                       resort_interval=RESORT_INTERVAL) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        sim.run(300, DT)
+        ms = _events_time(stream, lambda: sim.run(substeps, DT))
+        sim.sync()
+        st = sim.stats()
+    return {"workload": "snow blocks with NACC snow, %d particles, 256^3, dt=5e-5, %d substeps after 300"
+                        % (len(x), substeps),
+            "value": len(x) * substeps / (ms / 1e3), "unit": UNIT, "ms_per_substep": ms / substeps,
+            "rebuilds": st["rebuilds"]}
+
+
 def bench_sand(substeps=1000):
     """Drucker-Prager sand (phi = 30 deg), 4 random boxes, ~500K particles at
     8 per cell, 128^3, dt 1e-4."""
@@ -677,6 +699,7 @@ def main():
     if not args.no_workloads and world == 1:
         workloads = {}
         for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand),
+                         ("nacc_snow", bench_nacc_snow),
                          ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
                          ("ablations", bench_ablations), ("fast_math", bench_fast_math)):
             try:
