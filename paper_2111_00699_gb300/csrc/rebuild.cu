@@ -100,15 +100,36 @@ __global__ void __launch_bounds__(kResortThreads) k_resort_window(SimParams sp, 
         }
     }
     const int m = (int)min((int64_t)kResortWindow, n - p0);
-    for (int c = 0; c < kChannels; ++c) {
-        const float* in = src.ch(c) + p0;
-        float* out = dst.ch(c) + p0;
-        for (int i = tid; i < m; i += kResortThreads)
-            out[i] = in[idx[i]];
+    // permutation: each thread moves its 4 slots; 8 channels' loads in flight at a time
+    constexpr int kPer = kResortWindow / kResortThreads;
+    int src_i[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int i = tid + k * kResortThreads;
+        src_i[k] = i < m ? idx[i] : -1;
     }
-    for (int i = tid; i < m; i += kResortThreads) {
-        dst.mat[p0 + i] = src.mat[p0 + idx[i]];
-        dst.id[p0 + i] = src.id[p0 + idx[i]];
+#pragma unroll 1
+    for (int c0 = 0; c0 < kChannels; c0 += 8) {
+        float v[8][kPer];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int k = 0; k < kPer; ++k)
+                v[c][k] = src_i[k] >= 0 ? src.ch(c0 + c)[p0 + src_i[k]] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int k = 0; k < kPer; ++k)
+                if (src_i[k] >= 0)
+                    dst.ch(c0 + c)[p0 + tid + k * kResortThreads] = v[c][k];
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (src_i[k] < 0)
+            continue;
+        const int64_t o = p0 + tid + k * kResortThreads;
+        dst.mat[o] = src.mat[p0 + src_i[k]];
+        dst.id[o] = src.id[p0 + src_i[k]];
     }
 }
 
