@@ -449,7 +449,8 @@ KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "t
                         "chunk4": "k_p2g_chunk<4, false>", "chunk8": "k_p2g_chunk<8, false>", "stage4": "k_p2g_stage<4>",
                         "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
-                        "occ": "k_g2p_occ", "stage": "k_g2p_stage"}}
+                        "occ": "k_g2p_occ<8>", "stage": "k_g2p_stage",
+                        "occ10": "k_g2p_occ<10>"}}
 
 
 FUSED_SCATTER_VARIANTS = (0, 3, 4, 7)
@@ -494,7 +495,7 @@ def main():
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
                          "6 stage8, 7 sacc4); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
-                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage); -1 = autotune")
+                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10); -1 = autotune")
     ap.add_argument("--profile-substeps", type=int, default=0,
                     help="profiler mode: run this many substeps of the snow scene with the given variants "
                          "(default chunk4 P2G, occ G2P), print one status line and exit; no timing")

@@ -106,7 +106,8 @@ typedef struct {
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64
                               registers, 5 the same with each CTA's particle inputs and
-                              2x2x2-block grid tile staged by bulk asynchronous copies */
+                              2x2x2-block grid tile staged by bulk asynchronous copies,
+                              6 thread per particle at 48 registers */
     int32_t no_sort;       /* ablation (Sec. 6 sorting study): 1 = a rebuild maps the blocks
                               but leaves the particles in their storage order (no sort, no
                               permutation; mpm_read_order then returns MPM_EINVAL); results

@@ -46,7 +46,8 @@ enum G2PVariant : int {
     G2P_TILE = 3,     // CTA stages its grid tile in shared memory, gathers from there
     G2P_OCC = 4,      // thread per particle capped at 64 registers (occupancy)
     G2P_STAGE = 5,    // OCC with particle inputs and a 2x2x2-block grid tile staged by bulk async copies
-    kG2PVariants = 6
+    G2P_OCC10 = 6,    // thread per particle capped at 48 registers (10 CTAs of 128 per SM)
+    kG2PVariants = 7
 };
 
 // Device status word bits.

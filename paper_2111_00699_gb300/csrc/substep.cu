@@ -812,11 +812,14 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
     g2p_finish(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err);
 }
 
-// G2P_OCC: the thread-per-particle G2P capped at 64 registers (8 CTAs of 128
-// per SM) to trade register pressure for occupancy.
-__global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_occ(SimParams sp, PartView pv, GridView gv, int64_t n,
-                                                                float dt, uint32_t* __restrict__ flags,
-                                                                uint32_t* __restrict__ err)
+// G2P_OCC / G2P_OCC10: the thread-per-particle G2P capped at 64 (48)
+// registers, 8 (10) CTAs of 128 per SM, trading register spills for
+// occupancy.
+template <int MinBlocks>
+__global__ void __launch_bounds__(kTransferThreads, MinBlocks) k_g2p_occ(SimParams sp, PartView pv, GridView gv,
+                                                                        int64_t n, float dt,
+                                                                        uint32_t* __restrict__ flags,
+                                                                        uint32_t* __restrict__ err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n)
@@ -1367,7 +1370,9 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
         else if (variant == G2P_TILE)
             k_g2p_tile<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
         else if (variant == G2P_OCC)
-            k_g2p_occ<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+            k_g2p_occ<8><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+        else if (variant == G2P_OCC10)
+            k_g2p_occ<10><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
         else if (variant == G2P_CHUNK8)
             k_g2p_chunk<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
                                                                                                  flags, err);
