@@ -272,7 +272,7 @@ def bench_small_elastic(substeps=100, reps=5):
     stream = torch.cuda.Stream()
     out = {"workload": "small elastic, 8192 particles, 64^3, dt=1e-4, 100 substeps", "unit": "us/substep"}
     for name, fused, graphs in (("separate", False, False), ("separate_graphs", False, True),
-                                ("g2p2g", True, False)):
+                                ("g2p2g", True, False), ("g2p2g_graphs", True, True)):
         best = None
         for _ in range(reps):
             with mpm.Simulator(64, 1 / 64, [mpm.material(mpm.ELASTIC, E=1e4, nu=0.2, rho=1.0)],
@@ -283,7 +283,7 @@ def bench_small_elastic(substeps=100, reps=5):
                 sim.sync()
             best = ms if best is None else min(best, ms)
         out[name] = 1e3 * best / substeps
-    out["value"] = min(out["separate"], out["separate_graphs"], out["g2p2g"])
+    out["value"] = min(out["separate"], out["separate_graphs"], out["g2p2g"], out["g2p2g_graphs"])
     out["particle_substeps_per_s"] = 8192 / (out["value"] * 1e-6)
     return out
 

@@ -101,9 +101,10 @@ struct mpm_ctx {
     // pointer and size a graph captures is fixed until the next rebuild,
     // particle addition, variant or dt change, which drop them all
     bool graphs = false;
-    cudaGraphExec_t gexec[4 * kRing] = {};   // by flag slot, current grid buffer, current particle buffer
+    cudaGraphExec_t gexec[8 * kRing] = {};   // by mode, flag slot, current grid buffer, current particle buffer
     float graph_dt = 0.0f;
     int64_t graph_launches = 0;
+    int64_t graph_drop_step = -1;   // substep of the last drop: that substep launches directly
 
     // host mirror of the block table (refreshed at every rebuild), used to
     // decide on the host whether emitted particles land in mapped blocks
@@ -349,6 +350,9 @@ void enqueue_separate(mpm_ctx* ctx, float dt, int slot)
 
 void drop_graphs(mpm_ctx* ctx)
 {
+    // a context that keeps changing (emission every substep) would capture a
+    // graph per substep: the substep of a drop launches directly instead
+    ctx->graph_drop_step = ctx->step;
     for (auto& g : ctx->gexec)
         if (g) {
             cudaGraphExecDestroy(g);
@@ -678,6 +682,52 @@ static bool host_stencil_mapped(const mpm_ctx* ctx, const float* x, int margin)
 // Fused G2P2G substep (Sec. 4.1): grid update of the primed momentum, then
 // one kernel doing this substep's G2P and the next substep's P2G.  Priming
 // (after a rebuild, a state write or an emission) is one plain P2G.
+// The steady-state fused substep: clear the flag slot, grid update, G2P2G,
+// copy the flags to the pinned ring.
+static void enqueue_fused(mpm_ctx* ctx, float dt, int slot)
+{
+    cudaStream_t s = ctx->stream;
+    const PartView& pv = ctx->pv[ctx->cur];
+    cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s);
+    GridView gv = grid_view(ctx);
+    cudaEvent_t e1 = nullptr, e2 = nullptr;
+    prof_begin(ctx, e1);
+    launch_grid_update(ctx->sp, gv, dt, s);
+    prof_end(ctx, 2, e1);
+    prof_begin(ctx, e2);
+    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.p2g_variant, s);
+    prof_end(ctx, 3, e2);
+    cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s);
+}
+
+// Replays the steady-state substep of the current mode from its CUDA graph,
+// capturing it on first use; graphs are keyed by mode, flag slot, current
+// grid buffer and current particle buffer.
+static cudaError_t replay(mpm_ctx* ctx, float dt, int slot, bool fused)
+{
+    cudaStream_t s = ctx->stream;
+    const int gi = 16 * (fused ? 1 : 0) + 4 * slot + 2 * ctx->gcur + ctx->cur;
+    if (!ctx->gexec[gi]) {
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess)
+            return e;
+        if (fused)
+            enqueue_fused(ctx, dt, slot);
+        else
+            enqueue_separate(ctx, dt, slot);
+        e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess)
+            return e;
+        e = cudaGraphInstantiate(&ctx->gexec[gi], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return e;
+    }
+    ctx->graph_launches += 1;
+    return cudaGraphLaunch(ctx->gexec[gi], s);
+}
+
 static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
 {
     cudaStream_t s = ctx->stream;
@@ -697,17 +747,12 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
         ctx->launches += 1;
         ctx->primed = true;
     }
-    CK(cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s));
-    GridView gv = grid_view(ctx);
-    cudaEvent_t e1 = nullptr, e2 = nullptr;
-    prof_begin(ctx, e1);
-    launch_grid_update(ctx->sp, gv, dt, s);
-    prof_end(ctx, 2, e1);
-    prof_begin(ctx, e2);
-    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.p2g_variant, s);
-    prof_end(ctx, 3, e2);
+    if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step && dt == ctx->graph_dt) {
+        CK(replay(ctx, dt, slot, true));
+    } else {
+        enqueue_fused(ctx, dt, slot);
+    }
     ctx->launches += 2;
-    CK(cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(ctx->ev[slot], s));
     CK(cudaGetLastError());
     ctx->gcur = 1 - ctx->gcur;   // grid[gcur] now holds the momentum of the new state
@@ -807,6 +852,10 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     }
     cudaStream_t s = ctx->stream;
     int slot = (int)(ctx->step % kRing);
+    if (ctx->graphs && dt != ctx->graph_dt) {
+        drop_graphs(ctx);   // captured graphs hold dt
+        ctx->graph_dt = dt;
+    }
     const int64_t since = ctx->step - (ctx->last_resort > ctx->last_rebuild ? ctx->last_resort : ctx->last_rebuild);
     if (ctx->cfg.resort_interval > 0 && !ctx->cfg.no_sort && since >= ctx->cfg.resort_interval) {
         launch_resort_window(ctx->sp, ctx->pv[ctx->cur], ctx->pv[1 - ctx->cur], ctx->n, s);
@@ -817,23 +866,8 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     }
     if (ctx->cfg.use_g2p2g)
         return substep_fused(ctx, dt, slot);
-    if (ctx->graphs && !ctx->prof) {
-        if (dt != ctx->graph_dt) {
-            drop_graphs(ctx);
-            ctx->graph_dt = dt;
-        }
-        const int gi = 4 * slot + 2 * ctx->gcur + ctx->cur;
-        if (!ctx->gexec[gi]) {
-            cudaGraph_t graph;
-            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            enqueue_separate(ctx, dt, slot);
-            CK(cudaStreamEndCapture(s, &graph));
-            cudaError_t e = cudaGraphInstantiate(&ctx->gexec[gi], graph, 0);
-            cudaGraphDestroy(graph);
-            CK(e);
-        }
-        CK(cudaGraphLaunch(ctx->gexec[gi], s));
-        ctx->graph_launches += 1;
+    if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step && dt == ctx->graph_dt) {
+        CK(replay(ctx, dt, slot, false));
     } else {
         enqueue_separate(ctx, dt, slot);
     }

@@ -678,17 +678,19 @@ def test_g2p2g_matches_oracle(M, kind, scatter):
     assert linf(g["Jp"], s.Jp) <= 1e-4
 
 
-def test_g2p2g_rebuilds_switches_and_reads(M):
+@pytest.mark.parametrize("graphs", [False, True])
+def test_g2p2g_rebuilds_switches_and_reads(M, graphs):
     """Fused mode with a fast block (rebuilds through the two-cell margin),
     switching to separate phases and back mid-run, and reading the state in
-    between: every segment matches the oracle."""
+    between: every segment matches the oracle, with and without graph replay
+    of both modes."""
     x = scenes.cube_uniform(4, 3000, 0.3, 0.4)
     gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
     v = np.tile(np.array([30.0, 20.0, 10.0], np.float32), (len(x), 1))
     vol = (1 / 64) ** 3 / 8
     cfg = orc.config(64, 1 / 64, orc.SLIP)
     s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
-    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=True) as sim:
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=True, stream=torch.cuda.Stream(), graphs=graphs) as sim:
         sim.add_particles(x, v=v)
         for fused, steps in ((True, 25), (False, 10), (True, 25)):
             sim.set_g2p2g(fused)
