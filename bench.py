@@ -134,6 +134,24 @@ def oracle_throughput(x, seconds=15.0, max_particles=None, steps=None):
 
 # --------------------------------------------------------------- reference
 
+def max_over_ranks(value, world, device="cuda"):
+    """The largest of `value` over all ranks of the process group: replicas
+    report the time of the slowest one."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(particles_per_rank, substeps, world, ms):
+    """Whole-job particle-substeps/s of `world` replicas that each advanced
+    `particles_per_rank` particles `substeps` times in `ms` (max over ranks)."""
+    return world * particles_per_rank * substeps / (ms / 1e3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -615,12 +633,9 @@ def main():
     launches = st["kernel_launches"] - launches0
     rebuilds = st["rebuilds"] - rebuilds0
     n_pblocks = st["n_pblocks"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     ms_per_step = ms / args.steps
-    value = world * n * args.steps / (ms / 1e3)
+    value = replica_throughput(n, args.steps, world, ms)
 
     # ---- per-phase timing with CUDA events on the simulator's stream ----
     prof_steps = min(args.steps, 1000)
@@ -680,12 +695,9 @@ def main():
                                 Jp=host["Jp"])
         el = time.perf_counter() - t0
         sim.close()
-        if world > 1:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, world)
         state_bytes = n * 4 * (3 + 3 + 9 + 9 + 1)
-        e2e = {"value": world * n * per_frame * args.e2e_frames / el, "unit": UNIT,
+        e2e = {"value": replica_throughput(n, per_frame * args.e2e_frames, world, el * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / per_frame, "d2h_bytes_per_step": state_bytes / per_frame,
                "protocol": "per frame: mpm_write_state of the full state from pinned host memory, %d mpm_substep "
                            "calls, mpm_read_state of the full state into pinned host memory; bytes are per "
