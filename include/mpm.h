@@ -363,6 +363,15 @@ mpm_status mpm_debug_stress(const mpm_material* mat, const float* F, const float
 /* Apply the end-of-G2P return map to n trial F (in place) and Jp. */
 mpm_status mpm_debug_plasticity(const mpm_material* mat, float* F, float* Jp, int64_t n);
 
+/* Failure-detection check of the bounded device waits (no counterpart in
+ * the paper): one CTA waits on a shared-memory mbarrier that expects bytes no
+ * copy will deliver, gives up after max_iter polls (1..65536, each at most
+ * ~1 us) and records the time-out as the staged kernels do.  Returns
+ * MPM_ETIMEOUT when the wait gave up (the expected result), MPM_OK if it
+ * did not, MPM_EINVAL for max_iter out of range.  The device stays usable:
+ * nothing faults, nothing is left in flight.  Synchronous. */
+mpm_status mpm_debug_wait_timeout(int max_iter);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ _PROTOS = {
     "mpm_set_g2p_variant": (I, [P, I]),
     "mpm_set_g2p2g": (I, [P, I]),
     "mpm_use_graphs": (I, [P, I]),
+    "mpm_debug_wait_timeout": (I, [I]),
     "mpm_graph_launches": (I64, [P]),
     "mpm_profile_enable": (I, [P, I]),
     "mpm_profile_read": (I, [P, P, P, I]),

@@ -1138,4 +1138,21 @@ mpm_status mpm_debug_plasticity(const mpm_material* mat, float* F, float* Jp, in
     return cudaDeviceSynchronize() == cudaSuccess && cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ECUDA;
 }
 
+mpm_status mpm_debug_wait_timeout(int max_iter)
+{
+    if (max_iter < 1 || max_iter > (1 << 16))
+        return MPM_EINVAL;
+    uint32_t* err = nullptr;
+    if (cudaMalloc(&err, 4) != cudaSuccess)
+        return MPM_ENOMEM;
+    uint32_t h = 0;
+    cudaMemset(err, 0, 4);
+    launch_debug_wait_timeout(max_iter, err, 0);
+    cudaError_t e = cudaMemcpy(&h, err, 4, cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return MPM_ECUDA;
+    return (h & ST_TIMEOUT) ? MPM_ETIMEOUT : MPM_OK;
+}
+
 }  // extern "C"

@@ -420,6 +420,12 @@ def debug_plasticity(mat, F: torch.Tensor, Jp: torch.Tensor):
     return F.reshape(-1, 3, 3), Jp
 
 
+def debug_wait_timeout(max_iter: int = 1000) -> int:
+    """Run the bounded-wait check (mpm_debug_wait_timeout); returns the status
+    (MPM_ETIMEOUT when the wait gave up, as it should)."""
+    return int(load().mpm_debug_wait_timeout(int(max_iter)))
+
+
 def radix_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32,
                              out: tuple | None = None, stream=None):
     """Stable sort of (key, value) pairs with the library's fixed scratch array

@@ -134,3 +134,9 @@ def test_splitmix64_reference_values():
     out = scenes.splitmix64(np.array([0, 0x9E3779B97F4A7C15, (2 * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF],
                                      dtype=np.uint64))
     assert [int(v) for v in out] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_wait_timeout_check_rejects_bad_limit_without_the_gpu(lib):
+    from paper_2111_00699_gb300 import _lib
+    assert lib.mpm_debug_wait_timeout(0) == _lib.MPM_EINVAL
+    assert lib.mpm_debug_wait_timeout(1 << 20) == _lib.MPM_EINVAL

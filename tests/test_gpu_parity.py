@@ -631,6 +631,21 @@ def test_window_resort_matches_oracle(M, graphs):
     assert stats["rebuilds"] >= 2
 
 
+def test_bounded_wait_times_out_and_device_stays_usable(M):
+    """Failure detection without a fault: a device wait on an mbarrier that no
+    copy completes gives up after its iteration limit and reports
+    MPM_ETIMEOUT; the device then runs a normal substep."""
+    from paper_2111_00699_gb300 import _lib
+    assert M.debug_wait_timeout(1000) == _lib.MPM_ETIMEOUT
+    assert M.debug_wait_timeout(0) == _lib.MPM_EINVAL
+    x = scenes.cube_uniform(0, 2048, 0.4, 0.6)
+    with M.Simulator(64, 1 / 64, [M.material(M.ELASTIC, E=1e4, nu=0.2, rho=1.0)]) as sim:
+        sim.add_particles(x)
+        sim.run(3, 1e-4)
+        sim.sync()
+        assert np.isfinite(sim.read_state()["x"].cpu().numpy()).all()
+
+
 def test_no_sort_ablation_matches_oracle(M):
     """With no_sort = 1 the rebuild maps blocks but leaves the particles in
     their (here shuffled) storage order: the substeps are the same up to
