@@ -28,6 +28,12 @@
 
 using namespace mpm;
 
+namespace mpm {
+// rebuild.cu: one warp polls an mbarrier no copy completes, with the bounded
+// wait of the staged transfer kernels, and sets ST_TIMEOUT when it gives up.
+void launch_debug_wait_timeout(int max_iter, uint32_t* err, cudaStream_t s);
+}  // namespace mpm
+
 namespace {
 
 constexpr int kRing = 4;

@@ -139,6 +139,5 @@ void launch_debug_svd(const float* F, float* U, float* sig, float* V, int64_t n,
 void launch_debug_stress(const MatParams& mp, const float* F, const float* Jp, float* tau, int64_t n,
                          cudaStream_t s);
 void launch_debug_plasticity(const MatParams& mp, float* F, float* Jp, int64_t n, cudaStream_t s);
-void launch_debug_wait_timeout(int max_iter, uint32_t* err, cudaStream_t s);
 
 }  // namespace mpm

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "device_math.cuh"
 #include "internal.h"
 
@@ -370,4 +371,30 @@ void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t
         k_grid_to_dense<<<blocks_for((int64_t)n_pblocks * 64), kBlock, 0, s>>>(sp, grid, pslot, n_pblocks, dense);
 }
 
+}  // namespace mpm
+
+// ---- bounded-wait check -----------------------------------------------------
+// One warp waits on an mbarrier that expects 1024 bytes no copy ever delivers,
+// with the same bounded poll the staged transfer kernels use; when the poll
+// gives up it records ST_TIMEOUT and the kernel returns normally.
+
+namespace mpm {
+namespace {
+__global__ void k_debug_wait_timeout(int max_iter, uint32_t* __restrict__ err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, 1024u);
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 0, max_iter) && threadIdx.x == 0)
+        atomicOr(err, ST_TIMEOUT);
+}
+}  // namespace
+
+void launch_debug_wait_timeout(int max_iter, uint32_t* err, cudaStream_t s)
+{
+    k_debug_wait_timeout<<<1, 32, 0, s>>>(max_iter, err);
+}
 }  // namespace mpm

@@ -1285,22 +1285,6 @@ __global__ void k_debug_plasticity(MatParams m, float* __restrict__ F, float* __
         Jp[p] = 1.0f + jm1;
 }
 
-// Exercises the bounded wait of the staged kernels: an mbarrier expects
-// bytes that no copy will deliver, so the wait gives up after max_iter polls
-// and records ST_TIMEOUT, exactly as a staged kernel does when a copy does
-// not complete.  No copy is issued, so nothing is in flight at exit.
-__global__ void k_debug_wait_timeout(int max_iter, uint32_t* __restrict__ err)
-{
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_arrive_expect_tx(&bar, 1024u);
-    }
-    __syncthreads();
-    if (!mbar_wait(&bar, 0, max_iter) && threadIdx.x == 0)
-        atomicOr(err, ST_TIMEOUT);
-}
-
 inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
 }  // namespace
@@ -1410,11 +1394,6 @@ void launch_debug_stress(const MatParams& mp, const float* F, const float* Jp, f
 {
     if (n > 0)
         k_debug_stress<<<blocks_for(n, 128), 128, 0, s>>>(mp, F, Jp, tau, n);
-}
-
-void launch_debug_wait_timeout(int max_iter, uint32_t* err, cudaStream_t s)
-{
-    k_debug_wait_timeout<<<1, 32, 0, s>>>(max_iter, err);
 }
 
 void launch_debug_plasticity(const MatParams& mp, float* F, float* Jp, int64_t n, cudaStream_t s)
