@@ -50,15 +50,21 @@ class Material(ctypes.Structure):
                 ("friction_M", ctypes.c_double), ("cohesion", ctypes.c_double), ("alpha0", ctypes.c_double)]
 
 
+APIC, ASFLIP = 0, 1
+
+
 class Config(ctypes.Structure):
     _fields_ = [("res", ctypes.c_int32 * 3), ("dx", ctypes.c_double),
                 ("boundary", ctypes.c_int32), ("wall", ctypes.c_int32),
-                ("gravity", ctypes.c_double * 3)]
+                ("gravity", ctypes.c_double * 3),
+                ("transfer", ctypes.c_int32), ("flip_alpha", ctypes.c_double),
+                ("flip_beta_min", ctypes.c_double), ("flip_beta_max", ctypes.c_double)]
 
 
 class Grid(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_int32 * 3), ("dim", ctypes.c_int32 * 3),
-                ("m", ctypes.POINTER(ctypes.c_double)), ("p", ctypes.POINTER(ctypes.c_double))]
+                ("m", ctypes.POINTER(ctypes.c_double)), ("p", ctypes.POINTER(ctypes.c_double)),
+                ("v0", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -115,9 +121,11 @@ def material(kind, E=1e4, nu=0.2, rho=1.0, gamma=7.0, theta_c=2.5e-2, theta_s=7.
                     alpha0)
 
 
-def config(res, dx, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0)) -> Config:
+def config(res, dx, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0), transfer=APIC, flip_alpha=0.0,
+           flip_beta_min=0.0, flip_beta_max=0.0) -> Config:
     r = (ctypes.c_int32 * 3)(*[int(v) for v in (res if hasattr(res, "__len__") else (res,) * 3)])
-    return Config(r, float(dx), int(boundary), int(wall), (ctypes.c_double * 3)(*gravity))
+    return Config(r, float(dx), int(boundary), int(wall), (ctypes.c_double * 3)(*gravity), int(transfer),
+                  float(flip_alpha), float(flip_beta_min), float(flip_beta_max))
 
 
 def _mats(mats):
@@ -190,11 +198,13 @@ class DenseGrid:
         self.dim = np.array(dim, dtype=np.int32)
         self.m = np.zeros(int(np.prod(dim)))
         self.p = np.zeros(3 * int(np.prod(dim)))
+        self.v0 = np.zeros(3 * int(np.prod(dim)))   # grid velocity before forces (ASFLIP)
 
     def cstruct(self) -> Grid:
         return Grid((ctypes.c_int32 * 3)(*self.lo), (ctypes.c_int32 * 3)(*self.dim),
                     self.m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    self.p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                    self.p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    self.v0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
     def mass(self):
         d = self.dim

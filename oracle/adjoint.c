@@ -89,6 +89,8 @@ static void pack(int64_t n, const double* x, const double* v, const double* C, c
 int orc_diff_forward(const orc_config* cfg, double nu, double rho, int64_t n, const double* vol, const double* E,
                      double dt, const double* s_in, double* s_out)
 {
+    if (cfg->transfer != ORC_APIC)
+        return ORC_EINVAL;   /* the reverse pass below is APIC's */
     double* x = malloc(sizeof(double) * 3 * n);
     double* v = malloc(sizeof(double) * 3 * n);
     double* C = malloc(sizeof(double) * 9 * n);
@@ -131,6 +133,8 @@ static void stress_vjp(const orc_material* m, const double F[9], const double ta
 int orc_diff_adjoint(const orc_config* cfg, double nu, double rho, int64_t n, const double* vol, const double* E,
                      double dt, const double* s_in, const double* g_out, double* g_in, double* gE)
 {
+    if (cfg->transfer != ORC_APIC)
+        return ORC_EINVAL;
     const double h = cfg->dx, inv_dx = 1.0 / h, D = 4.0 * inv_dx * inv_dx;
     double* x = malloc(sizeof(double) * 3 * n);
     double* v = malloc(sizeof(double) * 3 * n);
@@ -139,6 +143,7 @@ int orc_diff_adjoint(const orc_config* cfg, double nu, double rho, int64_t n, co
     unpack(n, s_in, x, v, C, F);
     /* ---- forward recomputation of the grid ---- */
     orc_grid g;
+    g.v0 = NULL;
     orc_grid_bounds(n, x, h, g.lo, g.dim);
     int64_t nn = (int64_t)g.dim[0] * g.dim[1] * g.dim[2];
     g.m = calloc(nn, sizeof(double));

@@ -57,12 +57,19 @@ typedef struct {
     double alpha0;     /* NACC: initial hardening state alpha (ln of the plastic volume ratio) */
 } orc_material;
 
+enum { ORC_APIC = 0, ORC_ASFLIP = 1 };
+
 typedef struct {
     int32_t res[3];    /* grid nodes per axis */
     double dx;
     int32_t boundary;  /* ORC_STICKY or ORC_SLIP */
     int32_t wall;      /* wall layer thickness in nodes */
     double gravity[3];
+    int32_t transfer;  /* ORC_APIC, or ORC_ASFLIP (the integrator of the paper's
+                          fountain, Sec. 6.5, after Fei et al. 2021) */
+    double flip_alpha; /* ASFLIP: weight of the particle's own velocity change */
+    double flip_beta_min, flip_beta_max; /* ASFLIP: positional weight when the particle
+                          is compressed (J < 1) / not compressed */
 } orc_config;
 
 typedef struct {
@@ -70,6 +77,7 @@ typedef struct {
     int32_t dim[3];
     double* m;         /* dim0*dim1*dim2 masses */
     double* p;         /* 3 per node: momentum after P2G, velocity after update */
+    double* v0;        /* NULL, or 3 per node: the update writes p/m before any force */
 } orc_grid;
 
 /* Quadratic B-spline weights for fractional offset f in [0.5, 1.5). */
@@ -106,7 +114,8 @@ int orc_p2g(const orc_config* cfg, const orc_material* mats, int64_t n,
  * wall boundary condition.  In place on g->p. */
 void orc_grid_update(const orc_config* cfg, double dt, orc_grid* g);
 
-/* Phase 5, grid-to-particle with the F update and the return mapping. */
+/* Phase 5, grid-to-particle with the F update and the return mapping.
+ * ASFLIP (cfg->transfer) needs g->v0 filled by orc_grid_update. */
 int orc_g2p(const orc_config* cfg, const orc_material* mats, int64_t n,
             double* x, double* v, double* C, double* F, double* Jp,
             const int32_t* mat, double dt, const orc_grid* g);

@@ -17,6 +17,16 @@
  *         x_p += dt v_p,  F_p <- (I + dt C_p) F_p, then the return map;
  *         fluid: J_p <- (1 + dt tr C_p) J_p and F is left unchanged.
  * m_p = rho_mat * V_p.
+ *
+ * ASFLIP (Fei et al. 2021; the integrator of the paper's fountain, Sec. 6.5)
+ * changes only the particle velocity and position of G2P.  With
+ * vbar_p = sum w_ip v_i (the new grid velocity, as above) and
+ * v0_p = sum w_ip v0_i, v0_i = p_i / m_i the grid velocity before any force:
+ *         v_p <- vbar_p + alpha (v_p - v0_p)
+ *         x_p <- x_p + dt [ vbar_p + beta alpha (v_p(old) - v0_p) ]
+ * with beta = beta_min if the particle is compressed (J < 1, J = det F, the
+ * tracked J for the fluid, taken before this G2P) and beta_max otherwise.
+ * C_p, F_p and J_p are updated exactly as in APIC.  alpha = beta = 0 is APIC.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -24,6 +34,13 @@
 #include "oracle.h"
 
 #define AT(M, r, c) (M)[3 * (r) + (c)]
+
+static double det3(const double* M)
+{
+    return AT(M, 0, 0) * (AT(M, 1, 1) * AT(M, 2, 2) - AT(M, 1, 2) * AT(M, 2, 1)) -
+           AT(M, 0, 1) * (AT(M, 1, 0) * AT(M, 2, 2) - AT(M, 1, 2) * AT(M, 2, 0)) +
+           AT(M, 0, 2) * (AT(M, 1, 0) * AT(M, 2, 1) - AT(M, 1, 1) * AT(M, 2, 0));
+}
 
 static void base_and_weights(const double* xp, double inv_dx, int32_t base[3],
                              double fx[3], double w[3][3])
@@ -117,8 +134,13 @@ void orc_grid_update(const orc_config* cfg, double dt, orc_grid* g)
         double* vi = &g->p[3 * id];
         if (!(g->m[id] > 0.0)) {
             vi[0] = vi[1] = vi[2] = 0.0;
+            if (g->v0)
+                g->v0[3 * id] = g->v0[3 * id + 1] = g->v0[3 * id + 2] = 0.0;
             continue;
         }
+        if (g->v0)
+            for (int a = 0; a < 3; ++a)
+                g->v0[3 * id + a] = vi[a] / g->m[id];
         for (int a = 0; a < 3; ++a)
             vi[a] = vi[a] / g->m[id] + dt * cfg->gravity[a];
         for (int a = 0; a < 3; ++a) {
@@ -142,10 +164,13 @@ int orc_g2p(const orc_config* cfg, const orc_material* mats, int64_t n,
 {
     double h = cfg->dx, inv_dx = 1.0 / h;
     int status = ORC_OK;
+    int asflip = cfg->transfer == ORC_ASFLIP;
+    if (asflip && !g->v0)
+        return ORC_EINVAL;
     for (int64_t p = 0; p < n; ++p) {
         const orc_material* M = &mats[mat[p]];
         int32_t base[3];
-        double f[3], w[3][3], vp[3] = {0, 0, 0}, B[9] = {0};
+        double f[3], w[3][3], vp[3] = {0, 0, 0}, B[9] = {0}, v0p[3] = {0, 0, 0};
         base_and_weights(&x[3 * p], inv_dx, base, f, w);
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j)
@@ -165,14 +190,26 @@ int orc_g2p(const orc_config* cfg, const orc_material* mats, int64_t n,
                         vp[a] += wt * vi[a];
                         for (int b = 0; b < 3; ++b)
                             AT(B, a, b) += wt * vi[a] * d[b];
+                        if (asflip)
+                            v0p[a] += wt * g->v0[3 * id + a];
                     }
                 }
         double* Cp = &C[9 * p];
         for (int e = 0; e < 9; ++e)
             Cp[e] = 4.0 * inv_dx * inv_dx * B[e];
-        for (int a = 0; a < 3; ++a) {
-            v[3 * p + a] = vp[a];
-            x[3 * p + a] += dt * vp[a];
+        if (asflip) {
+            double J = M->kind == ORC_FLUID ? Jp[p] : det3(&F[9 * p]);
+            double beta = J < 1.0 ? cfg->flip_beta_min : cfg->flip_beta_max;
+            for (int a = 0; a < 3; ++a) {
+                double dv = v[3 * p + a] - v0p[a];
+                x[3 * p + a] += dt * (vp[a] + beta * cfg->flip_alpha * dv);
+                v[3 * p + a] = vp[a] + cfg->flip_alpha * dv;
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                v[3 * p + a] = vp[a];
+                x[3 * p + a] += dt * vp[a];
+            }
         }
         if (M->kind == ORC_FLUID) {
             Jp[p] *= 1.0 + dt * (AT(Cp, 0, 0) + AT(Cp, 1, 1) + AT(Cp, 2, 2));
@@ -202,9 +239,11 @@ int orc_substep(const orc_config* cfg, const orc_material* mats, int64_t n,
     int64_t nn = (int64_t)g.dim[0] * g.dim[1] * g.dim[2];
     g.m = (double*)calloc(nn > 0 ? nn : 1, sizeof(double));
     g.p = (double*)calloc(nn > 0 ? 3 * nn : 1, sizeof(double));
-    if (!g.m || !g.p) {
+    g.v0 = cfg->transfer == ORC_ASFLIP ? (double*)calloc(nn > 0 ? 3 * nn : 1, sizeof(double)) : NULL;
+    if (!g.m || !g.p || (cfg->transfer == ORC_ASFLIP && !g.v0)) {
         free(g.m);
         free(g.p);
+        free(g.v0);
         return ORC_EINVAL;
     }
     int s1 = orc_p2g(cfg, mats, n, x, v, C, F, Jp, vol, mat, dt, &g);
@@ -212,6 +251,7 @@ int orc_substep(const orc_config* cfg, const orc_material* mats, int64_t n,
     int s2 = orc_g2p(cfg, mats, n, x, v, C, F, Jp, mat, dt, &g);
     free(g.m);
     free(g.p);
+    free(g.v0);
     return s1 != ORC_OK ? s1 : s2;
 }
 

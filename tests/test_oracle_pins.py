@@ -464,6 +464,77 @@ def test_substep_is_phase_composition(orc):
         np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
 
 
+# ------------------------------------------------------------------ ASFLIP
+
+@pytest.mark.parametrize("J_F", [1.0, 0.9, 1.1])
+def test_asflip_two_coincident_particles_closed_form(orc, J_F):
+    """Two particles at one point, zero stress (E = 0), no gravity, no wall:
+    every node of their common stencil carries their mean velocity vbar,
+    before and after the grid update, so APIC would give both vbar.  ASFLIP
+    (Fei et al. 2021) keeps alpha times each particle's deviation v - vbar in
+    its velocity and beta alpha times it in its motion, beta = beta_min when
+    J = det F < 1 and beta_max otherwise (three distinct weights, so that a
+    swapped or dropped one fails)."""
+    dx = 1 / 32
+    alpha, bmin, bmax = 0.9, 0.3, 0.7
+    cfg = orc.config(32, dx, gravity=(0.0, 0.0, 0.0), transfer=orc.ASFLIP, flip_alpha=alpha,
+                     flip_beta_min=bmin, flip_beta_max=bmax)
+    mat = orc.material(orc.ELASTIC, E=0.0)
+    xp = np.array([0.503, 0.49, 0.51])
+    v = np.array([[0.3, -0.1, 0.2], [-0.1, 0.25, 0.0]])
+    F = np.diag([J_F, 1.0, 1.0])
+    s = orc.State(np.tile(xp, (2, 1)), v, F=np.tile(F, (2, 1, 1)), vol=1e-5)
+    dt = 1e-3
+    assert orc.substep(cfg, mat, s, dt) == 0
+    vbar = v.mean(0)
+    beta = bmin if J_F < 1 else bmax
+    np.testing.assert_allclose(s.v, vbar + alpha * (v - vbar), atol=1e-13)
+    np.testing.assert_allclose(s.x, xp + dt * (vbar + beta * alpha * (v - vbar)), atol=1e-15)
+    np.testing.assert_allclose(s.C, 0, atol=1e-10)
+    np.testing.assert_allclose(s.F, np.tile(F, (2, 1, 1)), atol=1e-12)
+
+
+def test_asflip_with_zero_weights_is_apic(orc):
+    """alpha = beta = 0 reduces ASFLIP to APIC exactly, all materials."""
+    rng = np.random.default_rng(61)
+    dx = 1 / 32
+    mats = [orc.material(orc.ELASTIC), orc.material(orc.SNOW, E=1.4e5, rho=400.0),
+            orc.material(orc.FLUID, E=1e4, rho=1000.0), orc.material(orc.SAND, E=3.5e5, nu=0.3, rho=2200.0)]
+    s = _random_state(orc, rng, 120, 0.3, 0.7, dx, F_noise=0.01, C_scale=0.1, v_scale=0.1)
+    s.mat[:] = rng.integers(0, 4, s.n)
+    s.Jp[:] = 1.0
+    a, b = s.copy(), s.copy()
+    orc.substep(orc.config(32, dx, orc.SLIP), mats, a, 1e-4)
+    orc.substep(orc.config(32, dx, orc.SLIP, transfer=orc.ASFLIP, flip_beta_max=0.0), mats, b, 1e-4)
+    for f in ("x", "v", "C", "F", "Jp"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_asflip_keeps_the_momentum_and_centre_of_mass_of_apic(orc):
+    """v0_i = p_i / m_i after P2G, so sum_p m_p v0_p = sum_i p_i = sum_p m_p
+    v_p (the moments of the weights vanish): the blended-in deviations carry
+    no net momentum.  Hence for any alpha the total particle momentum after
+    G2P equals APIC's, and with one beta for all particles so does the mass
+    centre.  A v0 taken after gravity or the walls breaks both (gravity on,
+    sticky walls reached by some stencils)."""
+    rng = np.random.default_rng(62)
+    dx = 1 / 32
+    mat = orc.material(orc.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    s = _random_state(orc, rng, 300, 0.08, 0.5, dx, F_noise=0.02, C_scale=0.5, v_scale=0.5)
+    a, b = s.copy(), s.copy()
+    dt = 1e-4
+    orc.substep(orc.config(32, dx, orc.STICKY), mat, a, dt)
+    orc.substep(orc.config(32, dx, orc.STICKY, transfer=orc.ASFLIP, flip_alpha=0.8, flip_beta_min=0.6,
+                           flip_beta_max=0.6), mat, b, dt)
+    m = s.vol[:, None] * 1000.0
+    pa, pb = (m * a.v).sum(0), (m * b.v).sum(0)
+    assert np.abs(pb - pa).max() <= 1e-12 * np.abs(m * s.v).sum()
+    assert np.abs(b.v - a.v).max() > 1e-3            # the blend did change the particles
+    np.testing.assert_allclose((m * b.x).sum(0), (m * a.x).sum(0), rtol=1e-13)
+    np.testing.assert_array_equal(a.C, b.C)
+    np.testing.assert_array_equal(a.F, b.F)
+
+
 # -------------------------------------------------------- keys, sort, pblocks
 
 def _morton(c, bits):
