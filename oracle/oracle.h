@@ -69,7 +69,7 @@ typedef struct {
                           fountain, Sec. 6.5, after Fei et al. 2021) */
     double flip_alpha; /* ASFLIP: weight of the particle's own velocity change */
     double flip_beta_min, flip_beta_max; /* ASFLIP: positional weight when the particle
-                          is compressed (J < 1) / not compressed */
+                          is compressed (J < 1 - 1e-4) / not compressed */
 } orc_config;
 
 typedef struct {

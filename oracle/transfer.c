@@ -24,8 +24,11 @@
  * v0_p = sum w_ip v0_i, v0_i = p_i / m_i the grid velocity before any force:
  *         v_p <- vbar_p + alpha (v_p - v0_p)
  *         x_p <- x_p + dt [ vbar_p + beta alpha (v_p(old) - v0_p) ]
- * with beta = beta_min if the particle is compressed (J < 1, J = det F, the
- * tracked J for the fluid, taken before this G2P) and beta_max otherwise.
+ * with beta = beta_min if the particle is compressed and beta_max otherwise.
+ * Compressed means J < 1 - 1e-4 (J = det F, the tracked J for the fluid,
+ * taken before this G2P): the sand return map sets every particle under
+ * tension to J = 1 exactly, where the rounding of det F (FP32 ~1e-6) would
+ * otherwise choose beta at random; such particles count as not compressed.
  * C_p, F_p and J_p are updated exactly as in APIC.  alpha = beta = 0 is APIC.
  */
 #include <math.h>
@@ -199,7 +202,7 @@ int orc_g2p(const orc_config* cfg, const orc_material* mats, int64_t n,
             Cp[e] = 4.0 * inv_dx * inv_dx * B[e];
         if (asflip) {
             double J = M->kind == ORC_FLUID ? Jp[p] : det3(&F[9 * p]);
-            double beta = J < 1.0 ? cfg->flip_beta_min : cfg->flip_beta_max;
+            double beta = J < 1.0 - 1e-4 ? cfg->flip_beta_min : cfg->flip_beta_max;
             for (int a = 0; a < 3; ++a) {
                 double dv = v[3 * p + a] - v0p[a];
                 x[3 * p + a] += dt * (vp[a] + beta * cfg->flip_alpha * dv);

@@ -466,15 +466,16 @@ def test_substep_is_phase_composition(orc):
 
 # ------------------------------------------------------------------ ASFLIP
 
-@pytest.mark.parametrize("J_F", [1.0, 0.9, 1.1])
+@pytest.mark.parametrize("J_F", [1.0, 0.9, 1.1, 0.99995, 0.9998])
 def test_asflip_two_coincident_particles_closed_form(orc, J_F):
     """Two particles at one point, zero stress (E = 0), no gravity, no wall:
     every node of their common stencil carries their mean velocity vbar,
     before and after the grid update, so APIC would give both vbar.  ASFLIP
     (Fei et al. 2021) keeps alpha times each particle's deviation v - vbar in
     its velocity and beta alpha times it in its motion, beta = beta_min when
-    J = det F < 1 and beta_max otherwise (three distinct weights, so that a
-    swapped or dropped one fails)."""
+    the particle is compressed, J = det F < 1 - 1e-4, and beta_max otherwise
+    (three distinct weights, so that a swapped or dropped one fails; J within
+    1e-4 below 1 counts as not compressed)."""
     dx = 1 / 32
     alpha, bmin, bmax = 0.9, 0.3, 0.7
     cfg = orc.config(32, dx, gravity=(0.0, 0.0, 0.0), transfer=orc.ASFLIP, flip_alpha=alpha,
@@ -487,7 +488,7 @@ def test_asflip_two_coincident_particles_closed_form(orc, J_F):
     dt = 1e-3
     assert orc.substep(cfg, mat, s, dt) == 0
     vbar = v.mean(0)
-    beta = bmin if J_F < 1 else bmax
+    beta = bmin if J_F < 1 - 1e-4 else bmax
     np.testing.assert_allclose(s.v, vbar + alpha * (v - vbar), atol=1e-13)
     np.testing.assert_allclose(s.x, xp + dt * (vbar + beta * alpha * (v - vbar)), atol=1e-15)
     np.testing.assert_allclose(s.C, 0, atol=1e-10)
