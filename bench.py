@@ -251,17 +251,20 @@ def bench_batched(steps=100, warmup=5):
     return out
 
 
-def bench_fountain(substeps=3600):
+def bench_fountain(substeps=3600, asflip=False):
     """Fountain: weakly compressible fluid (K 1e4, gamma 7) emitted through a
-    disk inlet every substep up to the 143K-particle budget, 128^3, dt 1e-4."""
+    disk inlet every substep up to the 143K-particle budget, 128^3, dt 1e-4.
+    asflip: the ASFLIP transfer the paper's fountain uses (alpha 0.95, beta 0
+    compressed / 1 otherwise) instead of APIC."""
     import torch
     from paper_2111_00699_gb300 import mpm, scenes
     res, dt = 128, 1e-4
     vol = (1.0 / res) ** 3 / 8
     batches = [scenes.fountain_batch(2, k, dt, vol) for k in range(substeps)]
     stream = torch.cuda.Stream()
+    flip = dict(transfer=mpm.ASFLIP, flip_alpha=0.95, flip_beta_min=0.0, flip_beta_max=1.0) if asflip else {}
     with mpm.Simulator(res, 1.0 / res, [mpm.material(mpm.FLUID, E=1e4, gamma=7.0, rho=1000.0)],
-                       boundary=mpm.SLIP, stream=stream, p2g_variant=3, g2p_variant=0) as sim:
+                       boundary=mpm.SLIP, stream=stream, p2g_variant=3, g2p_variant=0, **flip) as sim:
         def run():
             for xe, ve in batches:
                 sim.emit_particles(xe, v=ve)
@@ -272,7 +275,8 @@ def bench_fountain(substeps=3600):
         st = sim.stats()
     ps = sum(len(b[0]) * (substeps - k) for k, b in enumerate(batches))
     frame = round((1.0 / 60.0) / dt)
-    return {"workload": "fountain, %d substeps, %d particles at the end, 128^3, dt=1e-4" % (substeps, n_end),
+    return {"workload": "fountain%s, %d substeps, %d particles at the end, 128^3, dt=1e-4"
+                        % (" (ASFLIP)" if asflip else "", substeps, n_end),
             "value": ps / (ms / 1e3), "unit": UNIT, "ms_per_substep": ms / substeps,
             "ms_per_frame": ms / substeps * frame, "particles_end": n_end, "rebuilds": st["rebuilds"]}
 
@@ -711,7 +715,8 @@ def main():
     workloads = None
     if not args.no_workloads and world == 1:
         workloads = {}
-        for name, fn in (("batched", bench_batched), ("fountain", bench_fountain), ("sand", bench_sand),
+        for name, fn in (("batched", bench_batched), ("fountain", bench_fountain),
+                         ("fountain_asflip", lambda: bench_fountain(asflip=True)), ("sand", bench_sand),
                          ("nacc_snow", bench_nacc_snow),
                          ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
                          ("ablations", bench_ablations), ("fast_math", bench_fast_math)):

@@ -117,8 +117,23 @@ typedef struct {
                               (block, cell) key, so that P2G keeps merging runs of particles
                               in one cell; 0: only the sort at rebuild (Sec. 4.2.2).  Same
                               results up to floating-point summation order. */
-    int32_t reserved[3];
+    int32_t transfer;      /* MPM_APIC (0): G2P sets v_p to the interpolated new grid velocity
+                              vbar_p and moves x_p by dt vbar_p.  MPM_ASFLIP (1): the
+                              integrator of the paper's fountain (Sec. 6.5, after Fei et al.
+                              2021): with v0_p the interpolated grid velocity before forces,
+                              v_p <- vbar_p + flip_alpha (v_p - v0_p) and
+                              x_p <- x_p + dt (vbar_p + beta flip_alpha (v_p(old) - v0_p)),
+                              beta = flip_beta_min if J < 1 - 1e-4 (det F; the fluid's J)
+                              else flip_beta_max.  C, F and J update as in APIC.  ASFLIP keeps a
+                              third grid buffer, always gathers with one thread per particle
+                              (g2p_variant is ignored) and needs use_g2p2g = 0. */
+    float flip_alpha;      /* ASFLIP, in [0, 1] */
+    float flip_beta_min;   /* ASFLIP, in [0, 1] */
+    float flip_beta_max;   /* ASFLIP, in [0, 1] */
+    int32_t reserved[2];
 } mpm_config;
+
+enum { MPM_APIC = 0, MPM_ASFLIP = 1 };
 
 /* Device memory provider.  alloc returns device memory usable on `stream`
  * or NULL; free releases it.  Pass NULL to mpm_create to use
@@ -239,7 +254,8 @@ void mpm_batch_destroy(mpm_batch* b);
  * (checkpointing is the caller's choice). */
 typedef struct mpm_diff mpm_diff; /* opaque */
 
-/* vol0: n device floats, or NULL for dx^3/8 each. */
+/* vol0: n device floats, or NULL for dx^3/8 each.  cfg->transfer must be
+ * MPM_APIC (else MPM_EINVAL). */
 mpm_status mpm_diff_create(const mpm_config* cfg, float nu, float rho, int64_t n, const float* vol0,
                            const mpm_allocator* allocator, void* cuda_stream, mpm_diff** out);
 /* s_out = one substep of s_in with moduli E (n floats); s_out must not alias s_in. */
@@ -290,7 +306,8 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant);
 /* Same for the G2P gather variant (mpm_config.g2p_variant). */
 mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
 /* Switch between separate phases (0) and the fused G2P2G transfer (1)
- * between substeps (mpm_config.use_g2p2g). */
+ * between substeps (mpm_config.use_g2p2g).  MPM_EINVAL for on = 1 when the
+ * context uses MPM_ASFLIP. */
 mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on);
 
 /* Replay the separate substep (flag clear, P2G, grid update, G2P, flag

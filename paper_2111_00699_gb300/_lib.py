@@ -21,6 +21,7 @@ STATUS_NAMES = ["MPM_OK", "MPM_EINVAL", "MPM_ENOMEM", "MPM_ECAPACITY", "MPM_EDOM
                 "MPM_ETIMEOUT", "MPM_ECUDA", "MPM_ENOTSUP"]
 ELASTIC, FLUID, SNOW, SAND, NACC = 0, 1, 2, 3, 4
 STICKY, SLIP = 0, 1
+APIC, ASFLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
 P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4")
@@ -38,7 +39,9 @@ class Config(ctypes.Structure):
     _fields_ = [("res", ctypes.c_int32 * 3), ("dx", ctypes.c_float), ("boundary", ctypes.c_int32),
                 ("wall", ctypes.c_int32), ("gravity", ctypes.c_float * 3), ("max_particles", ctypes.c_int64),
                 ("use_g2p2g", ctypes.c_int32), ("p2g_variant", ctypes.c_int32), ("g2p_variant", ctypes.c_int32),
-                ("no_sort", ctypes.c_int32), ("resort_interval", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("no_sort", ctypes.c_int32), ("resort_interval", ctypes.c_int32), ("transfer", ctypes.c_int32),
+                ("flip_alpha", ctypes.c_float), ("flip_beta_min", ctypes.c_float), ("flip_beta_max", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

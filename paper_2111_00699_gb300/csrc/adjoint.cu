@@ -620,6 +620,8 @@ mpm_status mpm_diff_create(const mpm_config* cfg, float nu, float rho, int64_t n
 {
     if (!cfg || !out || n <= 0 || !(rho > 0.f) || !(nu > -1.f && nu < 0.5f) || !(cfg->dx > 0.f))
         return MPM_EINVAL;
+    if (cfg->transfer != MPM_APIC)
+        return MPM_EINVAL;   // the differentiable substep is APIC only
     for (int a = 0; a < 3; ++a)
         if (cfg->res[a] < 8 || cfg->res[a] > 512)
             return MPM_EINVAL;

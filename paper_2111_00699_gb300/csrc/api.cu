@@ -71,6 +71,7 @@ struct mpm_ctx {
     int32_t n_pblocks = 0;
     int64_t grid_cap = 0;
     float4* grid[2] = {nullptr, nullptr};
+    float4* gold = nullptr;   // ASFLIP: grid velocity before forces, same layout and capacity
     int gcur = 0;
 
     // sort
@@ -329,6 +330,7 @@ GridView grid_view(mpm_ctx* ctx)
     g.table = ctx->table;
     g.pslot = ctx->pslot;
     g.interior = ctx->interior;
+    g.old = ctx->cfg.transfer == MPM_ASFLIP ? ctx->gold : nullptr;
     g.n_pblocks = ctx->n_pblocks;
     return g;
 }
@@ -415,6 +417,10 @@ mpm_status rebuild(mpm_ctx* ctx)
         mpm_status st;
         if ((st = realloc_buf(ctx, ctx->grid[0], have0, (size_t)gcap * 1024)) != MPM_OK) return st;
         if ((st = realloc_buf(ctx, ctx->grid[1], have1, (size_t)gcap * 1024)) != MPM_OK) return st;
+        if (ctx->cfg.transfer == MPM_ASFLIP) {
+            size_t have2 = (size_t)ctx->grid_cap * 1024;
+            if ((st = realloc_buf(ctx, ctx->gold, have2, (size_t)gcap * 1024)) != MPM_OK) return st;
+        }
         ctx->grid_cap = gcap;
     }
     if (npb > 0) {
@@ -471,6 +477,16 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         return MPM_EINVAL;
     if (cfg->resort_interval < 0)
         return MPM_EINVAL;
+    if (cfg->transfer != MPM_APIC && cfg->transfer != MPM_ASFLIP)
+        return MPM_EINVAL;
+    if (cfg->transfer == MPM_ASFLIP) {
+        const float w[3] = {cfg->flip_alpha, cfg->flip_beta_min, cfg->flip_beta_max};
+        for (float v : w)
+            if (!(v >= 0.f && v <= 1.f))
+                return MPM_EINVAL;
+        if (cfg->use_g2p2g)
+            return MPM_EINVAL;   // the fused transfer has no ASFLIP form
+    }
     if (cfg->p2g_variant < 0 || cfg->p2g_variant >= kP2GVariants)
         return MPM_EINVAL;
     if (cfg->g2p_variant < 0 || cfg->g2p_variant >= kG2PVariants)
@@ -498,6 +514,10 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
     sp.inv_dx = 1.0f / cfg->dx;
     sp.boundary = cfg->boundary;
     sp.wall = cfg->wall;
+    sp.transfer = cfg->transfer;
+    sp.flip_alpha = cfg->transfer == MPM_ASFLIP ? cfg->flip_alpha : 0.f;
+    sp.flip_beta_min = cfg->transfer == MPM_ASFLIP ? cfg->flip_beta_min : 0.f;
+    sp.flip_beta_max = cfg->transfer == MPM_ASFLIP ? cfg->flip_beta_max : 0.f;
     int L = 0;
     while ((4 << L) < maxres)
         ++L;
@@ -591,6 +611,7 @@ void mpm_destroy(mpm_ctx* ctx)
     dfree(ctx, ctx->scan_scr, ctx->scan_scr_bytes);
     dfree(ctx, ctx->grid[0], (size_t)ctx->grid_cap * 1024);
     dfree(ctx, ctx->grid[1], (size_t)ctx->grid_cap * 1024);
+    dfree(ctx, ctx->gold, (size_t)ctx->grid_cap * 1024);
     size_t kb = (size_t)ctx->sort_cap * 4;
     dfree(ctx, ctx->keys, kb);
     dfree(ctx, ctx->vals, kb);
@@ -1070,6 +1091,8 @@ mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on)
 {
     if (!ctx || (on != 0 && on != 1))
         return MPM_EINVAL;
+    if (on && ctx->cfg.transfer == MPM_ASFLIP)
+        return fail(ctx, MPM_EINVAL, "mpm_set_g2p2g: the fused transfer has no ASFLIP form");
     if (ctx->cfg.use_g2p2g && !on && ctx->primed) {
         // back to separate phases: the next P2G needs a zero grid and the stress
         if (ctx->n_pblocks > 0)

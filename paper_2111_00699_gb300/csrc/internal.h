@@ -76,6 +76,8 @@ struct SimParams {
     int boundary, wall;
     float g[3];
     int L;                   // Morton bits per axis of the block table
+    int transfer;            // MPM_APIC or MPM_ASFLIP
+    float flip_alpha, flip_beta_min, flip_beta_max;
     int n_mats;
     MatParams mat[kMaxMaterials];
 };
@@ -94,6 +96,7 @@ struct GridView {
     const int32_t* table; // Morton slot -> physical block index, or -1
     const int32_t* pslot; // physical block index -> Morton slot
     const uint8_t* interior; // physical block index -> 1 if its 26 neighbours (in the grid) are mapped
+    float4* old;          // ASFLIP: grid velocity before forces (p / m, 0) per node; else null
     int32_t n_pblocks;
 };
 

@@ -602,6 +602,11 @@ __global__ void k_grid(SimParams sp, GridView gv, float dt)
         }
     }
     gv.cur[idx] = make_float4(v[0], v[1], v[2], g.w);
+    if (gv.old) {
+        // ASFLIP: the grid velocity before forces and walls
+        const float im = g.w > 0.0f ? 1.0f / g.w : 0.0f;
+        gv.old[idx] = make_float4(g.x * im, g.y * im, g.z * im, 0.0f);
+    }
 }
 
 // True if every node in [lo, hi] (per axis, clipped to the grid) lies in a
@@ -662,8 +667,10 @@ __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartV
                                                 int64_t p, Get get, int mat, const float* x, const int* b,
                                                 int own_rank, const float* vp, const float* Bm, float dt,
                                                 uint32_t* __restrict__ flags, uint32_t* __restrict__ err,
-                                                G2POut* out)
+                                                G2POut* out, const float* va = nullptr)
 {
+    // va: the velocity that moves the particle, if not vp (ASFLIP)
+    const float* adv = va ? va : vp;
     // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
     float C[9];
     float c4 = 4.0f * sp.inv_dx;
@@ -675,7 +682,7 @@ __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartV
     float xn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        xn[a] = x[a] + dt * vp[a];
+        xn[a] = x[a] + dt * adv[a];
         pv.ch(CH_X + a)[p] = xn[a];
         pv.ch(CH_V + a)[p] = vp[a];
     }
@@ -839,6 +846,77 @@ __global__ void __launch_bounds__(kTransferThreads, MinBlocks) k_g2p_occ(SimPara
         return make_float3(g.x, g.y, g.z);
     }, vp, Bm);
     g2p_finish(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err);
+}
+
+// ASFLIP G2P (Fei et al. 2021, the integrator of the paper's fountain,
+// Sec. 6.5).  Besides the APIC gather of the new grid velocity (vbar, C) it
+// gathers v0, the grid velocity before forces, and blends in the particle's
+// own deviation from it: v <- vbar + alpha (v - v0), and the particle moves
+// with vbar + beta alpha (v - v0), beta = beta_min when the particle is
+// compressed (J < 1 - 1e-4) and beta_max otherwise.  The margin makes the
+// sand particles that the return map put at J = 1 exactly (tension) count as
+// not compressed whatever the rounding of det F.  C, F, J and the free-zone
+// test are those of APIC.  One thread per particle at 64 registers.
+__global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_asflip(SimParams sp, PartView pv, GridView gv,
+                                                                   int64_t n, float dt,
+                                                                   uint32_t* __restrict__ flags,
+                                                                   uint32_t* __restrict__ err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n)
+        return;
+    float x[3], f[3], w[3][3];
+    int b[3];
+    if (!g2p_weights(sp, pv, p, x, b, f, w, err))
+        return;
+    StencilIndex si;
+    if (!stencil_index(gv, b, si)) {
+        atomicOr(err, ST_MISSED);
+        return;
+    }
+    float vp[3], Bm[9];
+    g2p_accumulate(f, w, [&](int i, int j, int k) {
+        const float4 g = gv.cur[si(i, j, k)];
+        return make_float3(g.x, g.y, g.z);
+    }, vp, Bm);
+    float v0[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float wjk = w[1][j] * w[2][k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float4 g = gv.old[si(i, j, k)];
+                const float wt = w[0][i] * wjk;
+                v0[0] = fmaf(wt, g.x, v0[0]);
+                v0[1] = fmaf(wt, g.y, v0[1]);
+                v0[2] = fmaf(wt, g.z, v0[2]);
+            }
+        }
+    // J - 1 before this G2P: the fluid's tracked J, else det(I + H) - 1
+    // formed from H, so that its sign is that of the small quantity itself
+    const int mat = pv.mat[p];
+    float jm1;
+    if (sp.mat[mat].kind == MPM_FLUID) {
+        jm1 = pv.ch(CH_JP)[p];
+    } else {
+        float H[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            H[e] = pv.ch(CH_F + e)[p];
+        jm1 = det_m1(H);
+    }
+    const float beta = jm1 < -1e-4f ? sp.flip_beta_min : sp.flip_beta_max;
+    float vn[3], va[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float dv = pv.ch(CH_V + a)[p] - v0[a];
+        vn[a] = fmaf(sp.flip_alpha, dv, vp[a]);
+        va[a] = fmaf(beta * sp.flip_alpha, dv, vp[a]);
+    }
+    g2p_finish_from<false>(sp, pv, gv, p, [&](int c) { return pv.ch(c)[p]; }, mat, x, b, si.pb64[0] >> 6, vn, Bm,
+                           dt, flags, err, nullptr, va);
 }
 
 // G2P_TILE: shared-memory staging of the block-local grid tile.  The CTA's
@@ -1365,7 +1443,9 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n > 0)
     {
-        if (variant == G2P_STAGE && pv.cap % kCapQuantum == 0)
+        if (sp.transfer == MPM_ASFLIP)
+            k_g2p_asflip<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+        else if (variant == G2P_STAGE && pv.cap % kCapQuantum == 0)
             k_g2p_stage<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
         else if (variant == G2P_TILE)
             k_g2p_tile<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);

@@ -17,6 +17,7 @@ from ._lib import MpmError, load, material  # noqa: F401
 
 ELASTIC, FLUID, SNOW, SAND, NACC = _lib.ELASTIC, _lib.FLUID, _lib.SNOW, _lib.SAND, _lib.NACC
 STICKY, SLIP = _lib.STICKY, _lib.SLIP
+APIC, ASFLIP = _lib.APIC, _lib.ASFLIP
 
 
 def _check(st: int, ctx=None):
@@ -50,7 +51,8 @@ class Simulator:
     def __init__(self, res, dx, materials, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0),
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
                  device=None, p2g_variant: int = 3, g2p_variant: int = 0, g2p2g: bool = False,
-                 no_sort: bool = False, graphs: bool = False, resort_interval: int = 0):
+                 no_sort: bool = False, graphs: bool = False, resort_interval: int = 0, transfer: int = 0,
+                 flip_alpha: float = 0.0, flip_beta_min: float = 0.0, flip_beta_max: float = 0.0):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -72,6 +74,10 @@ class Simulator:
         cfg.g2p_variant = int(g2p_variant)
         cfg.no_sort = 1 if no_sort else 0
         cfg.resort_interval = int(resort_interval)
+        cfg.transfer = int(transfer)
+        cfg.flip_alpha = float(flip_alpha)
+        cfg.flip_beta_min = float(flip_beta_min)
+        cfg.flip_beta_max = float(flip_beta_max)
         mats = (_lib.Material * len(self.materials))(*self.materials)
         self._alloc = None
         if torch_allocator:

@@ -36,7 +36,9 @@ def test_exports_are_c_symbols(lib):
 def test_struct_layouts_match_header(lib):
     from paper_2111_00699_gb300 import _lib
     assert ctypes.sizeof(_lib.Material) == 4 * 12
-    assert ctypes.sizeof(_lib.Config) == 12 + 4 + 4 + 4 + 12 + 4 + 8 + 4 + 28   # with alignment padding
+    # res, dx, boundary, wall, gravity, padding, max_particles, five int32 knobs, transfer and the
+    # three ASFLIP weights, reserved[2], padding to the 8-byte alignment of max_particles
+    assert ctypes.sizeof(_lib.Config) == 12 + 4 + 4 + 4 + 12 + 4 + 8 + 5 * 4 + 4 * 4 + 2 * 4 + 4
     assert ctypes.sizeof(_lib.Stats) == 6 * 8
 
 
@@ -70,6 +72,13 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     bad = _lib.Config.from_buffer_copy(cfg)
     bad.no_sort = 2
     assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
+    for transfer, alpha, bmin, bmax, fused in ((2, 0.0, 0.0, 0.0, 0), (_lib.ASFLIP, 1.5, 0.0, 1.0, 0),
+                                                (_lib.ASFLIP, 0.9, -0.1, 1.0, 0), (_lib.ASFLIP, 0.9, 0.0, float("nan"), 0),
+                                                (_lib.ASFLIP, 0.9, 0.0, 1.0, 1)):
+        bad = _lib.Config.from_buffer_copy(cfg)
+        bad.transfer, bad.flip_alpha, bad.flip_beta_min, bad.flip_beta_max, bad.use_g2p2g = (transfer, alpha, bmin,
+                                                                                             bmax, fused)
+        assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad = _lib.Config.from_buffer_copy(cfg)
     bad.g2p_variant = 7
     assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL

@@ -314,6 +314,55 @@ def test_substeps_materials(M, kind):
     assert linf(g["Jp"], s.Jp) <= 1e-4
 
 
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+def test_asflip_substeps_match_oracle(M, kind):
+    """ASFLIP transfer (alpha 0.95, beta 0 compressed / 1 otherwise, the
+    usual weights) against the oracle over 10 substeps, random velocities and
+    strains so that both beta branches occur; then 20 more substeps from CUDA
+    graphs, where v is held to 1e-3 relative: the particle velocity carries
+    alpha of its own past, FP32 rounding included, so the error grows with the
+    substep count faster than under APIC (the fluid case reached 1.05e-4
+    relative after 30)."""
+    kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
+              snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
+    k = kw.pop("kind")
+    gm, om = mats_pair(M, k, **kw)
+    dt = 5e-5 if k == M.SNOW else 1e-4
+    x, _ = scenes.blocks(14, 20000, 64, 2)
+    vol = (1 / 64) ** 3 / 8
+    rng = np.random.default_rng(4)
+    n = len(x)
+    v = (0.3 * rng.normal(size=(n, 3))).astype(np.float32)
+    F = (np.eye(3) + 0.01 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    flip = dict(flip_alpha=0.95, flip_beta_min=0.0, flip_beta_max=1.0)
+    cfg = orc.config(64, 1 / 64, orc.SLIP, transfer=orc.ASFLIP, **flip)
+    stream = torch.cuda.Stream()
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, transfer=M.ASFLIP, stream=stream, **flip) as sim:
+        sim.add_particles(x, v=v)
+        if k != M.FLUID:
+            sim.write_state(F=torch.from_numpy(F).cuda())
+        else:
+            sim.write_state(Jp=torch.from_numpy(rng.uniform(0.99, 1.01, n).astype(np.float32)).cuda())
+        s = oracle_state_from(sim.read_state(), vol)
+        J = s.Jp if k == M.FLUID else np.linalg.det(s.F)
+        assert (J < 1 - 1e-4).mean() > 0.2 and (J >= 1 - 1e-4).mean() > 0.2
+        g = _run_both(M, sim, [om], s, 10, dt, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        if k != M.FLUID:
+            assert linf(g["F"], s.F) <= 1e-4
+        assert linf(g["Jp"], s.Jp) <= 1e-4
+        sim.use_graphs(True)
+        g = _run_both(M, sim, [om], s, 20, dt, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        assert linf(g["v"], s.v) <= 1e-3 * np.abs(s.v).max()
+        assert sim.graph_launches > 0
+        with pytest.raises(RuntimeError):
+            sim.set_g2p2g(True)
+
+
 def test_ten_substeps_snow_full_size_bench_configuration(M):
     """The 1.34M-particle snow scene in the launch configuration bench.py
     times (register-run P2G, 64-register G2P, CUDA-graph replay on a side
@@ -487,17 +536,20 @@ def test_substeps_variant_combinations(M, p2g, g2p):
 
 # ------------------------------------------------------------- emission (a7)
 
-def test_fountain_emission_parity(M):
+@pytest.mark.parametrize("asflip", [False, True])
+def test_fountain_emission_parity(M, asflip):
     """Fountain: weakly compressible fluid (K = 1e4, gamma = 7, rho = 1000)
     emitted through a disk inlet (r = 0.05, 3 m/s up) every substep on a 128^3
-    grid, dt = 1e-4.  The oracle gets the same particles appended before each
+    grid, dt = 1e-4, with APIC or with the ASFLIP transfer the paper's
+    fountain uses.  The oracle gets the same particles appended before each
     substep.  Emission must not force a rebuild every substep."""
     res, dt, steps = 128, 1e-4, 200
     vol = (1 / res) ** 3 / 8
     gm, om = mats_pair(M, M.FLUID, E=1e4, gamma=7.0, rho=1000.0)
-    cfg = orc.config(res, 1 / res, orc.SLIP)
+    flip = dict(flip_alpha=0.95, flip_beta_min=0.0, flip_beta_max=1.0) if asflip else {}
+    cfg = orc.config(res, 1 / res, orc.SLIP, transfer=orc.ASFLIP if asflip else orc.APIC, **flip)
     s = None
-    with M.Simulator(res, 1 / res, [gm], boundary=M.SLIP) as sim:
+    with M.Simulator(res, 1 / res, [gm], boundary=M.SLIP, transfer=M.ASFLIP if asflip else M.APIC, **flip) as sim:
         for k in range(steps):
             xe, ve = scenes.fountain_batch(2, k, dt, vol)
             sim.emit_particles(xe, v=ve)
