@@ -81,6 +81,10 @@ def lib():
         L.orc_svd3.argtypes = [P, P, P, P]
         L.orc_lame.argtypes = [ctypes.c_double, ctypes.c_double, P, P]
         L.orc_kirchhoff.argtypes = [P, P, ctypes.c_double, P]
+        L.orc_wave_speed.argtypes = [P]
+        L.orc_wave_speed.restype = ctypes.c_double
+        L.orc_cfl_dt.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_cfl_dt.restype = ctypes.c_double
         L.orc_plasticity.argtypes = [P, P, P]
         L.orc_grid_bounds.argtypes = [i64, P, ctypes.c_double, P, P]
         L.orc_p2g.argtypes = [P, P, i64, P, P, P, P, P, P, P, ctypes.c_double, P]
@@ -174,6 +178,15 @@ def lame(E, nu):
     mu, la = ctypes.c_double(), ctypes.c_double()
     lib().orc_lame(E, nu, ctypes.byref(mu), ctypes.byref(la))
     return mu.value, la.value
+
+
+def wave_speed(mat: Material) -> float:
+    return lib().orc_wave_speed(ctypes.byref(mat))
+
+
+def cfl_dt(cfg: Config, mats, v_bound: float, cfl: float, dt_max: float) -> float:
+    ma = _mats(mats)
+    return lib().orc_cfl_dt(ctypes.byref(cfg), ma, len(ma), float(v_bound), float(cfl), float(dt_max))
 
 
 def kirchhoff(mat: Material, F, Jp=1.0) -> np.ndarray:

@@ -235,3 +235,33 @@ void orc_plasticity(const orc_material* mat, double F[9], double* Jp)
         udwt(U, s, V, F);
     }
 }
+
+/* Adaptive step size (the paper's scenes take their step sizes from Fang et
+ * al. 2018, Sec. 6.5): dt = min(dt_max, cfl dx / (v + c)), v a bound on the
+ * particle speed and c the largest dilatational (p-wave) speed of the
+ * materials, c^2 = (lambda + 2 mu) / rho, or K gamma / rho for the fluid
+ * p = K (J^-gamma - 1), whose bulk modulus -J dp/dJ at J = 1 is K gamma. */
+double orc_wave_speed(const orc_material* mat)
+{
+    double mu, la;
+    if (mat->kind == ORC_FLUID)
+        return sqrt(mat->E * mat->gamma / mat->rho);
+    if (mat->kind == ORC_NACC)
+        nacc_lame(mat->E, mat->nu, &mu, &la);
+    else
+        orc_lame(mat->E, mat->nu, &mu, &la);
+    return sqrt((la + 2.0 * mu) / mat->rho);
+}
+
+double orc_cfl_dt(const orc_config* cfg, const orc_material* mats, int n_mats, double v_bound, double cfl,
+                  double dt_max)
+{
+    double c = 0.0;
+    for (int i = 0; i < n_mats; ++i) {
+        double ci = orc_wave_speed(&mats[i]);
+        if (ci > c)
+            c = ci;
+    }
+    double dt = cfl * cfg->dx / (v_bound + c);
+    return dt < dt_max ? dt : dt_max;
+}

@@ -90,6 +90,14 @@ void orc_svd3(const double F[9], double U[9], double sig[3], double V[9]);
 /* Lame parameters from (E, nu). */
 void orc_lame(double E, double nu, double* mu, double* la);
 
+/* Dilatational (p-wave) speed of a material at rest. */
+double orc_wave_speed(const orc_material* mat);
+
+/* Adaptive step size: min(dt_max, cfl dx / (v_bound + max wave speed of
+ * mats[0..n_mats-1])). */
+double orc_cfl_dt(const orc_config* cfg, const orc_material* mats, int n_mats, double v_bound, double cfl,
+                  double dt_max);
+
 /* Kirchhoff stress tau = P F^T of one particle.  Jp is the snow (and NACC)
  * plastic volume ratio, or the fluid J; ignored for elastic and sand.
  * ORC_NACC: E is the bulk modulus kappa, hardening is xi. */

@@ -536,6 +536,53 @@ def test_asflip_keeps_the_momentum_and_centre_of_mass_of_apic(orc):
     np.testing.assert_array_equal(a.F, b.F)
 
 
+# ------------------------------------------------------------- adaptive dt
+
+@pytest.mark.parametrize("kind", ["elastic", "snow", "sand"])
+def test_wave_speed_is_the_p_wave_speed(orc, kind):
+    """c^2 = E (1 - nu) / (rho (1 + nu)(1 - 2 nu)), the textbook P-wave
+    modulus from E and nu (not the Lame form the oracle uses)."""
+    E, nu, rho = 3.5e5, 0.3, 2200.0
+    mat = orc.material(getattr(orc, kind.upper()), E=E, nu=nu, rho=rho)
+    assert abs(orc.wave_speed(mat) ** 2 - E * (1 - nu) / (rho * (1 + nu) * (1 - 2 * nu))) <= 1e-12 * E / rho
+
+
+def test_wave_speed_nacc_from_bulk_modulus(orc):
+    """NACC takes kappa: the P-wave modulus is 3 kappa (1 - nu) / (1 + nu)."""
+    k, nu, rho = 5e4, 0.3, 400.0
+    c = orc.wave_speed(orc.material(orc.NACC, E=k, nu=nu, rho=rho))
+    assert abs(c * c - 3 * k * (1 - nu) / ((1 + nu) * rho)) <= 1e-12 * k / rho
+
+
+def test_wave_speed_fluid_from_the_stress(orc):
+    """Fluid: c^2 = (bulk modulus) / rho with the bulk modulus -J dp/dJ at
+    J = 1 differentiated numerically from the oracle's own stress
+    (tau = -p J I)."""
+    K, gamma, rho = 1e4, 7.0, 1000.0
+    mat = orc.material(orc.FLUID, E=K, gamma=gamma, rho=rho)
+    h = 1e-5
+
+    def p(J):
+        return -orc.kirchhoff(mat, np.eye(3), J)[0, 0] / J
+
+    kb = -(p(1 + h) - p(1 - h)) / (2 * h)
+    assert abs(orc.wave_speed(mat) ** 2 - kb / rho) <= 1e-7 * kb / rho
+
+
+def test_cfl_dt_cases(orc):
+    """The step takes the fastest material and the speed bound, and dt_max
+    caps it: a particle moving at the wave speed halves the rest step."""
+    cfg = orc.config(64, 1 / 64)
+    soft = orc.material(orc.ELASTIC, E=1e3, nu=0.2, rho=1000.0)
+    stiff = orc.material(orc.ELASTIC, E=1e5, nu=0.2, rho=1000.0)
+    c = orc.wave_speed(stiff)
+    rest = orc.cfl_dt(cfg, [soft, stiff], 0.0, 0.5, 1.0)
+    assert abs(rest - 0.5 / 64 / c) <= 1e-15
+    assert orc.cfl_dt(cfg, [stiff, soft], 0.0, 0.5, 1.0) == rest
+    assert abs(orc.cfl_dt(cfg, [soft, stiff], c, 0.5, 1.0) - rest / 2) <= 1e-15
+    assert orc.cfl_dt(cfg, [soft, stiff], 0.0, 0.5, 1e-6) == 1e-6
+
+
 # -------------------------------------------------------- keys, sort, pblocks
 
 def _morton(c, bits):
