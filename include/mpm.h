@@ -176,6 +176,23 @@ mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const flo
  * a rebuild costs one host wait for the new block count. */
 mpm_status mpm_substep(mpm_ctx* ctx, float dt);
 
+/* Advance by `duration` seconds of simulated time in adaptive substeps (the
+ * paper's scenes take their step sizes from Fang et al. 2018, Sec. 6.5):
+ * each substep uses dt = min(dt_max, cfl dx / (v + c)), c the largest
+ * dilatational wave speed of the context's materials (sqrt((lambda + 2 mu) /
+ * rho); sqrt(K gamma / rho) for the fluid) and v a bound on the particle
+ * speed; the last steps of the interval are made equal so that they end on
+ * it exactly.  v is the largest |v| that the G2P of substep s - 2 reduced
+ * (no stall: the host already waits for that substep), grown by |g| dt per
+ * substep of age; after particles were added or velocities written, one
+ * reduction with a stream sync supplies it instead.  cfl in (0, 1],
+ * dt_max > 0.  dts: NULL, or room for max_substeps floats that receive each
+ * substep's dt; n_substeps (may be NULL) receives the count.  MPM_ECAPACITY
+ * if the interval needs more than max_substeps substeps (those ran).  The
+ * first call turns on the speed reduction in G2P for the context. */
+mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, int64_t max_substeps,
+                       float* dts, int64_t* n_substeps);
+
 /* Copy the particle state out in insertion order; any pointer may be NULL
  * to skip that field.  Syncs; returns the sticky device error, if any. */
 mpm_status mpm_read_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, float* Jp,

@@ -73,6 +73,7 @@ _PROTOS = {
     "mpm_add_particles": (I, [P, I64, P, P, P, I, I]),
     "mpm_emit_particles": (I, [P, I64, P, P, P, I, I]),
     "mpm_substep": (I, [P, F]),
+    "mpm_advance": (I, [P, ctypes.c_double, F, F, I64, P, P]),
     "mpm_read_state": (I, [P, P, P, P, P, P, I]),
     "mpm_write_state": (I, [P, P, P, P, P, P, I]),
     "mpm_sync": (I, [P]),

@@ -15,6 +15,7 @@
 // (faster than one cell per substep) is reported as MPM_EDOMAIN, never
 // written out of bounds.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -37,6 +38,17 @@ void launch_debug_wait_timeout(int max_iter, uint32_t* err, cudaStream_t s);
 namespace {
 
 constexpr int kRing = 4;
+
+// Status words (dstat on the device, hstat its pinned mirror, same indices):
+//   [0]                    sticky error bits
+//   [kFlag0 + 2 slot]      flag word of ring slot `slot`; the word after it
+//                          holds the substep's max |v|^2 when speeds are tracked
+//   [kCountWord]           block count of the last rebuild
+//   [kErrCopyWord]         host copy of the error bits
+constexpr int kFlag0 = 2;
+constexpr int kCountWord = kFlag0 + 2 * kRing;
+constexpr int kErrCopyWord = kCountWord + 1;
+inline int flag_word(int slot) { return kFlag0 + 2 * slot; }
 
 struct ProfRec {
     int phase;
@@ -88,8 +100,7 @@ struct mpm_ctx {
     void* stage = nullptr;
     size_t stage_bytes = 0;
 
-    // status: dstat[0] sticky error bits, dstat[1 + slot] per-substep flags,
-    // dstat[1 + kRing] block count of the last rebuild
+    // status words (layout above kFlag0)
     uint32_t* dstat = nullptr;
     uint32_t* hstat = nullptr;  // pinned mirror
     cudaEvent_t ev[kRing] = {};
@@ -112,6 +123,15 @@ struct mpm_ctx {
     float graph_dt = 0.0f;
     int64_t graph_launches = 0;
     int64_t graph_drop_step = -1;   // substep of the last drop: that substep launches directly
+
+    // adaptive dt (mpm_advance): speeds known from the ring (substeps >=
+    // speed_ring_from write their max |v|^2) or from a reduction taken at the
+    // start of substep known_step; both reset when particles change
+    float c_max = 0.0f;             // largest dilatational wave speed of the materials
+    int64_t speed_ring_from = -1;
+    int64_t known_step = -1;
+    float known_v2 = 0.0f;
+    float last_dt = 0.0f;
 
     // host mirror of the block table (refreshed at every rebuild), used to
     // decide on the host whether emitted particles land in mapped blocks
@@ -247,9 +267,9 @@ void prof_end(mpm_ctx* ctx, int phase, cudaEvent_t a)
 mpm_status device_error(mpm_ctx* ctx)
 {
     uint32_t e = 0;
-    CK(cudaMemcpyAsync(&ctx->hstat[kRing], ctx->dstat, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->hstat[kErrCopyWord], ctx->dstat, 4, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    e = ctx->hstat[kRing];
+    e = ctx->hstat[kErrCopyWord];
     if (e & ST_ENONFINITE)
         return fail(ctx, MPM_ENONFINITE, "a particle position became non-finite");
     if (e & ST_EDOMAIN)
@@ -335,12 +355,20 @@ GridView grid_view(mpm_ctx* ctx)
     return g;
 }
 
+// Particle velocities changed outside G2P: the speeds the ring holds no
+// longer bound them.
+void forget_speeds(mpm_ctx* ctx)
+{
+    ctx->speed_ring_from = -1;
+    ctx->known_step = -1;
+}
+
 // One separate substep on the context's stream: clear the flag slot, P2G,
 // grid update, G2P, copy the flags to the pinned ring.
 void enqueue_separate(mpm_ctx* ctx, float dt, int slot)
 {
     cudaStream_t s = ctx->stream;
-    cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s);
+    cudaMemsetAsync(&ctx->dstat[flag_word(slot)], 0, 8, s);
     GridView gv = grid_view(ctx);
     const PartView& pv = ctx->pv[ctx->cur];
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -351,9 +379,9 @@ void enqueue_separate(mpm_ctx* ctx, float dt, int slot)
     launch_grid_update(ctx->sp, gv, dt, s);
     prof_end(ctx, 2, e1);
     prof_begin(ctx, e2);
-    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.g2p_variant, s);
+    launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[flag_word(slot)], ctx->dstat, ctx->cfg.g2p_variant, s);
     prof_end(ctx, 3, e2);
-    cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&ctx->hstat[flag_word(slot)], &ctx->dstat[flag_word(slot)], 8, cudaMemcpyDeviceToHost, s);
 }
 
 void drop_graphs(mpm_ctx* ctx)
@@ -389,21 +417,21 @@ mpm_status rebuild(mpm_ctx* ctx)
     launch_mark_pblocks(sort ? ctx->skeys : ctx->keys, n, sp.L, ctx->flags, s);
     CK(exclusive_scan(ctx->flags, ctx->ranks, ctx->n_slots, ctx->scan_scr, s, &ctx->launches));
     launch_build_table(ctx->flags, ctx->ranks, ctx->n_slots, ctx->table, ctx->pslot,
-                       (int32_t*)&ctx->dstat[1 + kRing], s);
+                       (int32_t*)&ctx->dstat[kCountWord], s);
     ctx->launches += 2;
     if (n > 0 && sort) {
         launch_permute(ctx->pv[ctx->cur], ctx->pv[1 - ctx->cur], ctx->svals, n, s);
         ctx->launches += 1;
         ctx->cur = 1 - ctx->cur;
     }
-    CK(cudaMemcpyAsync(&ctx->hstat[kRing + 1], &ctx->dstat[1 + kRing], 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&ctx->hstat[kCountWord], &ctx->dstat[kCountWord], 4, cudaMemcpyDeviceToHost, s));
     if (ctx->htable) {
         CK(cudaMemcpyAsync(ctx->htable, ctx->table, (size_t)ctx->n_slots * 4, cudaMemcpyDeviceToHost, s));
         ctx->htable_valid = true;
     }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
-    int32_t npb = (int32_t)ctx->hstat[kRing + 1];
+    int32_t npb = (int32_t)ctx->hstat[kCountWord];
     ctx->n_pblocks = npb;
     launch_interior(sp, ctx->table, ctx->pslot, npb, ctx->interior, s);
     ctx->launches += 1;
@@ -523,8 +551,16 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         ++L;
     sp.L = L;
     sp.n_mats = n_mats;
-    for (int i = 0; i < n_mats; ++i)
+    for (int i = 0; i < n_mats; ++i) {
         sp.mat[i] = make_mat_params(mats[i]);
+        const MatParams& m = sp.mat[i];
+        // dilatational (p-wave) speed: sqrt((lambda + 2 mu) / rho); for the
+        // fluid the bulk modulus of p = K (J^-gamma - 1) at J = 1 is K gamma
+        const double mod = m.kind == MPM_FLUID ? (double)m.K * m.gamma : (double)m.la + 2.0 * m.mu;
+        const double c = sqrt(mod > 0.0 ? mod / m.rho : 0.0);
+        if (c > ctx->c_max)
+            ctx->c_max = (float)c;
+    }
     ctx->n_slots = (int64_t)1 << (3 * L);
 
     mpm_status st = MPM_OK;
@@ -647,6 +683,7 @@ mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const floa
         return fail(ctx, MPM_EINVAL, "mpm_add_particles: bad argument");
     if (n == 0)
         return MPM_OK;
+    forget_speeds(ctx);
     mpm_status st = ensure_particle_capacity(ctx, ctx->n + n);
     if (st != MPM_OK)
         return st;
@@ -715,16 +752,16 @@ static void enqueue_fused(mpm_ctx* ctx, float dt, int slot)
 {
     cudaStream_t s = ctx->stream;
     const PartView& pv = ctx->pv[ctx->cur];
-    cudaMemsetAsync(&ctx->dstat[1 + slot], 0, 4, s);
+    cudaMemsetAsync(&ctx->dstat[flag_word(slot)], 0, 8, s);
     GridView gv = grid_view(ctx);
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(ctx, e1);
     launch_grid_update(ctx->sp, gv, dt, s);
     prof_end(ctx, 2, e1);
     prof_begin(ctx, e2);
-    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[1 + slot], ctx->dstat, ctx->cfg.p2g_variant, s);
+    launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[flag_word(slot)], ctx->dstat, ctx->cfg.p2g_variant, s);
     prof_end(ctx, 3, e2);
-    cudaMemcpyAsync(&ctx->hstat[slot], &ctx->dstat[1 + slot], 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&ctx->hstat[flag_word(slot)], &ctx->dstat[flag_word(slot)], 8, cudaMemcpyDeviceToHost, s);
 }
 
 // Replays the steady-state substep of the current mode from its CUDA graph,
@@ -797,6 +834,7 @@ mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const flo
         return fail(ctx, MPM_EINVAL, "mpm_emit_particles: bad argument");
     if (n == 0)
         return MPM_OK;
+    forget_speeds(ctx);
     if (ctx->n + n > ctx->cap / 2 || !ctx->pbuf[0]) {
         // growth (4x when half full) needs the stream idle; rare by design
         CK(cudaStreamSynchronize(ctx->stream));
@@ -869,7 +907,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     if (!ctx->need_rebuild && ctx->step >= 2 && ctx->step - 2 >= ctx->last_rebuild) {
         int slot = (int)((ctx->step - 2) % kRing);
         CK(cudaEventSynchronize(ctx->ev[slot]));
-        if (ctx->hstat[slot] & (ST_REBUILD_SOFT | ST_REBUILD_HARD))
+        if (ctx->hstat[flag_word(slot)] & (ST_REBUILD_SOFT | ST_REBUILD_HARD))
             ctx->need_rebuild = true;
     }
     if (ctx->need_rebuild) {
@@ -904,6 +942,85 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     ctx->gcur = 1 - ctx->gcur;
     ctx->step += 1;
     ctx->tau_valid = true;
+    return MPM_OK;
+}
+
+mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, int64_t max_substeps, float* dts,
+                       int64_t* n_substeps)
+{
+    if (!ctx)
+        return MPM_EINVAL;
+    if (n_substeps)
+        *n_substeps = 0;
+    if (!(duration > 0.0) || !(cfl > 0.f && cfl <= 1.f) || !(dt_max > 0.f) || max_substeps < 1)
+        return fail(ctx, MPM_EINVAL, "mpm_advance: bad argument");
+    if (!ctx->sp.track_speed) {
+        ctx->sp.track_speed = 1;   // G2P now also reduces the largest speed
+        drop_graphs(ctx);
+        forget_speeds(ctx);
+    }
+    const double g = sqrt((double)ctx->sp.g[0] * ctx->sp.g[0] + (double)ctx->sp.g[1] * ctx->sp.g[1] +
+                          (double)ctx->sp.g[2] * ctx->sp.g[2]);
+    double t = 0.0;
+    int64_t k = 0;
+    while (duration - t > 1e-9 * duration) {
+        if (k >= max_substeps)
+            return fail(ctx, MPM_ECAPACITY, "mpm_advance: max_substeps reached before the end of the interval");
+        const int64_t s = ctx->step;
+        // the freshest speed bound available without stalling the stream:
+        // the ring word of substep s - 2 (one substep old at the start of s),
+        // else a reduction taken earlier, else a reduction now (one sync)
+        float v2 = 0.0f;
+        int64_t age = 0;
+        if (ctx->n > 0) {
+            if (ctx->speed_ring_from >= 0 && s - 2 >= ctx->speed_ring_from) {
+                const int slot = (int)((s - 2) % kRing);
+                CK(cudaEventSynchronize(ctx->ev[slot]));
+                uint32_t bits = ctx->hstat[flag_word(slot) + 1];
+                memcpy(&v2, &bits, 4);
+                age = 1;
+            } else if (ctx->known_step >= 0) {
+                v2 = ctx->known_v2;
+                age = s - ctx->known_step;
+            } else {
+                CK(cudaMemsetAsync(&ctx->dstat[kErrCopyWord + 1], 0, 4, ctx->stream));
+                launch_max_speed2(ctx->pv[ctx->cur], ctx->n, &ctx->dstat[kErrCopyWord + 1], ctx->stream);
+                ctx->launches += 1;
+                CK(cudaMemcpyAsync(&ctx->hstat[kErrCopyWord + 1], &ctx->dstat[kErrCopyWord + 1], 4,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                uint32_t bits = ctx->hstat[kErrCopyWord + 1];
+                memcpy(&v2, &bits, 4);
+                ctx->known_v2 = v2;
+                ctx->known_step = s;
+            }
+        }
+        const double prev = ctx->last_dt > 0.f ? ctx->last_dt : dt_max;
+        const double v_est = sqrt((double)v2) + (double)age * g * prev;
+        double dt = (double)cfl * ctx->sp.dx / (v_est + ctx->c_max);
+        if (dt > dt_max)
+            dt = dt_max;
+        const double rem = duration - t;
+        if (dt >= rem) {
+            dt = rem;
+        } else {
+            const double parts = ceil(rem / dt);   // equal steps to the end: no sliver
+            dt = rem / parts;
+        }
+        const float dtf = (float)dt;
+        mpm_status st = mpm_substep(ctx, dtf);
+        if (st != MPM_OK)
+            return st;
+        if (ctx->speed_ring_from < 0 && ctx->n > 0)
+            ctx->speed_ring_from = s;
+        if (dts)
+            dts[k] = dtf;
+        ctx->last_dt = dtf;
+        t += dt;
+        ++k;
+        if (n_substeps)
+            *n_substeps = k;
+    }
     return MPM_OK;
 }
 
@@ -955,6 +1072,8 @@ mpm_status mpm_write_state(mpm_ctx* ctx, const float* x, const float* v, const f
 {
     if (!ctx)
         return MPM_EINVAL;
+    if (v)
+        forget_speeds(ctx);
     const float* ins[5] = {x, v, C, F, Jp};
     static const int W[5] = {3, 3, 9, 9, 1};
     int64_t n = ctx->n;

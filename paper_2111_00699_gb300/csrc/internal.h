@@ -78,6 +78,7 @@ struct SimParams {
     int L;                   // Morton bits per axis of the block table
     int transfer;            // MPM_APIC or MPM_ASFLIP
     float flip_alpha, flip_beta_min, flip_beta_max;
+    int track_speed;         // 1: G2P also max-reduces |v|^2 into flags[1] (adaptive dt)
     int n_mats;
     MatParams mat[kMaxMaterials];
 };
@@ -127,6 +128,8 @@ void launch_gather_out(const PartView& pv, int64_t n, int field, float* out, cud
 void launch_scatter_in(const PartView& pv, int64_t n, int field, const float* in, cudaStream_t s);
 void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t* pslot, int32_t n_pblocks,
                           float* dense, cudaStream_t s);
+// *word (zeroed by the caller) <- max over particles of |v|^2, as float bits
+void launch_max_speed2(const PartView& pv, int64_t n, uint32_t* word, cudaStream_t s);
 
 // substep.cu
 void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,

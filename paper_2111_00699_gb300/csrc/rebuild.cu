@@ -373,6 +373,32 @@ void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t
 
 }  // namespace mpm
 
+// ---- largest particle speed (adaptive dt) -----------------------------------
+
+namespace mpm {
+namespace {
+__global__ void k_max_speed2(PartView pv, int64_t n, uint32_t* __restrict__ word)
+{
+    float best = 0.0f;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const float a = pv.ch(CH_V)[p], b = pv.ch(CH_V + 1)[p], c = pv.ch(CH_V + 2)[p];
+        best = fmaxf(best, a * a + b * b + c * c);
+    }
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(best));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(word, m);
+}
+}  // namespace
+
+void launch_max_speed2(const PartView& pv, int64_t n, uint32_t* word, cudaStream_t s)
+{
+    if (n > 0) {
+        int64_t blocks = (n + kBlock - 1) / kBlock;
+        k_max_speed2<<<(unsigned)(blocks < 1216 ? blocks : 1216), kBlock, 0, s>>>(pv, n, word);
+    }
+}
+}  // namespace mpm
+
 // ---- bounded-wait check -----------------------------------------------------
 // One warp waits on an mbarrier that expects 1024 bytes no copy ever delivers,
 // with the same bounded poll the staged transfer kernels use; when the poll

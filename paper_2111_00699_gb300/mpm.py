@@ -160,6 +160,16 @@ class Simulator:
             if st:
                 _check(st, self._ctx)
 
+    def advance(self, duration: float, cfl: float = 0.5, dt_max: float = 1e-3, max_substeps: int = 1 << 20):
+        """Advance by `duration` seconds in adaptive substeps (mpm_advance);
+        returns the dt of each substep as a numpy array."""
+        dts = np.zeros(int(max_substeps), dtype=np.float32)
+        k = ctypes.c_int64(0)
+        st = load().mpm_advance(self._ctx, float(duration), float(cfl), float(dt_max), int(max_substeps),
+                                dts.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k))
+        _check(st, self._ctx)
+        return dts[:k.value].copy()
+
     def sync(self):
         _check(load().mpm_sync(self._ctx), self._ctx)
 

@@ -149,3 +149,9 @@ def test_wait_timeout_check_rejects_bad_limit_without_the_gpu(lib):
     from paper_2111_00699_gb300 import _lib
     assert lib.mpm_debug_wait_timeout(0) == _lib.MPM_EINVAL
     assert lib.mpm_debug_wait_timeout(1 << 20) == _lib.MPM_EINVAL
+
+
+def test_advance_rejects_a_null_context_without_the_gpu(lib):
+    from paper_2111_00699_gb300 import _lib
+    n = ctypes.c_int64(7)
+    assert lib.mpm_advance(None, 0.01, 0.5, 1e-3, 100, None, ctypes.byref(n)) == _lib.MPM_EINVAL

@@ -363,6 +363,73 @@ def test_asflip_substeps_match_oracle(M, kind):
             sim.set_g2p2g(True)
 
 
+def _expected_dt(om_list, cfg, starts, dts, reset, q, rem, cfl, dt_max, g=9.8):
+    """The step rule of mpm_advance for global substep q, evaluated on the
+    oracle's states (starts[k] = state at the start of substep k, dts[k] its
+    step).  Speeds were last forgotten (context creation, an addition) before
+    substep `reset`, where one reduction measured them.  The bound is the
+    largest |v| at the start of substep q - 1 (what the G2P of q - 2
+    reduced), grown by g dt_{q-1}, once q - 2 >= reset; before that it is the
+    reduction's value grown by g dt_{q-1} per substep of age.  The remaining
+    interval is then cut into equal steps."""
+    if q - 2 >= reset:
+        vb = np.linalg.norm(starts[q - 1].v, axis=1).max() + g * dts[q - 1]
+    else:
+        vb = np.linalg.norm(starts[reset].v, axis=1).max() + (q - reset) * g * (dts[q - 1] if q > reset else 0.0)
+    dt = orc.cfl_dt(cfg, om_list, vb, cfl, dt_max)
+    return rem if dt >= rem else rem / np.ceil(rem / dt)
+
+
+@pytest.mark.parametrize("kind", ["elastic", "fluid"])
+def test_adaptive_dt_matches_oracle(M, kind):
+    """mpm_advance: the substep sizes follow the rule (within FP32 rounding of
+    the speeds), each interval is covered exactly, and the state matches the
+    oracle run with the same steps -- over three calls: a fresh context, a
+    call that carries the speed bound over, and one after an addition (which
+    forces a fresh reduction)."""
+    kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0))[kind]
+    k = kw.pop("kind")
+    gm, om = mats_pair(M, k, **kw)
+    x, _ = scenes.blocks(15, 15000, 64, 2)
+    rng = np.random.default_rng(5)
+    v = (0.5 * rng.normal(size=(len(x), 3))).astype(np.float32)
+    vol = (1 / 64) ** 3 / 8
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    cfl, dt_max = 0.5, 5e-3
+    starts, steps, reset = [], [], 0
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP) as sim:
+        sim.add_particles(x, v=v)
+        s = oracle_state_from(sim.read_state(), vol)
+        for call, duration in enumerate((0.01, 0.0075, 0.0125)):
+            if call == 2:
+                x2 = scenes.cube_uniform(6, 400, 0.45, 0.55)
+                v2 = np.tile(np.array([0.0, 2.0, 0.0], np.float32), (400, 1))
+                sim.add_particles(x2, v=v2)
+                s = orc.State(np.concatenate([s.x, x2]), np.concatenate([s.v, v2]),
+                              np.concatenate([s.C, np.zeros((400, 3, 3))]),
+                              np.concatenate([s.F, np.tile(np.eye(3), (400, 1, 1))]),
+                              np.concatenate([s.Jp, np.ones(400)]), np.concatenate([s.vol, np.full(400, vol)]),
+                              np.concatenate([s.mat, np.zeros(400, s.mat.dtype)]))
+                reset = len(steps)
+            dts = sim.advance(duration, cfl=cfl, dt_max=dt_max)
+            assert len(dts) >= 4
+            assert abs(float(np.sum(dts.astype(np.float64))) - duration) <= 1e-6 * duration
+            t = 0.0
+            for dt in dts:
+                q = len(steps)
+                starts.append(s.copy())
+                want = _expected_dt([om], cfg, starts, steps, reset, q, duration - t, cfl, dt_max)
+                assert abs(float(dt) - want) <= 1e-4 * want, (call, q, float(dt), want)
+                steps.append(float(dt))
+                t += float(dt)
+                assert orc.substep(cfg, om, s, float(dt)) == 0
+            assert dts.max() < dt_max      # the speed bound, not the cap, set the steps
+            g = {key: val.double().cpu().numpy() for key, val in sim.read_state().items()}
+            assert linf(g["x"], s.x) <= 1e-4
+            assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+
+
 def test_ten_substeps_snow_full_size_bench_configuration(M):
     """The 1.34M-particle snow scene in the launch configuration bench.py
     times (register-run P2G, 64-register G2P, CUDA-graph replay on a side
