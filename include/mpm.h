@@ -182,14 +182,15 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt);
  * dilatational wave speed of the context's materials (sqrt((lambda + 2 mu) /
  * rho); sqrt(K gamma / rho) for the fluid) and v a bound on the particle
  * speed; the last steps of the interval are made equal so that they end on
- * it exactly.  v is the largest |v| that the G2P of substep s - 2 reduced
- * (no stall: the host already waits for that substep), grown by |g| dt per
- * substep of age; after particles were added or velocities written, one
- * reduction with a stream sync supplies it instead.  cfl in (0, 1],
+ * it exactly.  v is the largest |v| after substep s - 2, reduced on the
+ * device at the end of that substep (no stall: the host already waits for
+ * it), grown by |g| dt per substep of age; after particles were added or
+ * velocities written, one reduction with a stream sync supplies it instead.  cfl in (0, 1],
  * dt_max > 0.  dts: NULL, or room for max_substeps floats that receive each
  * substep's dt; n_substeps (may be NULL) receives the count.  MPM_ECAPACITY
  * if the interval needs more than max_substeps substeps (those ran).  The
- * first call turns on the speed reduction in G2P for the context. */
+ * first call turns on the per-substep speed reduction for the context (one
+ * small kernel reading v after G2P). */
 mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, int64_t max_substeps,
                        float* dts, int64_t* n_substeps);
 

@@ -127,6 +127,7 @@ struct mpm_ctx {
     // adaptive dt (mpm_advance): speeds known from the ring (substeps >=
     // speed_ring_from write their max |v|^2) or from a reduction taken at the
     // start of substep known_step; both reset when particles change
+    bool track_speed = false;       // each substep also reduces max |v|^2 into its ring slot
     float c_max = 0.0f;             // largest dilatational wave speed of the materials
     int64_t speed_ring_from = -1;
     int64_t known_step = -1;
@@ -381,6 +382,8 @@ void enqueue_separate(mpm_ctx* ctx, float dt, int slot)
     prof_begin(ctx, e2);
     launch_g2p(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[flag_word(slot)], ctx->dstat, ctx->cfg.g2p_variant, s);
     prof_end(ctx, 3, e2);
+    if (ctx->track_speed)
+        launch_max_speed2(pv, ctx->n, &ctx->dstat[flag_word(slot) + 1], s);
     cudaMemcpyAsync(&ctx->hstat[flag_word(slot)], &ctx->dstat[flag_word(slot)], 8, cudaMemcpyDeviceToHost, s);
 }
 
@@ -761,6 +764,8 @@ static void enqueue_fused(mpm_ctx* ctx, float dt, int slot)
     prof_begin(ctx, e2);
     launch_g2p2g(ctx->sp, pv, gv, ctx->n, dt, &ctx->dstat[flag_word(slot)], ctx->dstat, ctx->cfg.p2g_variant, s);
     prof_end(ctx, 3, e2);
+    if (ctx->track_speed)
+        launch_max_speed2(pv, ctx->n, &ctx->dstat[flag_word(slot) + 1], s);
     cudaMemcpyAsync(&ctx->hstat[flag_word(slot)], &ctx->dstat[flag_word(slot)], 8, cudaMemcpyDeviceToHost, s);
 }
 
@@ -816,7 +821,7 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
     } else {
         enqueue_fused(ctx, dt, slot);
     }
-    ctx->launches += 2;
+    ctx->launches += ctx->track_speed ? 3 : 2;
     CK(cudaEventRecord(ctx->ev[slot], s));
     CK(cudaGetLastError());
     ctx->gcur = 1 - ctx->gcur;   // grid[gcur] now holds the momentum of the new state
@@ -936,7 +941,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     } else {
         enqueue_separate(ctx, dt, slot);
     }
-    ctx->launches += 3;
+    ctx->launches += ctx->track_speed ? 4 : 3;
     CK(cudaEventRecord(ctx->ev[slot], s));
     CK(cudaGetLastError());
     ctx->gcur = 1 - ctx->gcur;
@@ -954,8 +959,8 @@ mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, i
         *n_substeps = 0;
     if (!(duration > 0.0) || !(cfl > 0.f && cfl <= 1.f) || !(dt_max > 0.f) || max_substeps < 1)
         return fail(ctx, MPM_EINVAL, "mpm_advance: bad argument");
-    if (!ctx->sp.track_speed) {
-        ctx->sp.track_speed = 1;   // G2P now also reduces the largest speed
+    if (!ctx->track_speed) {
+        ctx->track_speed = true;   // each substep now also reduces the largest speed
         drop_graphs(ctx);
         forget_speeds(ctx);
     }

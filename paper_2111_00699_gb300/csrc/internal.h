@@ -78,7 +78,6 @@ struct SimParams {
     int L;                   // Morton bits per axis of the block table
     int transfer;            // MPM_APIC or MPM_ASFLIP
     float flip_alpha, flip_beta_min, flip_beta_max;
-    int track_speed;         // 1: G2P also max-reduces |v|^2 into flags[1] (adaptive dt)
     int n_mats;
     MatParams mat[kMaxMaterials];
 };

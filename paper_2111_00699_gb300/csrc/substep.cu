@@ -671,16 +671,6 @@ __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartV
 {
     // va: the velocity that moves the particle, if not vp (ASFLIP)
     const float* adv = va ? va : vp;
-    if (sp.track_speed) {
-        // adaptive dt: flags[1] <- max |v|^2 over the substep's particles
-        // (non-negative floats order as their bit patterns)
-        float s2 = fmaxf(vp[0] * vp[0] + vp[1] * vp[1] + vp[2] * vp[2],
-                         adv[0] * adv[0] + adv[1] * adv[1] + adv[2] * adv[2]);
-        const unsigned act = __activemask();
-        const unsigned m = __reduce_max_sync(act, __float_as_uint(s2));
-        if ((threadIdx.x & 31) == __ffs(act) - 1)
-            atomicMax(flags + 1, m);
-    }
     // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) sum w v (node - f)^T
     float C[9];
     float c4 = 4.0f * sp.inv_dx;
