@@ -494,7 +494,7 @@ def _variant_name(kind, v):
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
                         "chunk4": "k_p2g_chunk<4, false>", "chunk8": "k_p2g_chunk<8, false>", "stage4": "k_p2g_stage<4>",
-                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>"},
+                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>", "slab4": "k_p2g_slab<4>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         "occ": "k_g2p_occ<8>", "stage": "k_g2p_stage",
                         "occ10": "k_g2p_occ<10>"}}
@@ -540,7 +540,7 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8, 7 sacc4); -1 = autotune")
+                         "6 stage8, 7 sacc4, 8 slab4); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10); -1 = autotune")
     ap.add_argument("--profile-substeps", type=int, default=0,

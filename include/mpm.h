@@ -101,7 +101,8 @@ typedef struct {
                               accumulation over runs of 4/8 particles, 5/6 the same with
                               each CTA's 512/1024 particles staged in shared memory by
                               bulk asynchronous copies, 7 as 3 with the accumulators in
-                              thread-private shared memory (see the autotuner) */
+                              thread-private shared memory, 8 as 3 split over three threads
+                              per particle run, one per z-slab of 9 nodes (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64

@@ -24,7 +24,7 @@ STICKY, SLIP = 0, 1
 APIC, ASFLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
-P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4")
+P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4", "slab4")
 G2P_VARIANTS = ("direct", "chunk4", "chunk8", "tile", "occ", "stage", "occ10")
 
 

@@ -31,7 +31,8 @@ enum P2GVariant : int {
     P2G_STAGE4 = 5,   // CHUNK4 reading a CTA's 512 particles from shared memory, staged by bulk async copies
     P2G_STAGE8 = 6,   // same with 8 particles per thread (1024 per CTA)
     P2G_SACC4 = 7,    // CHUNK4 with the 27 node accumulators in (thread-private) shared memory
-    kP2GVariants = 8
+    P2G_SLAB4 = 8,    // CHUNK4 split over three threads, one per z-slab of 9 nodes
+    kP2GVariants = 9
 };
 
 // Particle capacity is a multiple of this, so that a staged tile of

@@ -447,7 +447,87 @@ __global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 3) k_p2g_chunk(S
         acc_flush(gv, gv.cur, acc, cb, err);
 }
 
-// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the
+// P2G_SLAB4: the register runs of k_p2g_chunk<4> split over three threads,
+// one per z-slab of the stencil: 9 node accumulators (36 registers) instead
+// of 27, so about twice the warps fit on an SM to hide the latency of the
+// loads and reductions, for the price of evaluating each particle's weights
+// and affine matrix three times.  CTA b takes chunk group b / 3 and slab
+// b % 3: the three CTAs reading one group are launched back to back, so the
+// second and third reads of the particles hit L2.
+template <int K>
+__global__ void __launch_bounds__(kTransferThreads, 5) k_p2g_slab(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                  float dt, uint32_t* __restrict__ err)
+{
+    const int slab = (int)(blockIdx.x % 3u);
+    const int64_t p0 = ((int64_t)(blockIdx.x / 3u) * blockDim.x + threadIdx.x) * K;
+    if (p0 >= n)
+        return;
+    float4 acc[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m)
+        acc[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int cb[3] = {0, 0, 0};
+    bool open = false;
+    auto flush = [&]() {
+        StencilIndex si;
+        if (!stencil_index(gv, cb, si)) {
+            atomicOr(err, ST_MISSED);
+            return;
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                atomicAdd(&gv.cur[si(i, j, slab)], acc[i + 3 * j]);
+    };
+#pragma unroll 1
+    for (int c = 0; c < K; ++c) {
+        const int64_t p = p0 + c;
+        if (p >= n)
+            break;
+        P2GParticle q;
+        if (!load_p2g_particle(sp, pv, p, dt, q, err))
+            continue;
+        if (open && (q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2])) {
+            flush();
+#pragma unroll
+            for (int m = 0; m < 9; ++m)
+                acc[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            open = false;
+        }
+        if (!open) {
+            cb[0] = q.b[0];
+            cb[1] = q.b[1];
+            cb[2] = q.b[2];
+            open = true;
+        }
+        // this thread's slab k = slab: node (i, j, slab) receives
+        // w (m v + A (node - f)) and w m, the affine term split per axis
+        const float wz = slab == 0 ? q.w[2][0] : (slab == 1 ? q.w[2][1] : q.w[2][2]);
+        const float dz = (float)slab - q.f[2];
+        const float cx = q.mv[0] + q.A[2] * dz, cy = q.mv[1] + q.A[5] * dz, cz = q.mv[2] + q.A[8] * dz;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float dy = (float)j - q.f[1];
+            const float wyz = q.w[1][j] * wz;
+            const float bx = cx + q.A[1] * dy, by = cy + q.A[4] * dy, bz = cz + q.A[7] * dy;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float dx = (float)i - q.f[0];
+                const float wt = q.w[0][i] * wyz;
+                float4& a = acc[i + 3 * j];
+                a.x = fmaf(wt, bx + q.A[0] * dx, a.x);
+                a.y = fmaf(wt, by + q.A[3] * dx, a.y);
+                a.z = fmaf(wt, bz + q.A[6] * dx, a.z);
+                a.w = fmaf(wt, q.mp, a.w);
+            }
+        }
+    }
+    if (open)
+        flush();
+}
+
+// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the
 // CTA's 128 K consecutive particles brought into shared memory first by one
 // bulk asynchronous copy per channel (the TMA engine's 1-D form), issued by
 // one thread and completed on an mbarrier.  The channel arrays are read
@@ -1418,6 +1498,8 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
     else if (variant == P2G_CHUNK4)
         k_p2g_chunk<4, false><<<blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt,
                                                                                                    err);
+    else if (variant == P2G_SLAB4)
+        k_p2g_slab<4><<<3 * blocks_for((n + 3) / 4, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_STRIDED)
         k_p2g_strided<<<blocks_for(n, kTileThreads), kTileThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_TILE)

@@ -221,7 +221,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -246,7 +246,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -582,7 +582,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4), (3, 5), (5, 5), (7, 4), (3, 6)])
+@pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4), (3, 5), (5, 5), (7, 4), (3, 6), (8, 4)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
