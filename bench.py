@@ -43,7 +43,7 @@ FRAME = 1.0 / 60.0
 SUBSTEPS_PER_FRAME = FRAME / DT            # 333.33
 SNOW = dict(E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0)
 VOL = DX ** 3 / 8
-# Algorithmic bytes per particle per launch (FP32 SoA):
+# Algorithmic bytes per particle per launch (FP32 SoA, each channel read or written once):
 #   P2G reads x 12, v 12, C 36, tau 24, vol 4, material 1                  = 89 B
 #   G2P reads x 12, F 36, Jp 4, material 1; writes x, v, C, F, Jp, tau 124 = 177 B
 # grid update per node of a physical block: read 16, write 16, clear 16 = 48 B

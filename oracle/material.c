@@ -28,8 +28,9 @@
  *                     (non-associative), or moves to the tips (p0, 0) and
  *                     (-beta p0, 0) beyond them; Jp absorbs the volume the
  *                     projection removes.
- * Readings of points the sources leave open (log of non-positive singular
- * values, tie cases) are listed in the design doc.
+ * Points the sources leave open: a non-positive singular value is floored at
+ * 1e-4 before its logarithm (an inverted sand particle), and ties are broken
+ * as the comments at each case say.
  */
 #include <math.h>
 #include <string.h>

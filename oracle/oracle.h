@@ -22,7 +22,8 @@
  *   - weakly compressible fluid: p = K (J^-gamma - 1) (Tampubolon et al. 2017).
  *   - Drucker-Prager sand: Hencky-strain St. Venant-Kirchhoff stress and
  *     the three-case return map (Klar et al. 2016).
- * Every reading the paper leaves open is listed in the design doc.
+ * Where the paper leaves a point open, the reading taken is stated at the
+ * function that implements it.
  *
  * Layout: particle arrays are AoS row-major doubles: x[n*3], v[n*3],
  * C[n*9] (C[p*9 + 3*a + b] = C_ab), F[n*9], Jp[n].  Grid arrays are a dense
