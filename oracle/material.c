@@ -29,8 +29,9 @@
  *                     (-beta p0, 0) beyond them; Jp absorbs the volume the
  *                     projection removes.
  * Points the sources leave open: a non-positive singular value is floored at
- * 1e-4 before its logarithm (an inverted sand particle), and ties are broken
- * as the comments at each case say.
+ * 1e-4 before its logarithm (an inverted sand particle); on the boundaries of
+ * the sand return map, tr eps = 0 counts as tension (projected to the apex)
+ * and dgamma = 0 as inside the cone (left unchanged).
  */
 #include <math.h>
 #include <string.h>
