@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRCS = ["bspline.c", "svd.c", "material.c", "transfer.c", "keys.c", "adjoint.c"]
 
-ELASTIC, FLUID, SNOW, SAND, NACC = 0, 1, 2, 3, 4
+ELASTIC, FLUID, SNOW, SAND, NACC, NHSAND = 0, 1, 2, 3, 4, 5
 STICKY, SLIP = 0, 1
 
 

@@ -28,6 +28,10 @@
  *                     (non-associative), or moves to the tips (p0, 0) and
  *                     (-beta p0, 0) beyond them; Jp absorbs the volume the
  *                     projection removes.
+ *   neo-Hookean sand: the sand model the paper's sand benchmark uses (Sec. 6,
+ *                     after Yue et al. 2018): neo-Hookean elasticity,
+ *                     tau = mu (F F^T - I) + lambda ln(J) I, with the same
+ *                     Drucker-Prager return map on the Hencky strain as sand.
  * Points the sources leave open: a non-positive singular value is floored at
  * 1e-4 before its logarithm (an inverted sand particle); on the boundaries of
  * the sand return map, tr eps = 0 counts as tension (projected to the apex)
@@ -166,6 +170,18 @@ void orc_kirchhoff(const orc_material* mat, const double F[9], double Jp, double
             AT(tau, i, i) = -p * J;
         break;
     }
+    case ORC_NHSAND: {
+        orc_lame(mat->E, mat->nu, &mu, &la);
+        const double lnJ = log(det3(F));
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double b = 0.0;
+                for (int k = 0; k < 3; ++k)
+                    b += AT(F, i, k) * AT(F, j, k);
+                AT(tau, i, j) = mu * (b - (i == j ? 1.0 : 0.0)) + (i == j ? la * lnJ : 0.0);
+            }
+        break;
+    }
     case ORC_NACC:
     case ORC_SAND: {
         if (mat->kind == ORC_NACC)
@@ -207,7 +223,7 @@ void orc_plasticity(const orc_material* mat, double F[9], double* Jp)
             cl[i] = sig[i] < lo ? lo : (sig[i] > hi ? hi : sig[i]);
         *Jp *= (sig[0] * sig[1] * sig[2]) / (cl[0] * cl[1] * cl[2]);
         udwt(U, cl, V, F);
-    } else if (mat->kind == ORC_SAND) {
+    } else if (mat->kind == ORC_SAND || mat->kind == ORC_NHSAND) {
         double mu, la;
         orc_lame(mat->E, mat->nu, &mu, &la);
         double U[9], sig[3], V[9], eps[3], s[3];
@@ -252,7 +268,7 @@ double orc_wave_speed(const orc_material* mat)
         nacc_lame(mat->E, mat->nu, &mu, &la);
     else
         orc_lame(mat->E, mat->nu, &mu, &la);
-    return sqrt((la + 2.0 * mu) / mat->rho);
+    return sqrt((la + 2.0 * mu) / mat->rho);   /* neo-Hookean: the same at rest */
 }
 
 double orc_cfl_dt(const orc_config* cfg, const orc_material* mats, int n_mats, double v_bound, double cfl,

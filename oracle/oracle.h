@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-enum { ORC_ELASTIC = 0, ORC_FLUID = 1, ORC_SNOW = 2, ORC_SAND = 3, ORC_NACC = 4 };
+enum { ORC_ELASTIC = 0, ORC_FLUID = 1, ORC_SNOW = 2, ORC_SAND = 3, ORC_NACC = 4, ORC_NHSAND = 5 };
 enum { ORC_STICKY = 0, ORC_SLIP = 1 };
 enum { ORC_OK = 0, ORC_EDOMAIN = 4, ORC_EINVAL = 1 };
 

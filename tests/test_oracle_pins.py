@@ -203,6 +203,42 @@ def test_drucker_prager_cases(orc):
     np.testing.assert_allclose(dev2 / np.linalg.norm(dev2), np.sort(dev)[::-1] / np.linalg.norm(dev), atol=1e-9)
 
 
+def _psi_neo_hookean(F, mu, la):
+    """Compressible neo-Hookean energy mu/2 (tr F^T F - 3) - mu ln J + la/2 (ln J)^2."""
+    lnJ = np.log(np.linalg.det(F))
+    return 0.5 * mu * (np.sum(F * F) - 3.0) - mu * lnJ + 0.5 * la * lnJ * lnJ
+
+
+def test_neo_hookean_sand_stress_and_return_map(orc):
+    """Neo-Hookean sand: tau = P F^T with P the derivative of the neo-Hookean
+    energy (finite differences of the energy); rotations carry no stress;
+    the small-strain limit is linear elasticity, the Hencky sand stress to
+    first order; the return map is the sand's (cases I-III pinned above)."""
+    rng = np.random.default_rng(17)
+    E, nu = 3.5e5, 0.3
+    mu, la = orc.lame(E, nu)
+    nh = orc.material(orc.NHSAND, E=E, nu=nu, friction_deg=30.0)
+    sa = orc.material(orc.SAND, E=E, nu=nu, friction_deg=30.0)
+    for _ in range(10):
+        F = np.eye(3) + 0.3 * rng.normal(size=(3, 3))
+        if np.linalg.det(F) < 0.2:
+            continue
+        P = _fd_first_pk(lambda G: _psi_neo_hookean(G, mu, la), F)
+        np.testing.assert_allclose(orc.kirchhoff(nh, F), P @ F.T, rtol=0, atol=1e-4 * E)
+    np.testing.assert_allclose(orc.kirchhoff(nh, _rand_rot(rng)), 0, atol=1e-9 * E)
+    eps = 1e-6 * np.array([[1.0, 0.3, -0.2], [0.3, -0.5, 0.1], [-0.2, 0.1, 0.7]])
+    lin = 2 * mu * eps + la * np.trace(eps) * np.eye(3)
+    np.testing.assert_allclose(orc.kirchhoff(nh, np.eye(3) + eps), lin, rtol=0, atol=1e-8 * E)
+    np.testing.assert_allclose(orc.kirchhoff(nh, np.eye(3) + eps), orc.kirchhoff(sa, np.eye(3) + eps), rtol=0,
+                               atol=1e-8 * E)
+    for _ in range(20):
+        F = _rand_rot(rng) @ np.diag(rng.uniform(0.9, 1.1, 3)) @ _rand_rot(rng).T
+        a, ja = orc.plasticity(nh, F)
+        b, jb = orc.plasticity(sa, F)
+        np.testing.assert_array_equal(a, b)
+        assert ja == jb
+
+
 def _nacc_pq(F, kappa, nu):
     """p = -tr(tau)/3 and q = sqrt(3/2)|dev tau| of the Hencky St. Venant-
     Kirchhoff stress of F, from numpy's SVD (independent of the oracle)."""
