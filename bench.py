@@ -431,21 +431,24 @@ def bench_snow_adaptive(frames=3, cfl=0.3):
             "ms_per_substep": ms / n_sub, "rebuilds": st["rebuilds"]}
 
 
-def bench_sand(substeps=1000):
+def bench_sand(substeps=1000, neo_hookean=False):
     """Drucker-Prager sand (phi = 30 deg), 4 random boxes, ~500K particles at
-    8 per cell, 128^3, dt 1e-4."""
+    8 per cell, 128^3, dt 1e-4; neo_hookean: the neo-Hookean sand of the
+    paper's sand benchmark instead of the Hencky St. Venant-Kirchhoff one."""
     import torch
     from paper_2111_00699_gb300 import mpm, scenes
     x, _ = scenes.sand_blocks()
     stream = torch.cuda.Stream()
-    with mpm.Simulator(128, 1.0 / 128, [mpm.material(mpm.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0)],
+    kind = mpm.NHSAND if neo_hookean else mpm.SAND
+    with mpm.Simulator(128, 1.0 / 128, [mpm.material(kind, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0)],
                        boundary=mpm.SLIP, stream=stream, p2g_variant=3, g2p_variant=0) as sim:
         sim.add_particles(torch.from_numpy(x).cuda())
         sim.run(20, 1e-4)
         ms = _events_time(stream, lambda: sim.run(substeps, 1e-4))
         sim.sync()
         st = sim.stats()
-    return {"workload": "sand blocks, %d particles, 128^3, dt=1e-4" % len(x), "value": len(x) * substeps / (ms / 1e3),
+    return {"workload": "sand blocks%s, %d particles, 128^3, dt=1e-4" % (" (neo-Hookean)" if neo_hookean else "", len(x)),
+            "value": len(x) * substeps / (ms / 1e3),
             "unit": UNIT, "ms_per_substep": ms / substeps, "rebuilds": st["rebuilds"]}
 
 
@@ -742,6 +745,7 @@ def main():
         workloads = {}
         for name, fn in (("batched", bench_batched), ("fountain", bench_fountain),
                          ("fountain_asflip", lambda: bench_fountain(asflip=True)), ("sand", bench_sand),
+                         ("sand_neo_hookean", lambda: bench_sand(neo_hookean=True)),
                          ("snow_adaptive", bench_snow_adaptive),
                          ("nacc_snow", bench_nacc_snow),
                          ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),

@@ -53,7 +53,7 @@ typedef enum {
     MPM_ENOTSUP = 8     /* the request is valid but not supported by this build */
 } mpm_status;
 
-typedef enum { MPM_ELASTIC = 0, MPM_FLUID = 1, MPM_SNOW = 2, MPM_SAND = 3, MPM_NACC = 4 } mpm_kind;
+typedef enum { MPM_ELASTIC = 0, MPM_FLUID = 1, MPM_SNOW = 2, MPM_SAND = 3, MPM_NACC = 4, MPM_NHSAND = 5 } mpm_kind;
 typedef enum { MPM_STICKY = 0, MPM_SLIP = 1 } mpm_boundary;
 
 /* One material.  E is Young's modulus (for MPM_FLUID and MPM_NACC: the bulk
@@ -66,7 +66,10 @@ typedef enum { MPM_STICKY = 0, MPM_SLIP = 1 } mpm_boundary;
  * the same Hencky elasticity from the bulk modulus E and nu, the Cam-Clay
  * yield ellipse (1 + 2 beta) q^2 + M^2 (p + beta p0)(p - p0) <= 0 with
  * p0 = E sinh(hardening * max(-alpha, 0)), alpha = alpha0 + ln Jp, and a
- * non-associative return map (q scaled at fixed p, or the tips). */
+ * non-associative return map (q scaled at fixed p, or the tips); neo-Hookean
+ * sand (the sand of the paper's sand benchmark, Sec. 6, after Yue et al.
+ * 2018) = tau = mu (F F^T - I) + lambda ln(J) I with the sand's
+ * Drucker-Prager return map on the Hencky strain. */
 typedef struct {
     int32_t kind;          /* mpm_kind */
     float E, nu, rho;

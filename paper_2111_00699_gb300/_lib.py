@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mpm.h")
 MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECAPACITY, MPM_EDOMAIN, MPM_ENONFINITE, MPM_ETIMEOUT, MPM_ECUDA, MPM_ENOTSUP = range(9)
 STATUS_NAMES = ["MPM_OK", "MPM_EINVAL", "MPM_ENOMEM", "MPM_ECAPACITY", "MPM_EDOMAIN", "MPM_ENONFINITE",
                 "MPM_ETIMEOUT", "MPM_ECUDA", "MPM_ENOTSUP"]
-ELASTIC, FLUID, SNOW, SAND, NACC = 0, 1, 2, 3, 4
+ELASTIC, FLUID, SNOW, SAND, NACC, NHSAND = 0, 1, 2, 3, 4, 5
 STICKY, SLIP = 0, 1
 APIC, ASFLIP = 0, 1
 PHASES = 4

@@ -470,7 +470,7 @@ mpm_status rebuild(mpm_ctx* ctx)
 
 bool valid_material(const mpm_material& m)
 {
-    if (m.kind < MPM_ELASTIC || m.kind > MPM_NACC)
+    if (m.kind < MPM_ELASTIC || m.kind > MPM_NHSAND)
         return false;
     if (m.kind == MPM_NACC && !(m.friction_M > 0.f && m.cohesion >= 0.f && m.hardening >= 0.f))
         return false;

@@ -769,7 +769,7 @@ mpm_status mpm_batch_create(int n_scenes, const mpm_scene_desc* scenes, const mp
         return MPM_EINVAL;
     for (int i = 0; i < n_mats; ++i) {
         const mpm_material& m = mats[i];
-        if (m.kind < MPM_ELASTIC || m.kind > MPM_NACC || !(m.rho > 0.f) || !(m.E > 0.f) ||
+        if (m.kind < MPM_ELASTIC || m.kind > MPM_NHSAND || !(m.rho > 0.f) || !(m.E > 0.f) ||
             (m.kind != MPM_FLUID && !(m.nu > -1.f && m.nu < 0.5f)))
             return MPM_EINVAL;
     }

@@ -569,6 +569,7 @@ __device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H
         sym_to_t6(t, t6);
         return true;
     }
+    bool moved = false;
     if (project) {
         if (tr >= 0.0f) {
             // case II: project to the cone tip, F <- R = exp(-eps) F, tau = 0
@@ -584,7 +585,14 @@ __device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H
             const Sym x = sym_scale(dev, dgm / nd);
             left_exp_update(x, H);
             eps = {eps.xx - x.xx, eps.yy - x.yy, eps.zz - x.zz, -x.xy + eps.xy, eps.xz - x.xz, eps.yz - x.yz};
+            moved = true;
         }
+    }
+    if (m.kind == MPM_NHSAND) {
+        // neo-Hookean: tau = mu (B - I) + lambda ln J I; the projection keeps tr eps = ln J
+        const Sym gb = moved ? left_cg_m1(H) : g;
+        sym_to_t6(sym_add_diag(sym_scale(gb, m.mu), m.la * tr), t6);
+        return true;
     }
     const Sym t = sym_add_diag(sym_scale(eps, 2.0f * m.mu), m.la * tr);
     sym_to_t6(t, t6);
@@ -596,6 +604,7 @@ __device__ __forceinline__ bool small_strain_update(const MatParams& m, float* H
 //   fixed-corotated: tau = U diag(2 mu (s - 1) s) U^T + lambda J (J - 1) I,
 //     mu, lambda scaled by exp(xi (1 - Jp)) for snow [Stomakhin 2013];
 //   sand: tau = U diag(2 mu e + lambda tr e) U^T, e = ln s [Klar 2016];
+//   neo-Hookean sand: tau = U diag(mu (s^2 - 1) + lambda ln J) U^T [Yue 2018];
 //   fluid: tau = -p J I, p = K (J^-gamma - 1) [Tampubolon 2017].
 __device__ __forceinline__ void stress_h(const MatParams& m, const float* H, float jm1, float* t6)
 {
@@ -615,12 +624,13 @@ __device__ __forceinline__ void stress_h(const MatParams& m, const float* H, flo
     SVDH d;
     svd_h(H, d);
     float dg[3];
-    if (m.kind == MPM_SAND || m.kind == MPM_NACC) {
+    if (m.kind == MPM_SAND || m.kind == MPM_NACC || m.kind == MPM_NHSAND) {
         float e[3] = {hencky(d.s[0], d.sm1[0]), hencky(d.s[1], d.sm1[1]), hencky(d.s[2], d.sm1[2])};
         float tr = e[0] + e[1] + e[2];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            dg[k] = 2.0f * m.mu * e[k] + m.la * tr;
+            dg[k] = m.kind == MPM_NHSAND ? m.mu * d.sm1[k] * (d.s[k] + 1.0f) + m.la * tr
+                                         : 2.0f * m.mu * e[k] + m.la * tr;
         tau6(d.U, dg, 0.0f, t6);
         return;
     }
@@ -707,7 +717,7 @@ __device__ __forceinline__ void constitutive_update(const MatParams& m, float* H
         tau6(d.U, dg, 0.0f, t6);
         return;
     }
-    if (m.kind == MPM_SAND) {
+    if (m.kind == MPM_SAND || m.kind == MPM_NHSAND) {
         float e[3] = {hencky(d.s[0], d.sm1[0]), hencky(d.s[1], d.sm1[1]), hencky(d.s[2], d.sm1[2])};
         float tr = e[0] + e[1] + e[2];
         if (tr >= 0.0f) {
@@ -740,8 +750,8 @@ __device__ __forceinline__ void constitutive_update(const MatParams& m, float* H
         }
         float tr2 = e[0] + e[1] + e[2];
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            dg[k] = 2.0f * m.mu * e[k] + m.la * tr2;
+        for (int k = 0; k < 3; ++k)   // neo-Hookean: s^2 - 1 = expm1(2 e)
+            dg[k] = m.kind == MPM_NHSAND ? m.mu * expm1f(2.0f * e[k]) + m.la * tr2 : 2.0f * m.mu * e[k] + m.la * tr2;
         tau6(d.U, dg, 0.0f, t6);
         return;
     }

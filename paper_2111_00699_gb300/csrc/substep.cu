@@ -1434,7 +1434,7 @@ __global__ void k_debug_plasticity(MatParams m, float* __restrict__ F, float* __
     for (int e = 0; e < 9; ++e)
         h[e] = F[9 * p + e] - ((e % 4 == 0) ? 1.0f : 0.0f);
     float jm1 = Jp ? Jp[p] - 1.0f : 0.0f;
-    if (m.kind == MPM_SNOW || m.kind == MPM_SAND || m.kind == MPM_NACC)
+    if (m.kind == MPM_SNOW || m.kind == MPM_SAND || m.kind == MPM_NACC || m.kind == MPM_NHSAND)
         constitutive_update(m, h, jm1, t);
 #pragma unroll
     for (int e = 0; e < 9; ++e)

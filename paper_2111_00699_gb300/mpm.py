@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import MpmError, load, material  # noqa: F401
 
-ELASTIC, FLUID, SNOW, SAND, NACC = _lib.ELASTIC, _lib.FLUID, _lib.SNOW, _lib.SAND, _lib.NACC
+ELASTIC, FLUID, SNOW, SAND, NACC, NHSAND = _lib.ELASTIC, _lib.FLUID, _lib.SNOW, _lib.SAND, _lib.NACC, _lib.NHSAND
 STICKY, SLIP = _lib.STICKY, _lib.SLIP
 APIC, ASFLIP = _lib.APIC, _lib.ASFLIP
 

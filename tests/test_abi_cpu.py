@@ -91,7 +91,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad_mat = (_lib.Material * 1)(_lib.material(_lib.NACC, E=5e4, nu=0.3, friction_M=0.0))
     assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
-    bad_mat = (_lib.Material * 1)(_lib.material(5))
+    bad_mat = (_lib.Material * 1)(_lib.material(6))
     assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     assert not ctx.value
 

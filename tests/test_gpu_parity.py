@@ -87,7 +87,7 @@ def test_svd_matches_numpy(M):
 
 
 @pytest.mark.parametrize("scale", [0.05, 0.01])
-@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc", "nhsand"])
 def test_stress_matches_oracle(M, kind, scale):
     """Stress of stored states, on the SVD path (5 % strain) and on the
     small-strain series path (1 %)."""
@@ -95,7 +95,8 @@ def test_stress_matches_oracle(M, kind, scale):
     n = 2048
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2), snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, hardening=10.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0), sand=dict(kind=M.SAND, E=3.5e5, nu=0.3),
-              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, hardening=5.0))[kind]
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, hardening=5.0),
+              nhsand=dict(kind=M.NHSAND, E=3.5e5, nu=0.3))[kind]
     k = kw.pop("kind")
     gm, om = M.material(k, **kw), orc.material(k, **kw)
     F = (np.eye(3) + scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
@@ -105,7 +106,7 @@ def test_stress_matches_oracle(M, kind, scale):
     assert linf(tau, ref) <= 1e-4 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("kind", ["elastic", "snow", "sand"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "sand", "nhsand"])
 def test_stress_small_strain_matches_oracle(M, kind):
     """Strains of 1e-4: the stress is proportional to sigma - 1, which an SVD
     of F itself resolves only to ~1e-7 / 1e-4 = 1e-3 relative.  The kernels
@@ -115,7 +116,7 @@ def test_stress_small_strain_matches_oracle(M, kind):
     rng = np.random.default_rng(11)
     n = 2048
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2), snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, hardening=10.0),
-              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3))[kind]
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3), nhsand=dict(kind=M.NHSAND, E=3.5e5, nu=0.3))[kind]
     k = kw.pop("kind")
     gm, om = M.material(k, **kw), orc.material(k, **kw)
     F = (np.eye(3) + 1e-4 * rng.normal(size=(n, 3, 3))).astype(np.float32)
@@ -135,6 +136,7 @@ def test_plasticity_matches_oracle(M, scale):
     n = 1024
     for kind, kw in ((M.SNOW, dict(E=1.4e5, nu=0.2, theta_c=2.5e-2, theta_s=7.5e-3)),
                      (M.SAND, dict(E=3.5e5, nu=0.3, friction_deg=30.0)),
+                     (M.NHSAND, dict(E=3.5e5, nu=0.3, friction_deg=30.0)),
                      (M.NACC, dict(E=5e4, nu=0.3, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01))):
         gm, om = M.material(kind, **kw), orc.material(kind, **kw)
         F = (np.eye(3) + scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
@@ -284,13 +286,14 @@ def test_substeps_small_elastic(M):
         assert linf(g["v"], s.v) <= 1e-3 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc", "nhsand"])
 def test_substeps_materials(M, kind):
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
               snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
               sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0),
-              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01))[kind]
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01),
+              nhsand=dict(kind=M.NHSAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
     k = kw.pop("kind")
     gm, om = mats_pair(M, k, **kw)
     dt = 5e-5 if k == M.SNOW else 1e-4
