@@ -494,6 +494,28 @@ def test_empty_and_ragged_sizes(M):
         assert linf(g["v"], s.v) <= 1e-4 * max(np.abs(s.v).max(), 1e-12), n
 
 
+@pytest.mark.parametrize("res", [(1024, 1024, 1024), (1024, 16, 512)])
+def test_maximum_grid_far_corner(M, res):
+    """The largest grid the key layout allows (1024 nodes per axis: 8 Morton
+    bits per axis, 30-bit keys) and a flat, non-cubic one, with a cluster
+    against the far corner's walls moving into them: parity with the oracle
+    over 10 substeps."""
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
+    dx = 1 / 1024
+    hi = np.array(res) * dx
+    rng = np.random.default_rng(21)
+    x = (hi - 0.012 + 0.008 * rng.random((3000, 3))).astype(np.float32)
+    v = np.tile(np.array([0.5, 0.5, 0.5], np.float32), (3000, 1))
+    vol = dx ** 3 / 8
+    cfg = orc.config(list(res), dx, orc.STICKY)
+    with M.Simulator(list(res), dx, [gm], boundary=M.STICKY) as sim:
+        sim.add_particles(x, v=v, vol=np.full(3000, vol, np.float32))
+        s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
+        g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+
+
 def test_growth_insertion_order_and_capacity(M):
     gm = M.material(M.ELASTIC)
     xs = [scenes.cube_uniform(i, m, 0.3, 0.7) for i, m in enumerate((100, 1000, 5000))]
