@@ -686,6 +686,7 @@ mpm_status mpm_diff_create(const mpm_config* cfg, float nu, float rho, int64_t n
 
 mpm_status mpm_diff_forward(mpm_diff* d, float dt, const float* E, const float* s_in, float* s_out)
 {
+    TraceRange trace("mpm_diff_forward");
     if (!d || !E || !s_in || !s_out || !(dt > 0.f) || s_in == s_out)
         return MPM_EINVAL;
     forward_grid(d, dt, E, s_in);
@@ -697,6 +698,7 @@ mpm_status mpm_diff_forward(mpm_diff* d, float dt, const float* E, const float* 
 mpm_status mpm_diff_adjoint(mpm_diff* d, float dt, const float* E, const float* s_in, const float* g_out,
                             float* g_in, float* gE)
 {
+    TraceRange trace("mpm_diff_adjoint");
     if (!d || !E || !s_in || !g_out || !g_in || !gE || !(dt > 0.f) || g_in == g_out)
         return MPM_EINVAL;
     cudaStream_t st = d->stream;

@@ -402,6 +402,7 @@ void drop_graphs(mpm_ctx* ctx)
 // Rebuild-mapping + full sort (Sec. 4.2.1, Sec. 4.2.2).
 mpm_status rebuild(mpm_ctx* ctx)
 {
+    TraceRange trace("rebuild");
     drop_graphs(ctx);
     cudaEvent_t pa = nullptr;
     prof_begin(ctx, pa);
@@ -680,6 +681,7 @@ void mpm_destroy(mpm_ctx* ctx)
 mpm_status mpm_add_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v, const float* vol0,
                              int material, int on_device)
 {
+    TraceRange trace("mpm_add_particles");
     if (!ctx)
         return MPM_EINVAL;
     if (n < 0 || (n > 0 && !x) || material < 0 || material >= ctx->sp.n_mats)
@@ -833,6 +835,7 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
 mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const float* v, const float* vol0,
                               int material, int on_device)
 {
+    TraceRange trace("mpm_emit_particles");
     if (!ctx)
         return MPM_EINVAL;
     if (n < 0 || (n > 0 && !x) || material < 0 || material >= ctx->sp.n_mats)
@@ -900,6 +903,7 @@ mpm_status mpm_emit_particles(mpm_ctx* ctx, int64_t n, const float* x, const flo
 
 mpm_status mpm_substep(mpm_ctx* ctx, float dt)
 {
+    TraceRange trace("mpm_substep");
     if (!ctx)
         return MPM_EINVAL;
     if (!(dt > 0.f))
@@ -953,6 +957,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
 mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, int64_t max_substeps, float* dts,
                        int64_t* n_substeps)
 {
+    TraceRange trace("mpm_advance");
     if (!ctx)
         return MPM_EINVAL;
     if (n_substeps)
@@ -1048,6 +1053,7 @@ mpm_status mpm_rebuild(mpm_ctx* ctx)
 
 mpm_status mpm_read_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, float* Jp, int on_device)
 {
+    TraceRange trace("mpm_read_state");
     if (!ctx)
         return MPM_EINVAL;
     float* outs[5] = {x, v, C, F, Jp};

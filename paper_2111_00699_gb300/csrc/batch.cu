@@ -916,6 +916,7 @@ mpm_status mpm_batch_add_particles(mpm_batch* b, int scene, int64_t n, const flo
 
 mpm_status mpm_batch_substep(mpm_batch* b, const float* dt)
 {
+    TraceRange trace("mpm_batch_substep");
     if (!b || !dt)
         return MPM_EINVAL;
     bool dt_changed = false;

@@ -1,6 +1,7 @@
 // Internal types shared by the libmpm translation units (not part of the ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "mpm.h"
@@ -99,6 +100,15 @@ struct GridView {
     const uint8_t* interior; // physical block index -> 1 if its 26 neighbours (in the grid) are mapped
     float4* old;          // ASFLIP: grid velocity before forces (p / m, 0) per node; else null
     int32_t n_pblocks;
+};
+
+// NVTX range over a host call (visible in Nsight Systems timelines; a no-op
+// unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
 };
 
 // ---- launchers implemented in the .cu files -------------------------------
