@@ -44,10 +44,11 @@ SUBSTEPS_PER_FRAME = FRAME / DT            # 333.33
 SNOW = dict(E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0)
 VOL = DX ** 3 / 8
 # Algorithmic bytes per particle per launch (FP32 SoA, each channel read or written once):
-#   P2G reads x 12, v 12, C 36, tau 24, vol 4, material 1                  = 89 B
+#   P2G reads x 12, v 12, C 36, tau 24, vol 4 (the bench scene has one material: no
+#   per-particle material index)                                         = 88 B
 #   G2P reads x 12, F 36, Jp 4, material 1; writes x, v, C, F, Jp, tau 124 = 177 B
 # grid update per node of a physical block: read 16, write 16, clear 16 = 48 B
-BYTES_P2G = 89
+BYTES_P2G = 88
 BYTES_G2P = 177
 BYTES_GRID_NODE = 48
 
@@ -499,7 +500,8 @@ KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "t
                         "chunk4": "k_p2g_chunk<4, false>", "chunk8": "k_p2g_chunk<8, false>", "stage4": "k_p2g_stage<4>",
                         "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>", "slab4": "k_p2g_slab<4>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
-                        "occ": "k_g2p_occ<8>", "stage": "k_g2p_stage",
+                        # the bench scene has one material (snow, kind 2): the kernel specialised to it
+                        "occ": "k_g2p_occ<8, 2>", "stage": "k_g2p_stage",
                         "occ10": "k_g2p_occ<10>"}}
 
 

@@ -133,7 +133,8 @@ __device__ __forceinline__ bool make_p2g_particle(const SimParams& sp, Get get, 
 __device__ __forceinline__ bool load_p2g_particle(const SimParams& sp, const PartView& pv, int64_t p, float dt,
                                                   P2GParticle& q, uint32_t* err)
 {
-    return make_p2g_particle(sp, [&](int c) { return pv.ch(c)[p]; }, pv.mat[p], dt, q, err);
+    // a single-material scene needs no per-particle material index
+    return make_p2g_particle(sp, [&](int c) { return pv.ch(c)[p]; }, sp.n_mats == 1 ? 0 : (int)pv.mat[p], dt, q, err);
 }
 
 __device__ __forceinline__ float4 node_contribution(const P2GParticle& q, int i, int j, int k)
@@ -741,8 +742,11 @@ struct G2POut {
     float xn[3], vp[3], C[9], t6[6];
 };
 
-// get(c) reads input channel c (F - I, Jp - 1) of particle p; mat is its material.
-template <bool kFused, class Get>
+// get(c) reads input channel c (F - I, Jp - 1) of particle p; mat is its
+// material.  Kind >= 0 asserts that every particle has a material of that
+// kind (a single-material scene), so the constitutive code of the others
+// drops out of the kernel.
+template <bool kFused, int Kind, class Get>
 __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartView& pv, const GridView& gv,
                                                 int64_t p, Get get, int mat, const float* x, const int* b,
                                                 int own_rank, const float* vp, const float* Bm, float dt,
@@ -766,7 +770,9 @@ __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartV
         pv.ch(CH_X + a)[p] = xn[a];
         pv.ch(CH_V + a)[p] = vp[a];
     }
-    const MatParams m = sp.mat[mat];
+    MatParams m = sp.mat[mat];
+    if (Kind >= 0)
+        m.kind = Kind;
     float jm1 = get(CH_JP);
     float t6[6];
     if (m.kind == MPM_FLUID) {
@@ -857,14 +863,14 @@ __device__ __forceinline__ bool g2p_finish_from(const SimParams& sp, const PartV
     return true;
 }
 
-template <bool kFused>
+template <bool kFused, int Kind = -1>
 __device__ __forceinline__ bool g2p_finish_t(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
                                              const float* x, const int* b, int own_rank, const float* vp,
                                              const float* Bm, float dt, uint32_t* __restrict__ flags,
                                              uint32_t* __restrict__ err, G2POut* out)
 {
-    return g2p_finish_from<kFused>(sp, pv, gv, p, [&](int c) { return pv.ch(c)[p]; }, pv.mat[p], x, b, own_rank, vp,
-                                   Bm, dt, flags, err, out);
+    return g2p_finish_from<kFused, Kind>(sp, pv, gv, p, [&](int c) { return pv.ch(c)[p]; }, pv.mat[p], x, b,
+                                         own_rank, vp, Bm, dt, flags, err, out);
 }
 
 __device__ __forceinline__ void g2p_finish(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t p,
@@ -901,8 +907,8 @@ __global__ void __launch_bounds__(kTransferThreads) k_g2p(SimParams sp, PartView
 
 // G2P_OCC / G2P_OCC10: the thread-per-particle G2P capped at 64 (48)
 // registers, 8 (10) CTAs of 128 per SM, trading register spills for
-// occupancy.
-template <int MinBlocks>
+// occupancy.  Kind >= 0: the scene has one material, of that kind.
+template <int MinBlocks, int Kind = -1>
 __global__ void __launch_bounds__(kTransferThreads, MinBlocks) k_g2p_occ(SimParams sp, PartView pv, GridView gv,
                                                                         int64_t n, float dt,
                                                                         uint32_t* __restrict__ flags,
@@ -925,7 +931,7 @@ __global__ void __launch_bounds__(kTransferThreads, MinBlocks) k_g2p_occ(SimPara
         const float4 g = gv.cur[si(i, j, k)];
         return make_float3(g.x, g.y, g.z);
     }, vp, Bm);
-    g2p_finish(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err);
+    g2p_finish_t<false, Kind>(sp, pv, gv, p, x, b, si.pb64[0] >> 6, vp, Bm, dt, flags, err, nullptr);
 }
 
 // ASFLIP G2P (Fei et al. 2021, the integrator of the paper's fountain,
@@ -995,7 +1001,7 @@ __global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_asflip(SimParams sp
         vn[a] = fmaf(sp.flip_alpha, dv, vp[a]);
         va[a] = fmaf(beta * sp.flip_alpha, dv, vp[a]);
     }
-    g2p_finish_from<false>(sp, pv, gv, p, [&](int c) { return pv.ch(c)[p]; }, mat, x, b, si.pb64[0] >> 6, vn, Bm,
+    g2p_finish_from<false, -1>(sp, pv, gv, p, [&](int c) { return pv.ch(c)[p]; }, mat, x, b, si.pb64[0] >> 6, vn, Bm,
                            dt, flags, err, nullptr, va);
 }
 
@@ -1212,7 +1218,7 @@ __global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_stage(SimParams sp,
                 }
             }
             if (ok && have)
-                g2p_finish_from<false>(sp, pv, gv, p, get, smat[l], x, b, own_rank, vp, Bm, dt, flags, err, nullptr);
+                g2p_finish_from<false, -1>(sp, pv, gv, p, get, smat[l], x, b, own_rank, vp, Bm, dt, flags, err, nullptr);
         }
     }
     // no CTA exits with copies into its shared memory still in flight
@@ -1520,6 +1526,22 @@ void launch_grid_update(const SimParams& sp, const GridView& gv, float dt, cudaS
         k_grid<<<blocks_for((int64_t)gv.n_pblocks * 64, 256), 256, 0, s>>>(sp, gv, dt);
 }
 
+// G2P_OCC, specialised to the material kind when the scene has only one.
+static void launch_g2p_occ8(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
+                            uint32_t* flags, uint32_t* err, cudaStream_t s)
+{
+    const unsigned g = blocks_for(n, kTransferThreads);
+    switch (sp.n_mats == 1 ? sp.mat[0].kind : -1) {
+    case MPM_ELASTIC: k_g2p_occ<8, MPM_ELASTIC><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_FLUID: k_g2p_occ<8, MPM_FLUID><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_SNOW: k_g2p_occ<8, MPM_SNOW><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_SAND: k_g2p_occ<8, MPM_SAND><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_NACC: k_g2p_occ<8, MPM_NACC><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_NHSAND: k_g2p_occ<8, MPM_NHSAND><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    default: k_g2p_occ<8><<<g, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    }
+}
+
 void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt, uint32_t* flags,
                 uint32_t* err, int variant, cudaStream_t s)
 {
@@ -1532,7 +1554,7 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
         else if (variant == G2P_TILE)
             k_g2p_tile<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
         else if (variant == G2P_OCC)
-            k_g2p_occ<8><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
+            launch_g2p_occ8(sp, pv, gv, n, dt, flags, err, s);
         else if (variant == G2P_OCC10)
             k_g2p_occ<10><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);
         else if (variant == G2P_CHUNK8)

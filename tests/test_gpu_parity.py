@@ -433,6 +433,42 @@ def test_adaptive_dt_matches_oracle(M, kind):
             assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
 
 
+@pytest.mark.parametrize("g2p", [0, 4])
+def test_mixed_materials_match_oracle(M, g2p):
+    """One scene with all six material kinds, one per block of particles (the
+    generic kernels, which read each particle's material index), against the
+    oracle over 10 substeps."""
+    specs = [(M.ELASTIC, dict(E=1e4, nu=0.2, rho=1000.0)),
+             (M.SNOW, dict(E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0)),
+             (M.FLUID, dict(E=1e4, gamma=7.0, rho=1000.0)),
+             (M.SAND, dict(E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0)),
+             (M.NACC, dict(E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01)),
+             (M.NHSAND, dict(E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))]
+    gms = [M.material(k, **kw) for k, kw in specs]
+    oms = [orc.material(k, **kw) for k, kw in specs]
+    rng = np.random.default_rng(8)
+    vol = (1 / 64) ** 3 / 8
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    xs, vs, ms = [], [], []
+    with M.Simulator(64, 1 / 64, gms, boundary=M.SLIP, g2p_variant=g2p) as sim:
+        for i in range(len(specs)):
+            lo = np.array([0.1 + 0.13 * i, 0.2, 0.3])
+            x = (lo + 0.1 * rng.random((1500, 3))).astype(np.float32)
+            v = (0.3 * rng.normal(size=(1500, 3))).astype(np.float32)
+            sim.add_particles(x, v=v, material=i)
+            xs.append(x), vs.append(v), ms.append(np.full(1500, i, np.int32))
+        n = sim.n
+        F = (np.eye(3) + 0.01 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+        F[np.concatenate(ms) == 2] = np.eye(3)            # the fluid tracks J, not F
+        sim.write_state(F=torch.from_numpy(F).cuda())
+        s = oracle_state_from(sim.read_state(), vol, np.concatenate(ms))
+        g = _run_both(M, sim, oms, s, 10, 5e-5, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+    assert linf(g["F"], s.F) <= 1e-4
+    assert linf(g["Jp"], s.Jp) <= 1e-4
+
+
 def test_ten_substeps_snow_full_size_bench_configuration(M):
     """The 1.34M-particle snow scene in the launch configuration bench.py
     times (register-run P2G, 64-register G2P, CUDA-graph replay on a side
