@@ -329,7 +329,9 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant);
 mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
 /* Switch between separate phases (0) and the fused G2P2G transfer (1)
  * between substeps (mpm_config.use_g2p2g).  MPM_EINVAL for on = 1 when the
- * context uses MPM_ASFLIP. */
+ * context uses MPM_ASFLIP.  The fused kernel scatters the next substep's
+ * momentum with the current dt, so a substep whose dt differs from the
+ * previous one first repeats that P2G with its own dt (one extra launch). */
 mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on);
 
 /* Replay the separate substep (flag clear, P2G, grid update, G2P, flag

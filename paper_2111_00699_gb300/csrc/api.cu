@@ -109,6 +109,7 @@ struct mpm_ctx {
     // fused G2P2G mode: grid[gcur] holds the momentum of the current state
     // (primed); the stress channels are stale after fused substeps
     bool primed = false;
+    float primed_dt = 0.0f;   // the dt whose stress impulse the primed momentum carries
     bool tau_valid = true;
 
     int64_t rebuilds = 0, launches = 0;
@@ -352,6 +353,7 @@ GridView grid_view(mpm_ctx* ctx)
     g.pslot = ctx->pslot;
     g.interior = ctx->interior;
     g.old = ctx->cfg.transfer == MPM_ASFLIP ? ctx->gold : nullptr;
+    g.slot = nullptr;
     g.n_pblocks = ctx->n_pblocks;
     return g;
 }
@@ -364,13 +366,23 @@ void forget_speeds(mpm_ctx* ctx)
     ctx->known_step = -1;
 }
 
+// The grid update clears the substep's two status words before G2P sets
+// them (one launch fewer per substep); without blocks to update, a memset.
+void clear_slot(mpm_ctx* ctx, GridView& gv, int slot)
+{
+    if (gv.n_pblocks > 0)
+        gv.slot = &ctx->dstat[flag_word(slot)];
+    else
+        cudaMemsetAsync(&ctx->dstat[flag_word(slot)], 0, 8, ctx->stream);
+}
+
 // One separate substep on the context's stream: clear the flag slot, P2G,
 // grid update, G2P, copy the flags to the pinned ring.
 void enqueue_separate(mpm_ctx* ctx, float dt, int slot)
 {
     cudaStream_t s = ctx->stream;
-    cudaMemsetAsync(&ctx->dstat[flag_word(slot)], 0, 8, s);
     GridView gv = grid_view(ctx);
+    clear_slot(ctx, gv, slot);
     const PartView& pv = ctx->pv[ctx->cur];
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     prof_begin(ctx, e0);
@@ -757,8 +769,8 @@ static void enqueue_fused(mpm_ctx* ctx, float dt, int slot)
 {
     cudaStream_t s = ctx->stream;
     const PartView& pv = ctx->pv[ctx->cur];
-    cudaMemsetAsync(&ctx->dstat[flag_word(slot)], 0, 8, s);
     GridView gv = grid_view(ctx);
+    clear_slot(ctx, gv, slot);
     cudaEvent_t e1 = nullptr, e2 = nullptr;
     prof_begin(ctx, e1);
     launch_grid_update(ctx->sp, gv, dt, s);
@@ -803,6 +815,10 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
 {
     cudaStream_t s = ctx->stream;
     const PartView& pv = ctx->pv[ctx->cur];
+    // the primed momentum holds the stress impulse of the dt it was scattered
+    // with: a new dt needs a fresh P2G of the current state
+    if (ctx->primed && dt != ctx->primed_dt)
+        ctx->primed = false;
     if (!ctx->primed) {
         if (!ctx->tau_valid) {
             launch_prepare_stress(ctx->sp, pv, ctx->n, s);
@@ -818,6 +834,7 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
         ctx->launches += 1;
         ctx->primed = true;
     }
+    ctx->primed_dt = dt;   // the fused kernel scatters the next substep's momentum with this dt
     if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step && dt == ctx->graph_dt) {
         CK(replay(ctx, dt, slot, true));
     } else {

@@ -99,6 +99,7 @@ struct GridView {
     const int32_t* pslot; // physical block index -> Morton slot
     const uint8_t* interior; // physical block index -> 1 if its 26 neighbours (in the grid) are mapped
     float4* old;          // ASFLIP: grid velocity before forces (p / m, 0) per node; else null
+    uint32_t* slot;       // null, or the substep's two status words (flags, speed), zeroed by the grid update
     int32_t n_pblocks;
 };
 

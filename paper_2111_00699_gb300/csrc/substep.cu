@@ -651,6 +651,11 @@ __global__ void k_prepare_stress(SimParams sp, PartView pv, int64_t n)
 __global__ void k_grid(SimParams sp, GridView gv, float dt)
 {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0 && gv.slot) {
+        // clear this substep's status words before the G2P that sets them
+        gv.slot[0] = 0u;
+        gv.slot[1] = 0u;
+    }
     if (idx >= (int64_t)gv.n_pblocks * 64)
         return;
     float4 g = gv.cur[idx];
