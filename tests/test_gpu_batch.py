@@ -133,3 +133,26 @@ def test_batched_full_size_sampled_scenes(M):
         assert np.abs(g["x"] - s.x).max() <= 1e-4, i
         assert np.abs(g["v"] - s.v).max() <= 1e-4 * np.abs(s.v).max(), i
         assert np.abs(g["Jp"] - s.Jp).max() <= 1e-4, i
+
+
+def test_batched_paper_materials(M):
+    """The paper's own materials in one batch: an NACC snow scene and a
+    neo-Hookean sand scene, each against the oracle run alone (10 substeps,
+    random velocities so that both return maps act)."""
+    kw = [dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9, alpha0=-0.01),
+          dict(kind=M.NHSAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0)]
+    gm = [M.material(**m) for m in kw]
+    om = [orc.material(**m) for m in kw]
+    rng = np.random.default_rng(44)
+    xs = [scenes.cube_uniform(3, 4000, 0.3, 0.5), scenes.cube_uniform(4, 4000, 0.4, 0.6)]
+    vs = [(0.5 * rng.normal(size=(4000, 3))).astype(np.float32) for _ in range(2)]
+    descs = [dict(res=64, dx=1 / 64, material=0), dict(res=32, dx=1 / 32, material=1)]
+    with M.BatchSimulator(descs, gm) as bsim:
+        for i in range(2):
+            bsim.add_particles(i, xs[i], vs[i])
+        bsim.run(10, 5e-5)
+        got = [bsim.read_state(i) for i in range(2)]
+    for i, res in enumerate((64, 32)):
+        s = _oracle_run(dict(res=res), xs[i], vs[i], om[i], 5e-5, 10)
+        assert np.abs(got[i]["x"] - s.x).max() <= 1e-4
+        assert np.abs(got[i]["v"] - s.v).max() <= 1e-4 * np.abs(s.v).max()
