@@ -416,7 +416,7 @@ def bench_snow_adaptive(frames=3, cfl=0.3):
     x, _ = scenes.snow_blocks()
     stream = torch.cuda.Stream()
     with mpm.Simulator(RES, DX, [mpm.material(mpm.SNOW, **SNOW)], boundary=mpm.SLIP, stream=stream, p2g_variant=3,
-                       g2p_variant=4, resort_interval=RESORT_INTERVAL) as sim:
+                       g2p_variant=4, resort_interval=RESORT_INTERVAL, graphs=True) as sim:
         sim.add_particles(torch.from_numpy(x).cuda())
         sim.advance(1.0 / 60.0, cfl=cfl, dt_max=5e-4)
         dts = []

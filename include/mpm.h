@@ -334,15 +334,18 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
  * previous one first repeats that P2G with its own dt (one extra launch). */
 mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on);
 
-/* Replay the separate substep (flag clear, P2G, grid update, G2P, flag
- * copy) from CUDA graphs (on = 1): one graph per flag-ring slot and current
- * grid buffer, captured on first use and dropped at every rebuild, particle
- * addition, variant change or change of dt.  Removes the launch gaps between
- * the phases, which dominate small scenes.  The paper launches kernels
- * directly; this is a GB300-side choice with the same results.  EINVAL if
- * the context runs on the legacy default stream (it cannot be captured).
- * Not used while profiling is on or in fused G2P2G mode.
- * mpm_graph_launches returns the number of graph replays so far. */
+/* Replay the steady-state substep (P2G, grid update, G2P and the flag copy;
+ * in fused mode the grid update and G2P2G) from CUDA graphs (on = 1): one
+ * graph per mode, flag-ring slot, current grid buffer and current particle
+ * buffer, captured on first use and dropped at every rebuild, particle
+ * addition or variant change (the substep of a drop launches directly).  A
+ * change of dt re-captures the substep and updates the instantiated graph in
+ * place, so adaptive steps (mpm_advance) replay too.  Removes the launch gaps
+ * between the phases, which dominate small scenes.  The paper launches
+ * kernels directly; this is a GB300-side choice with the same results.
+ * EINVAL if the context runs on the legacy default stream (it cannot be
+ * captured).  Not used while profiling is on.  mpm_graph_launches returns
+ * the number of graph replays so far. */
 mpm_status mpm_use_graphs(mpm_ctx* ctx, int on);
 int64_t mpm_graph_launches(const mpm_ctx* ctx);
 

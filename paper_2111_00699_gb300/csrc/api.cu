@@ -115,13 +115,15 @@ struct mpm_ctx {
     int64_t rebuilds = 0, launches = 0;
     std::string err;
 
-    // CUDA-graph replay of the separate substep (memset, P2G, grid update,
-    // G2P, flag copy): one graph per (flag slot, current grid buffer); every
-    // pointer and size a graph captures is fixed until the next rebuild,
-    // particle addition, variant or dt change, which drop them all
+    // CUDA-graph replay of the substep (P2G, grid update, G2P, flag copy):
+    // one graph per (mode, flag slot, current grid buffer, current particle
+    // buffer); every pointer and size a graph captures is fixed until the
+    // next rebuild, particle addition or variant change, which drop them
+    // all.  A new dt re-captures the substep and updates the instantiated
+    // graph in place (same topology, new kernel arguments).
     bool graphs = false;
     cudaGraphExec_t gexec[8 * kRing] = {};   // by mode, flag slot, current grid buffer, current particle buffer
-    float graph_dt = 0.0f;
+    float gexec_dt[8 * kRing] = {};          // the dt each instantiated graph carries
     int64_t graph_launches = 0;
     int64_t graph_drop_step = -1;   // substep of the last drop: that substep launches directly
 
@@ -790,7 +792,7 @@ static cudaError_t replay(mpm_ctx* ctx, float dt, int slot, bool fused)
 {
     cudaStream_t s = ctx->stream;
     const int gi = 16 * (fused ? 1 : 0) + 4 * slot + 2 * ctx->gcur + ctx->cur;
-    if (!ctx->gexec[gi]) {
+    if (!ctx->gexec[gi] || ctx->gexec_dt[gi] != dt) {
         cudaGraph_t graph;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess)
@@ -802,10 +804,21 @@ static cudaError_t replay(mpm_ctx* ctx, float dt, int slot, bool fused)
         e = cudaStreamEndCapture(s, &graph);
         if (e != cudaSuccess)
             return e;
-        e = cudaGraphInstantiate(&ctx->gexec[gi], graph, 0);
+        if (ctx->gexec[gi]) {
+            // same nodes, new dt in the kernel arguments: update in place
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(ctx->gexec[gi], graph, &info) != cudaSuccess) {
+                cudaGetLastError();   // clear the update's error; instantiate afresh
+                cudaGraphExecDestroy(ctx->gexec[gi]);
+                ctx->gexec[gi] = nullptr;
+            }
+        }
+        if (!ctx->gexec[gi])
+            e = cudaGraphInstantiate(&ctx->gexec[gi], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess)
             return e;
+        ctx->gexec_dt[gi] = dt;
     }
     ctx->graph_launches += 1;
     return cudaGraphLaunch(ctx->gexec[gi], s);
@@ -835,7 +848,7 @@ static mpm_status substep_fused(mpm_ctx* ctx, float dt, int slot)
         ctx->primed = true;
     }
     ctx->primed_dt = dt;   // the fused kernel scatters the next substep's momentum with this dt
-    if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step && dt == ctx->graph_dt) {
+    if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step) {
         CK(replay(ctx, dt, slot, true));
     } else {
         enqueue_fused(ctx, dt, slot);
@@ -943,10 +956,6 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     }
     cudaStream_t s = ctx->stream;
     int slot = (int)(ctx->step % kRing);
-    if (ctx->graphs && dt != ctx->graph_dt) {
-        drop_graphs(ctx);   // captured graphs hold dt
-        ctx->graph_dt = dt;
-    }
     const int64_t since = ctx->step - (ctx->last_resort > ctx->last_rebuild ? ctx->last_resort : ctx->last_rebuild);
     if (ctx->cfg.resort_interval > 0 && !ctx->cfg.no_sort && since >= ctx->cfg.resort_interval) {
         launch_resort_window(ctx->sp, ctx->pv[ctx->cur], ctx->pv[1 - ctx->cur], ctx->n, s);
@@ -957,7 +966,7 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt)
     }
     if (ctx->cfg.use_g2p2g)
         return substep_fused(ctx, dt, slot);
-    if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step && dt == ctx->graph_dt) {
+    if (ctx->graphs && !ctx->prof && ctx->step > ctx->graph_drop_step) {
         CK(replay(ctx, dt, slot, false));
     } else {
         enqueue_separate(ctx, dt, slot);

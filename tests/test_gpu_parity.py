@@ -383,8 +383,8 @@ def _expected_dt(om_list, cfg, starts, dts, reset, q, rem, cfl, dt_max, g=9.8):
     return rem if dt >= rem else rem / np.ceil(rem / dt)
 
 
-@pytest.mark.parametrize("kind,fused", [("elastic", False), ("fluid", False), ("elastic", True)])
-def test_adaptive_dt_matches_oracle(M, kind, fused):
+@pytest.mark.parametrize("kind,fused,graphs", [("elastic", False, False), ("fluid", False, True), ("elastic", True, True)])
+def test_adaptive_dt_matches_oracle(M, kind, fused, graphs):
     """mpm_advance: the substep sizes follow the rule (within FP32 rounding of
     the speeds), each interval is covered exactly, and the state matches the
     oracle run with the same steps -- over three calls: a fresh context, a
@@ -401,7 +401,8 @@ def test_adaptive_dt_matches_oracle(M, kind, fused):
     cfg = orc.config(64, 1 / 64, orc.SLIP)
     cfl, dt_max = 0.5, 5e-3
     starts, steps, reset = [], [], 0
-    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=fused) as sim:
+    stream = torch.cuda.Stream()
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, g2p2g=fused, graphs=graphs, stream=stream) as sim:
         sim.add_particles(x, v=v)
         s = oracle_state_from(sim.read_state(), vol)
         for call, duration in enumerate((0.01, 0.0075, 0.0125)):
@@ -431,6 +432,8 @@ def test_adaptive_dt_matches_oracle(M, kind, fused):
             g = {key: val.double().cpu().numpy() for key, val in sim.read_state().items()}
             assert linf(g["x"], s.x) <= 1e-4
             assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        if graphs:   # steps of new sizes update the captured graphs instead of dropping them
+            assert sim.graph_launches >= 10
 
 
 @pytest.mark.parametrize("g2p", [0, 4])
