@@ -626,7 +626,7 @@ def test_p2g_sparse_cloud_tile_fallback(M, variant):
 
 
 def test_autotuner_picks_a_variant_and_keeps_parity(M):
-    from paper_2111_00699_gb300 import tune
+    from paper_2111_00699_gb300 import _lib, tune
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
     gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
@@ -634,9 +634,11 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     with M.Simulator(64, 1 / 64, [gm]) as sim:
         sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
         res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1)
-        assert res["best"] in range(8) and all(v > 0 for v in res["ms"].values())
+        assert res["best"] in range(len(_lib.P2G_VARIANTS)) and len(res["ms"]) == len(_lib.P2G_VARIANTS)
+        assert all(v > 0 for v in res["ms"].values())
         res = tune.tune_g2p(sim, 1e-4, steps=2, rounds=1)
-        assert res["best"] in range(7) and all(v > 0 for v in res["ms"].values())
+        assert res["best"] in range(len(_lib.G2P_VARIANTS)) and len(res["ms"]) == len(_lib.G2P_VARIANTS)
+        assert all(v > 0 for v in res["ms"].values())
         ran = sim.stats()["substeps"]
         s = orc.State(x.astype(np.float64), vol=vol)
         for _ in range(ran):
