@@ -23,6 +23,7 @@ import hashlib
 import io
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -515,11 +516,15 @@ KERNEL_SOURCES = ("substep.cu", "device_math.cuh", "async_copy.cuh", "internal.h
 
 
 def kernel_source_hash():
-    """SHA-1 over the sources the transfer kernels are compiled from: a DRAM
-    traffic figure recorded from an ncu capture is valid only for them."""
+    """SHA-1 over the code the transfer kernels are compiled from (comments and
+    whitespace removed, so that editing a comment keeps the record): a DRAM
+    traffic figure recorded from an ncu capture is valid only for that code."""
     h = hashlib.sha1()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2111_00699_gb300", "csrc", f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -1,5 +1,6 @@
 // Device-side math for the MLS-MPM kernels: Morton codes, quadratic B-spline
-// weights, the 3x3 SVD and the four constitutive models.  FP32 throughout,
+// weights, the 3x3 SVD and the constitutive models (fixed-corotated, snow,
+// fluid, Drucker-Prager sand, NACC snow, neo-Hookean sand).  FP32 throughout,
 // compiled with fast-math intrinsics as the paper does (Sec. 4.3).
 #pragma once
 #include <cuda_runtime.h>

@@ -7,9 +7,9 @@ and to the oracle.  Every generator is deterministic in its seed.
 Scenes (paper Sec. 6):
   * ``cube_uniform``  -- i.i.d. uniform particles in a cube (small elastic case).
   * ``blocks``        -- axis-aligned boxes of random sizes sampled at 8
-    particles per cell with stratified jitter, as in the Sand Blocks setting
-    (Sec. 6, "eight particles ... in a stratified random way"); used for the
-    snow blocks and sand blocks scenes.
+    particles per cell with stratified jitter (one random point in each of a
+    cell's 2x2x2 sub-cells), the sampling of the Sand Blocks setting (Sec. 6);
+    used for the snow blocks and sand blocks scenes.
   * ``jelly_cube``    -- a jittered lattice cube with random initial velocity.
   * ``fountain_batch`` -- the particles a disk inlet emits in one substep,
     drawn from a counter-based generator (splitmix64) keyed by
