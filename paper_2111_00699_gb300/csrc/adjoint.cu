@@ -157,47 +157,88 @@ __device__ __forceinline__ void fc_tau(const DiffParams& dp, float E, const FCDe
         }
 }
 
-__global__ void dk_p2g(DiffParams dp, int64_t n, const float* __restrict__ s, const float* __restrict__ E,
-                       const float* __restrict__ vol, float dt, double* __restrict__ grid, uint32_t* err)
+// P2G of the differentiable substep.  A thread takes kRun consecutive
+// particles; while they share a base cell their node contributions add up in
+// 27 float4 registers, and each such run goes to the grid as FP64 atomics.
+// The FP32 partial sums are formed in a fixed order, so the grid sums do not
+// depend on the order of the atomics beyond FP64 rounding.
+constexpr int kRun = 4;
+constexpr int kRunThreads = 64;
+constexpr int kRunMinBlocks = 4;
+
+__global__ void __launch_bounds__(kRunThreads, kRunMinBlocks) dk_p2g(DiffParams dp, int64_t n, const float* __restrict__ s,
+                                                 const float* __restrict__ E, const float* __restrict__ vol, float dt,
+                                                 double* __restrict__ grid, uint32_t* err)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kRun;
+    if (p0 >= n)
         return;
-    const float* q = s + 24 * p;
-    DStencil S;
-    if (!d_stencil(dp, q, S)) {
-        atomicOr(err, ST_EDOMAIN);
-        return;
+    float4 acc[27];
+    DStencil run;          // stencil of the open run (its base cell addresses the flush)
+    bool open = false;
+    auto flush = [&]() {
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float4 v = acc[i + 3 * j + 9 * kk];
+                    double* g = grid + 4 * d_node(dp, run, i, j, kk);
+                    atomicAdd(g + 0, (double)v.x);
+                    atomicAdd(g + 1, (double)v.y);
+                    atomicAdd(g + 2, (double)v.z);
+                    atomicAdd(g + 3, (double)v.w);
+                }
+    };
+#pragma unroll 1
+    for (int c = 0; c < kRun; ++c) {
+        const int64_t p = p0 + c;
+        if (p >= n)
+            break;
+        const float* q = s + 24 * p;
+        DStencil S;
+        if (!d_stencil(dp, q, S)) {
+            atomicOr(err, ST_EDOMAIN);
+            continue;
+        }
+        FCDecomp dec;
+        fc_decomp(q + 15, dec);
+        float tau[9];
+        fc_tau(dp, E[p], dec, tau);
+        const float mp = dp.rho * vol[p];
+        const float k = 4.0f * dt * vol[p] * dp.inv_dx * dp.inv_dx;
+        float A[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e)
+            A[e] = (mp * q[6 + e] - k * tau[e]) * dp.dx;
+        const bool same = open && S.b[0] == run.b[0] && S.b[1] == run.b[1] && S.b[2] == run.b[2];
+        if (open && !same)
+            flush();
+        if (!same) {
+            run = S;
+#pragma unroll
+            for (int m = 0; m < 27; ++m)
+                acc[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            open = true;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float wt = S.w[0][i] * S.w[1][j] * S.w[2][kk];
+                    const float d0 = (float)i - S.f[0], d1 = (float)j - S.f[1], d2 = (float)kk - S.f[2];
+                    float4& a = acc[i + 3 * j + 9 * kk];
+                    a.x += wt * (mp * q[3] + A[0] * d0 + A[1] * d1 + A[2] * d2);
+                    a.y += wt * (mp * q[4] + A[3] * d0 + A[4] * d1 + A[5] * d2);
+                    a.z += wt * (mp * q[5] + A[6] * d0 + A[7] * d1 + A[8] * d2);
+                    a.w += wt * mp;
+                }
     }
-    FCDecomp dec;
-    fc_decomp(q + 15, dec);
-    float tau[9];
-    fc_tau(dp, E[p], dec, tau);
-    float mp = dp.rho * vol[p];
-    float k = 4.0f * dt * vol[p] * dp.inv_dx * dp.inv_dx;
-    float A[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e)
-        A[e] = (mp * q[6 + e] - k * tau[e]) * dp.dx;
-#pragma unroll
-    for (int kk = 0; kk < 3; ++kk)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float wt = S.w[0][i] * S.w[1][j] * S.w[2][kk];
-                float d0 = (float)i - S.f[0], d1 = (float)j - S.f[1], d2 = (float)kk - S.f[2];
-                float4 val;
-                val.x = wt * (mp * q[3] + A[0] * d0 + A[1] * d1 + A[2] * d2);
-                val.y = wt * (mp * q[4] + A[3] * d0 + A[4] * d1 + A[5] * d2);
-                val.z = wt * (mp * q[5] + A[6] * d0 + A[7] * d1 + A[8] * d2);
-                val.w = wt * mp;
-                double* g = grid + 4 * d_node(dp, S, i, j, kk);
-                atomicAdd(g + 0, (double)val.x);
-                atomicAdd(g + 1, (double)val.y);
-                atomicAdd(g + 2, (double)val.z);
-                atomicAdd(g + 3, (double)val.w);
-            }
+    if (open)
+        flush();
 }
 
 // v = P / m + dt g with the wall condition; Pm keeps (P, m), vel gets (v, m).
@@ -608,7 +649,8 @@ static void forward_grid(mpm_diff* d, float dt, const float* E, const float* s)
 {
     cudaStream_t st = d->stream;
     cudaMemsetAsync(d->Pm, 0, (size_t)d->nodes * 32, st);
-    dk_p2g<<<dblk(d->n, kDT), kDT, 0, st>>>(d->dp, d->n, s, E, d->vol, dt, d->Pm, d->err);
+    dk_p2g<<<dblk((d->n + kRun - 1) / kRun, kRunThreads), kRunThreads, 0, st>>>(d->dp, d->n, s, E, d->vol, dt, d->Pm,
+                                                                              d->err);
     dk_grid<<<dblk(d->nodes, 256), 256, 0, st>>>(d->dp, d->nodes, dt, d->Pm, d->vel);
     d->launches += 2;
 }
