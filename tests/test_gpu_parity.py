@@ -957,3 +957,60 @@ print("ok")
     r = subprocess.run([sys.executable, "-c", code], cwd=root, env=dict(os.environ, MPM_LIBRARY="ieee"),
                        capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
+
+
+def test_fast_math_stress_error_against_ieee_and_oracle(M):
+    """Fast-math acceptance in the paper's style (Sec. 4.3): the infinity norm
+    of the stacked n x 3 x 3 Kirchhoff stresses of the fast-math build against
+    the build without fast-math intrinsics and against the FP64 oracle, for
+    random states on both constitutive paths (5 % and 1 % strain)."""
+    import json
+    import subprocess
+    import sys
+    import tempfile
+    from paper_2111_00699_gb300 import build
+    build.build(ieee=True)
+    rng = np.random.default_rng(12)
+    n = 4096
+    kinds = {"elastic": dict(kind=M.ELASTIC, E=1e4, nu=0.2), "snow": dict(kind=M.SNOW, E=1.4e5, nu=0.2, hardening=10.0),
+             "sand": dict(kind=M.SAND, E=3.5e5, nu=0.3), "nacc": dict(kind=M.NACC, E=5e4, nu=0.3, hardening=5.0),
+             "nhsand": dict(kind=M.NHSAND, E=3.5e5, nu=0.3)}
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for scale in (0.05, 0.01):
+        F = (np.eye(3) + scale * rng.normal(size=(n, 3, 3))).astype(np.float32)
+        Jp = rng.uniform(0.95, 1.05, n).astype(np.float32)
+        code = r"""
+import json, sys, numpy as np, torch
+from paper_2111_00699_gb300 import mpm, _lib
+assert _lib.LIB_PATH.endswith("libmpm_ieee.so")
+kinds = json.loads(%r)
+F = torch.from_numpy(np.load(sys.argv[1])).cuda()
+J = torch.from_numpy(np.load(sys.argv[2])).cuda()
+out = {}
+for name, kw in kinds.items():
+    kw = dict(kw); k = kw.pop("kind")
+    out[name] = mpm.debug_stress(mpm.material(k, **kw), F, J).double().cpu().numpy().tolist()
+print(json.dumps(out))
+""" % json.dumps(kinds)
+        with tempfile.TemporaryDirectory() as tmp:
+            fp, jp = os.path.join(tmp, "F.npy"), os.path.join(tmp, "J.npy")
+            np.save(fp, F)
+            np.save(jp, Jp)
+            r = subprocess.run([sys.executable, "-c", code, fp, jp], cwd=root, env=dict(os.environ, MPM_LIBRARY="ieee"),
+                               capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        ieee = json.loads(r.stdout.strip().splitlines()[-1])
+        for name, kw in kinds.items():
+            kw = dict(kw)
+            k = kw.pop("kind")
+            fast = M.debug_stress(M.material(k, **kw), torch.from_numpy(F).cuda(),
+                                  torch.from_numpy(Jp).cuda()).double().cpu().numpy()
+            ref = np.stack([orc.kirchhoff(orc.material(k, **kw), F[i].astype(np.float64), float(Jp[i]))
+                            for i in range(n)])
+            scale_ref = np.abs(ref).max()
+            e_fast_ieee = linf(fast, np.array(ieee[name])) / scale_ref
+            e_fast = linf(fast, ref) / scale_ref
+            e_ieee = linf(np.array(ieee[name]), ref) / scale_ref
+            print("stress %-7s strain %.2f  |fast-ieee|/|tau| %.2e  |fast-oracle| %.2e  |ieee-oracle| %.2e"
+                  % (name, scale, e_fast_ieee, e_fast, e_ieee))
+            assert e_fast <= 1e-4 and e_ieee <= 1e-4 and e_fast_ieee <= 1e-4
