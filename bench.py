@@ -539,6 +539,16 @@ def _traffic_for(kernel, src_hash):
     return rec.get("bytes_per_launch")
 
 
+# The other workloads reported beside the headline scene (name, function).
+WORKLOADS = (("batched", bench_batched), ("fountain", bench_fountain),
+             ("fountain_asflip", lambda: bench_fountain(asflip=True)), ("sand", bench_sand),
+             ("sand_neo_hookean", lambda: bench_sand(neo_hookean=True)),
+             ("snow_adaptive", bench_snow_adaptive),
+             ("nacc_snow", bench_nacc_snow),
+             ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
+             ("ablations", bench_ablations), ("fast_math", bench_fast_math))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,6 +557,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true", help="skip the batched / fountain / sand sections")
+    ap.add_argument("--workload", default=None, choices=[w[0] for w in WORKLOADS],
+                    help="run only this one of the other workloads and print its JSON (for profiling)")
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
@@ -576,6 +588,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+
+    if args.workload:
+        if rank == 0:
+            print(json.dumps({args.workload: dict(WORKLOADS)[args.workload]()}))
+        return 0
 
     def barrier():
         if world > 1:
@@ -750,13 +767,7 @@ def main():
     workloads = None
     if not args.no_workloads and world == 1:
         workloads = {}
-        for name, fn in (("batched", bench_batched), ("fountain", bench_fountain),
-                         ("fountain_asflip", lambda: bench_fountain(asflip=True)), ("sand", bench_sand),
-                         ("sand_neo_hookean", lambda: bench_sand(neo_hookean=True)),
-                         ("snow_adaptive", bench_snow_adaptive),
-                         ("nacc_snow", bench_nacc_snow),
-                         ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
-                         ("ablations", bench_ablations), ("fast_math", bench_fast_math)):
+        for name, fn in WORKLOADS:
             try:
                 workloads[name] = fn()
             except Exception as exc:   # report, do not lose the main line
