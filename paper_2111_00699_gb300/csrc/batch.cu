@@ -412,7 +412,10 @@ __global__ void bk_active_scene(const SceneParams* __restrict__ scenes, int n_sc
     ascene[i] = lo;
 }
 
-__global__ void __launch_bounds__(kT, 8) bk_g2p(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ flags,
+// Thread per particle, capped at 72 registers (7 CTAs of 128 per SM): with
+// every material's constitutive code in one kernel this cap measured faster
+// than 64 (8 CTAs) or 80 (6 CTAs) registers on the 256-scene batch.
+__global__ void __launch_bounds__(kT, 7) bk_g2p(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ flags,
                                               uint32_t* __restrict__ err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
