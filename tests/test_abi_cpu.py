@@ -2,6 +2,7 @@
 function include/mpm.h declares, and argument validation that needs no GPU
 returns the documented status."""
 import ctypes
+import os
 import subprocess
 
 import numpy as np
@@ -155,3 +156,31 @@ def test_advance_rejects_a_null_context_without_the_gpu(lib):
     from paper_2111_00699_gb300 import _lib
     n = ctypes.c_int64(7)
     assert lib.mpm_advance(None, 0.01, 0.5, 1e-3, 100, None, ctypes.byref(n)) == _lib.MPM_EINVAL
+
+
+def test_header_is_plain_c_and_layouts_match_the_binding(tmp_path):
+    """include/mpm.h compiles as C11, and the sizes and field offsets a C
+    compiler gives its structs are the ones the ctypes binding uses."""
+    from paper_2111_00699_gb300 import _lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "mpm.h"
+int main(void) {
+    printf("%zu %zu %zu %zu\n", sizeof(mpm_config), sizeof(mpm_material), sizeof(mpm_stats), sizeof(mpm_scene_desc));
+    printf("%zu %zu %zu %zu\n", offsetof(mpm_config, max_particles), offsetof(mpm_config, transfer),
+           offsetof(mpm_config, flip_beta_max), offsetof(mpm_material, alpha0));
+    return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    sizes, offs = [int(v) for v in out[:4]], [int(v) for v in out[4:]]
+    assert sizes == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Material), ctypes.sizeof(_lib.Stats),
+                     ctypes.sizeof(_lib.SceneDesc)]
+    assert offs == [_lib.Config.max_particles.offset, _lib.Config.transfer.offset, _lib.Config.flip_beta_max.offset,
+                    _lib.Material.alpha0.offset]
