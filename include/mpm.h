@@ -221,10 +221,11 @@ void mpm_destroy(mpm_ctx* ctx);                  /* NULL is a no-op; syncs */
 /* ---- batched scenes ---------------------------------------------------- */
 /* Many small independent scenes advanced together: each phase of a substep
  * is one launch over all scenes, and the substep can be replayed from a CUDA
- * graph (Sec. 3.1 "minimise the number of kernels", Sec. 4.1 tail effect;
- * the batching itself is not in the paper).  Grid blocks are indexed by
- * (scene, Morton code) without compaction, and rebuild-mapping runs per
- * scene, only for the scenes whose free-zone test fired. */
+ * graph (the paper's principle of few kernels per substep, Sec. 3.1, and its
+ * tail-effect argument, Sec. 4.1; the batching itself is not in the paper).
+ * Grid blocks are indexed by (scene, Morton code) without compaction, and
+ * rebuild-mapping runs per scene, only for the scenes whose free-zone test
+ * fired.  Transfers are APIC (no ASFLIP form). */
 typedef struct mpm_batch mpm_batch; /* opaque */
 
 typedef struct {

@@ -4,8 +4,8 @@
  *
  * Sec. 4: the particle code interleaves the three integer indices; the high
  * bits are the block code, the low bits the cell code.  Sec. 4.2.2: the
- * histogram sort uses "block index concatenated with cell code" as the key;
- * with the block index equal to the rank of the block's Morton code, the
+ * histogram sort keys each particle by its block's index followed by its
+ * cell code; with the block index equal to the rank of the block's Morton code, the
  * sort order is the order of (Morton(block) << 6 | Morton(cell)).
  * Sec. 4.2.1: particle blocks are shifted by -dx/2 (base = floor(x/dx - 1/2))
  * and the physical blocks are the gblocks with their 3x3x3 neighbours.

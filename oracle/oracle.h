@@ -10,8 +10,8 @@
  * Material Point Method on Modern GPUs", Sec. 4 and Sec. 6): the five-phase
  * explicit MLS-MPM time step (Sec. 4, phase list) with quadratic B-spline
  * weights (Sec. 3.1), the particle code of Sec. 4 (block code in the high
- * bits, cell code in the low bits), the histogram sort key "block index
- * concatenated with cell code" (Sec. 4.2.2), and the physical-block set
+ * bits, cell code in the low bits), the histogram sort key (the block's
+ * index, then the cell code; Sec. 4.2.2), and the physical-block set
  * (gblocks plus their 3x3x3 neighbours, Sec. 4 and Sec. 4.2.1).  The paper
  * names MLS-MPM [Hu et al. 2018] but prints no equation, so the transfer and
  * constitutive formulas are the cited literature's, written out plainly:
