@@ -1,15 +1,18 @@
-// The three essential phases of one MLS-MPM substep (Sec. 4): P2G with the
-// stress computation merged in (Sec. 4.1), the grid update with the boundary
-// condition and the clearing of the next buffer merged in (Sec. 4.1), and
-// G2P with the F update, the return mapping and the free-zone test merged in.
+// The three essential phases of one MLS-MPM substep (Sec. 4): P2G, which
+// scatters the Kirchhoff stress the previous G2P stored; the grid update
+// with the boundary condition and the clearing of the next buffer merged in
+// (Sec. 4.1); and G2P with the F update, the return mapping, the stress of
+// the projected state and the free-zone test merged in (the SVD, projection
+// and stress of Sec. 4.1 done once per substep).
 //
 // Layout: particles are SoA float channels (coalesced per warp); grid nodes
 // are float4 (p_x, p_y, p_z, m) -- after the update (v_x, v_y, v_z, m) -- in
 // physical blocks of 4x4x4 = 64 nodes, node (i, j, k) of a block at
 // (i & 3) + 4 (j & 3) + 16 (k & 3).  A node's block index comes from the
-// direct-mapped Morton table.  P2G adds into the grid with native global
-// float4 atomics (Sec. 4.3: native atomics only, no shared-memory float
-// atomics, no __syncthreads).
+// direct-mapped Morton table.  The default P2G adds into the grid with
+// native global float4 reductions (Sec. 4.3 prefers native atomics to
+// shared-memory float atomics); the shared-memory variants are kept for the
+// ablation.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
