@@ -634,8 +634,10 @@ def main():
     tuned_g = {"best": args.g2p_variant, "best_name": _variant_name("G2P", args.g2p_variant), "ms": None}
     warm = args.warmup
     if args.p2g_variant < 0:
-        tuned = tune.tune_p2g(sim, DT, steps=20, rounds=2)      # advances 200 substeps
-        warm -= 200
+        s0 = sim.stats()["substeps"]
+        # the close candidates are re-timed after 200 substeps of drift, 100 substeps each
+        tuned = tune.tune_p2g(sim, DT, steps=20, rounds=2, refine_top=3, refine_steps=100, drift=200)
+        warm -= sim.stats()["substeps"] - s0
     else:
         sim.set_p2g_variant(args.p2g_variant)
     if args.g2p_variant < 0:

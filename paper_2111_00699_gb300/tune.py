@@ -7,33 +7,53 @@ cached over runs of 4 or 8) on the caller's own scene, with CUDA events on
 the simulator's stream, and leaves the fastest of each selected.  The
 simulation advances while it is tuned (every variant computes the same
 substep, up to float summation order).
+
+Variants whose times lie within a few per cent can rank differently once
+the particle order has drifted from the last sort; ``refine_top`` re-times
+the best few after ``drift`` further substeps, with longer runs, and keeps
+the fastest of those.
 """
 from __future__ import annotations
 
 from . import _lib
 
 
-def _tune(sim, dt, names, setter, phase, steps, rounds):
-    ms = {name: [] for name in names}
+def _time(sim, dt, names, setter, phase, steps, rounds, candidates):
+    ms = {names[v]: [] for v in candidates}
     sim.profile_enable(True)
     sim.profile_read()
     for _ in range(rounds):
-        for v, name in enumerate(names):
+        for v in candidates:
             setter(v)
             sim.run(steps, dt)
             t, k = sim.profile_read()[phase]
             if k:
-                ms[name].append(t / k)
+                ms[names[v]].append(t / k)
     sim.profile_enable(False)
-    avg = {name: (min(v) if v else float("inf")) for name, v in ms.items()}
+    return {name: (min(v) if v else float("inf")) for name, v in ms.items()}
+
+
+def _tune(sim, dt, names, setter, phase, steps, rounds, refine_top=0, refine_steps=100, drift=0):
+    avg = _time(sim, dt, names, setter, phase, steps, rounds, range(len(names)))
     best = min(range(len(names)), key=lambda v: avg[names[v]])
+    out = {"ms": avg}
+    if refine_top > 1:
+        top = sorted(range(len(names)), key=lambda v: avg[names[v]])[:refine_top]
+        setter(best)
+        sim.run(drift, dt)
+        refined = _time(sim, dt, names, setter, phase, refine_steps, rounds, top)
+        best = min(top, key=lambda v: refined[names[v]])
+        out["refined_ms"] = refined
     setter(best)
-    return {"best": best, "best_name": names[best], "ms": avg}
+    out.update({"best": best, "best_name": names[best]})
+    return out
 
 
-def tune_p2g(sim, dt: float, steps: int = 50, rounds: int = 2) -> dict:
-    """Return {"best": variant, "best_name", "ms": {name: ms per P2G launch}}; sim keeps `best`."""
-    return _tune(sim, dt, _lib.P2G_VARIANTS, sim.set_p2g_variant, "p2g", steps, rounds)
+def tune_p2g(sim, dt: float, steps: int = 50, rounds: int = 2, refine_top: int = 0, refine_steps: int = 100,
+             drift: int = 0) -> dict:
+    """Return {"best": variant, "best_name", "ms": {name: ms per P2G launch}, and with refine_top > 1
+    "refined_ms" for the re-timed candidates}; sim keeps `best`."""
+    return _tune(sim, dt, _lib.P2G_VARIANTS, sim.set_p2g_variant, "p2g", steps, rounds, refine_top, refine_steps, drift)
 
 
 def tune_g2p(sim, dt: float, steps: int = 50, rounds: int = 2) -> dict:
