@@ -633,8 +633,9 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
     cfg = orc.config(64, 1 / 64, orc.STICKY)
     with M.Simulator(64, 1 / 64, [gm]) as sim:
         sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
-        res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1)
+        res = tune.tune_p2g(sim, 1e-4, steps=2, rounds=1, refine_top=2, refine_steps=3, drift=2)
         assert res["best"] in range(len(_lib.P2G_VARIANTS)) and len(res["ms"]) == len(_lib.P2G_VARIANTS)
+        assert len(res["refined_ms"]) == 2 and _lib.P2G_VARIANTS[res["best"]] in res["refined_ms"]
         assert all(v > 0 for v in res["ms"].values())
         res = tune.tune_g2p(sim, 1e-4, steps=2, rounds=1)
         assert res["best"] in range(len(_lib.G2P_VARIANTS)) and len(res["ms"]) == len(_lib.G2P_VARIANTS)
