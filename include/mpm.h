@@ -192,7 +192,8 @@ mpm_status mpm_substep(mpm_ctx* ctx, float dt);
  * velocities written, one reduction with a stream sync supplies it instead.  cfl in (0, 1],
  * dt_max > 0.  dts: NULL, or room for max_substeps floats that receive each
  * substep's dt; n_substeps (may be NULL) receives the count.  MPM_ECAPACITY
- * if the interval needs more than max_substeps substeps (those ran).  The
+ * if the interval needs more than max_substeps substeps (those ran);
+ * MPM_ENONFINITE if the speed bound is not finite.  The
  * first call turns on the per-substep speed reduction for the context (one
  * small kernel reading v after G2P). */
 mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, int64_t max_substeps,

@@ -1031,6 +1031,8 @@ mpm_status mpm_advance(mpm_ctx* ctx, double duration, float cfl, float dt_max, i
                 ctx->known_step = s;
             }
         }
+        if (!(v2 >= 0.0f) || !isfinite(v2))
+            return fail(ctx, MPM_ENONFINITE, "mpm_advance: a particle velocity became non-finite");
         const double prev = ctx->last_dt > 0.f ? ctx->last_dt : dt_max;
         const double v_est = sqrt((double)v2) + (double)age * g * prev;
         double dt = (double)cfl * ctx->sp.dx / (v_est + ctx->c_max);
