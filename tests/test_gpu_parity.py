@@ -317,7 +317,7 @@ def test_substeps_materials(M, kind):
     assert linf(g["Jp"], s.Jp) <= 1e-4
 
 
-@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc", "nhsand"])
 def test_asflip_substeps_match_oracle(M, kind):
     """ASFLIP transfer (alpha 0.95, beta 0 compressed / 1 otherwise, the
     usual weights) against the oracle over 10 substeps, random velocities and
@@ -329,7 +329,10 @@ def test_asflip_substeps_match_oracle(M, kind):
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
               snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
-              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0),
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9,
+                        alpha0=-0.01),
+              nhsand=dict(kind=M.NHSAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
     k = kw.pop("kind")
     gm, om = mats_pair(M, k, **kw)
     dt = 5e-5 if k == M.SNOW else 1e-4
@@ -853,14 +856,17 @@ def test_no_sort_ablation_matches_oracle(M):
 
 
 @pytest.mark.parametrize("scatter", [0, 3, 4, 7])
-@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand"])
+@pytest.mark.parametrize("kind", ["elastic", "snow", "fluid", "sand", "nacc", "nhsand"])
 def test_g2p2g_matches_oracle(M, kind, scatter):
     """The fused transfer computes the same substeps as the separate phases,
     with each scatter form (thread per particle; register runs of 4 and 8)."""
     kw = dict(elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0),
               snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
-              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0))[kind]
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0),
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9,
+                        alpha0=-0.01),
+              nhsand=dict(kind=M.NHSAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0))[kind]
     k = kw.pop("kind")
     gm, om = mats_pair(M, k, **kw)
     dt = 5e-5 if k == M.SNOW else 1e-4
