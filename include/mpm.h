@@ -127,14 +127,20 @@ typedef struct {
                               2021): with v0_p the interpolated grid velocity before forces,
                               v_p <- vbar_p + flip_alpha (v_p - v0_p) and
                               x_p <- x_p + dt (vbar_p + beta flip_alpha (v_p(old) - v0_p)),
-                              beta = flip_beta_min if J < 1 - 1e-4 (det F; the fluid's J)
-                              else flip_beta_max.  C, F and J update as in APIC.  ASFLIP keeps a
+                              beta = flip_beta_min if J < 1 - flip_compress_margin (J = det F
+                              before this G2P; the fluid's tracked J) else flip_beta_max.
+                              C, F and J update as in APIC.  ASFLIP keeps a
                               third grid buffer, always gathers with one thread per particle
                               (g2p_variant is ignored) and needs use_g2p2g = 0. */
     float flip_alpha;      /* ASFLIP, in [0, 1] */
     float flip_beta_min;   /* ASFLIP, in [0, 1] */
     float flip_beta_max;   /* ASFLIP, in [0, 1] */
-    int32_t reserved[2];
+    float flip_compress_margin; /* ASFLIP: m in [0, 1) of the compressed-state test J < 1 - m.
+                              0 (the default) is the plain test J < 1.  A particle the sand
+                              return map left at J = 1 exactly (in tension) sits on the plain
+                              test's threshold, where the rounding of det F decides; m > 0
+                              counts such particles as not compressed. */
+    int32_t reserved[1];
 } mpm_config;
 
 enum { MPM_APIC = 0, MPM_ASFLIP = 1 };
@@ -385,7 +391,10 @@ mpm_status mpm_radix_sort_pairs(const uint32_t* keys_in, const int32_t* vals_in,
  *   - n > MPM_SORT_NOALLOC_MAX_KEYS returns MPM_ECAPACITY and launches nothing.
  *   - The first call on each device looks up that device's address of the
  *     array (a one-time set-up with that device current); make that first
- *     call before any CUDA stream capture.
+ *     call before any CUDA stream capture.  The address is kept for the life
+ *     of the process: after cudaDeviceReset (or any teardown of the device's
+ *     primary context) it may be stale, so do not call this entry point on a
+ *     device that was reset after its first call.
  *   - No call allocates or frees memory (no cudaMalloc / cudaFree, no
  *     allocating library routine).
  *   - All calls share the one array and it keeps whatever the last call left

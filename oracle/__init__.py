@@ -58,7 +58,8 @@ class Config(ctypes.Structure):
                 ("boundary", ctypes.c_int32), ("wall", ctypes.c_int32),
                 ("gravity", ctypes.c_double * 3),
                 ("transfer", ctypes.c_int32), ("flip_alpha", ctypes.c_double),
-                ("flip_beta_min", ctypes.c_double), ("flip_beta_max", ctypes.c_double)]
+                ("flip_beta_min", ctypes.c_double), ("flip_beta_max", ctypes.c_double),
+                ("flip_compress_margin", ctypes.c_double)]
 
 
 class Grid(ctypes.Structure):
@@ -126,10 +127,10 @@ def material(kind, E=1e4, nu=0.2, rho=1.0, gamma=7.0, theta_c=2.5e-2, theta_s=7.
 
 
 def config(res, dx, boundary=STICKY, wall=3, gravity=(0.0, -9.8, 0.0), transfer=APIC, flip_alpha=0.0,
-           flip_beta_min=0.0, flip_beta_max=0.0) -> Config:
+           flip_beta_min=0.0, flip_beta_max=0.0, flip_compress_margin=0.0) -> Config:
     r = (ctypes.c_int32 * 3)(*[int(v) for v in (res if hasattr(res, "__len__") else (res,) * 3)])
     return Config(r, float(dx), int(boundary), int(wall), (ctypes.c_double * 3)(*gravity), int(transfer),
-                  float(flip_alpha), float(flip_beta_min), float(flip_beta_max))
+                  float(flip_alpha), float(flip_beta_min), float(flip_beta_max), float(flip_compress_margin))
 
 
 def _mats(mats):

@@ -70,7 +70,9 @@ typedef struct {
                           fountain, Sec. 6.5, after Fei et al. 2021) */
     double flip_alpha; /* ASFLIP: weight of the particle's own velocity change */
     double flip_beta_min, flip_beta_max; /* ASFLIP: positional weight when the particle
-                          is compressed (J < 1 - 1e-4) / not compressed */
+                          is compressed (J < 1 - flip_compress_margin) / not compressed */
+    double flip_compress_margin; /* ASFLIP: m >= 0 in the compressed-state test J < 1 - m
+                          (0 is the plain test J < 1) */
 } orc_config;
 
 typedef struct {

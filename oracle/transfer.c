@@ -202,7 +202,7 @@ int orc_g2p(const orc_config* cfg, const orc_material* mats, int64_t n,
             Cp[e] = 4.0 * inv_dx * inv_dx * B[e];
         if (asflip) {
             double J = M->kind == ORC_FLUID ? Jp[p] : det3(&F[9 * p]);
-            double beta = J < 1.0 - 1e-4 ? cfg->flip_beta_min : cfg->flip_beta_max;
+            double beta = J < 1.0 - cfg->flip_compress_margin ? cfg->flip_beta_min : cfg->flip_beta_max;
             for (int a = 0; a < 3; ++a) {
                 double dv = v[3 * p + a] - v0p[a];
                 x[3 * p + a] += dt * (vp[a] + beta * cfg->flip_alpha * dv);

@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("use_g2p2g", ctypes.c_int32), ("p2g_variant", ctypes.c_int32), ("g2p_variant", ctypes.c_int32),
                 ("no_sort", ctypes.c_int32), ("resort_interval", ctypes.c_int32), ("transfer", ctypes.c_int32),
                 ("flip_alpha", ctypes.c_float), ("flip_beta_min", ctypes.c_float), ("flip_beta_max", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("flip_compress_margin", ctypes.c_float), ("reserved", ctypes.c_int32 * 1)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

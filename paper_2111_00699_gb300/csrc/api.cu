@@ -530,6 +530,8 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
         for (float v : w)
             if (!(v >= 0.f && v <= 1.f))
                 return MPM_EINVAL;
+        if (!(cfg->flip_compress_margin >= 0.f && cfg->flip_compress_margin < 1.f))
+            return MPM_EINVAL;
         if (cfg->use_g2p2g)
             return MPM_EINVAL;   // the fused transfer has no ASFLIP form
     }
@@ -564,6 +566,7 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
     sp.flip_alpha = cfg->transfer == MPM_ASFLIP ? cfg->flip_alpha : 0.f;
     sp.flip_beta_min = cfg->transfer == MPM_ASFLIP ? cfg->flip_beta_min : 0.f;
     sp.flip_beta_max = cfg->transfer == MPM_ASFLIP ? cfg->flip_beta_max : 0.f;
+    sp.flip_margin = cfg->transfer == MPM_ASFLIP ? cfg->flip_compress_margin : 0.f;
     int L = 0;
     while ((4 << L) < maxres)
         ++L;

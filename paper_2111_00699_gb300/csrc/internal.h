@@ -79,7 +79,7 @@ struct SimParams {
     float g[3];
     int L;                   // Morton bits per axis of the block table
     int transfer;            // MPM_APIC or MPM_ASFLIP
-    float flip_alpha, flip_beta_min, flip_beta_max;
+    float flip_alpha, flip_beta_min, flip_beta_max, flip_margin;
     int n_mats;
     MatParams mat[kMaxMaterials];
 };

@@ -377,14 +377,17 @@ void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t
 
 namespace mpm {
 namespace {
+// The maximum is taken over the bit patterns: for |v|^2 >= 0 they order as
+// the floats do, and every NaN pattern (either sign) lies above +Inf's, so a
+// NaN speed reaches the host as NaN (fmaxf would drop it).
 __global__ void k_max_speed2(PartView pv, int64_t n, uint32_t* __restrict__ word)
 {
-    float best = 0.0f;
+    uint32_t best = 0u;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const float a = pv.ch(CH_V)[p], b = pv.ch(CH_V + 1)[p], c = pv.ch(CH_V + 2)[p];
-        best = fmaxf(best, a * a + b * b + c * c);
+        best = max(best, __float_as_uint(a * a + b * b + c * c));
     }
-    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(best));
+    const unsigned m = __reduce_max_sync(0xffffffffu, best);
     if ((threadIdx.x & 31) == 0)
         atomicMax(word, m);
 }

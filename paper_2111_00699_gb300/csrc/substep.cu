@@ -301,9 +301,6 @@ __device__ __forceinline__ void acc_zero(NodeAcc& acc)
         acc.a[n] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
-// acc += contributions of particle q (same base cell as the accumulator).
-// The affine term is split per axis: (mv + A d) = (mv + A_y dy + A_z dz) +
-// A_x dx, with the (j, k) part computed once per row.
 // The contributions of particle q to its 27 nodes: add(n, wt, vx, vy, vz, m)
 // for node n = i + 3 j + 9 k receives w (m v + A (node - f)) as wt * (vx, vy,
 // vz) and w m as wt * m.  The affine term is split per axis: (mv + A d) =
@@ -531,7 +528,7 @@ __global__ void __launch_bounds__(kTransferThreads, 5) k_p2g_slab(SimParams sp, 
         flush();
 }
 
-// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the
+// P2G_STAGE4 / P2G_STAGE8: the chunked scatter of k_p2g_chunk, with the
 // CTA's 128 K consecutive particles brought into shared memory first by one
 // bulk asynchronous copy per channel (the TMA engine's 1-D form), issued by
 // one thread and completed on an mbarrier.  The channel arrays are read
@@ -947,10 +944,11 @@ __global__ void __launch_bounds__(kTransferThreads, MinBlocks) k_g2p_occ(SimPara
 // gathers v0, the grid velocity before forces, and blends in the particle's
 // own deviation from it: v <- vbar + alpha (v - v0), and the particle moves
 // with vbar + beta alpha (v - v0), beta = beta_min when the particle is
-// compressed (J < 1 - 1e-4) and beta_max otherwise.  The margin makes the
-// sand particles that the return map put at J = 1 exactly (tension) count as
-// not compressed whatever the rounding of det F.  C, F, J and the free-zone
-// test are those of APIC.  One thread per particle at 64 registers.
+// compressed (J < 1 - m, m the configured margin, 0 by default) and beta_max
+// otherwise.  J - 1 is formed from the small H = F - I (or is the fluid's
+// tracked J - 1), so it carries the rounding of H, not of F.  C, F, J and the
+// free-zone test are those of APIC.  One thread per particle at 64
+// registers.
 __global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_asflip(SimParams sp, PartView pv, GridView gv,
                                                                    int64_t n, float dt,
                                                                    uint32_t* __restrict__ flags,
@@ -1001,7 +999,7 @@ __global__ void __launch_bounds__(kTransferThreads, 8) k_g2p_asflip(SimParams sp
             H[e] = pv.ch(CH_F + e)[p];
         jm1 = det_m1(H);
     }
-    const float beta = jm1 < -1e-4f ? sp.flip_beta_min : sp.flip_beta_max;
+    const float beta = jm1 < -sp.flip_margin ? sp.flip_beta_min : sp.flip_beta_max;
     float vn[3], va[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

@@ -52,7 +52,8 @@ class Simulator:
                  max_particles=0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
                  device=None, p2g_variant: int = 3, g2p_variant: int = 0, g2p2g: bool = False,
                  no_sort: bool = False, graphs: bool = False, resort_interval: int = 0, transfer: int = 0,
-                 flip_alpha: float = 0.0, flip_beta_min: float = 0.0, flip_beta_max: float = 0.0):
+                 flip_alpha: float = 0.0, flip_beta_min: float = 0.0, flip_beta_max: float = 0.0,
+                 flip_compress_margin: float = 0.0):
         lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -78,6 +79,7 @@ class Simulator:
         cfg.flip_alpha = float(flip_alpha)
         cfg.flip_beta_min = float(flip_beta_min)
         cfg.flip_beta_max = float(flip_beta_max)
+        cfg.flip_compress_margin = float(flip_compress_margin)
         mats = (_lib.Material * len(self.materials))(*self.materials)
         self._alloc = None
         if torch_allocator:

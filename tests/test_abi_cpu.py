@@ -38,8 +38,9 @@ def test_struct_layouts_match_header(lib):
     from paper_2111_00699_gb300 import _lib
     assert ctypes.sizeof(_lib.Material) == 4 * 12
     # res, dx, boundary, wall, gravity, padding, max_particles, five int32 knobs, transfer and the
-    # three ASFLIP weights, reserved[2], padding to the 8-byte alignment of max_particles
-    assert ctypes.sizeof(_lib.Config) == 12 + 4 + 4 + 4 + 12 + 4 + 8 + 5 * 4 + 4 * 4 + 2 * 4 + 4
+    # three ASFLIP weights, the ASFLIP margin, reserved[1], padding to the 8-byte alignment of
+    # max_particles
+    assert ctypes.sizeof(_lib.Config) == 12 + 4 + 4 + 4 + 12 + 4 + 8 + 5 * 4 + 4 * 4 + 4 + 4 + 4
     assert ctypes.sizeof(_lib.Stats) == 6 * 8
 
 
@@ -79,6 +80,10 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
         bad = _lib.Config.from_buffer_copy(cfg)
         bad.transfer, bad.flip_alpha, bad.flip_beta_min, bad.flip_beta_max, bad.use_g2p2g = (transfer, alpha, bmin,
                                                                                              bmax, fused)
+        assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
+    for margin in (-1e-4, 1.0, float("nan")):
+        bad = _lib.Config.from_buffer_copy(cfg)
+        bad.transfer, bad.flip_alpha, bad.flip_beta_max, bad.flip_compress_margin = _lib.ASFLIP, 0.9, 1.0, margin
         assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad = _lib.Config.from_buffer_copy(cfg)
     bad.g2p_variant = 7
@@ -170,8 +175,9 @@ def test_header_is_plain_c_and_layouts_match_the_binding(tmp_path):
 #include "mpm.h"
 int main(void) {
     printf("%zu %zu %zu %zu\n", sizeof(mpm_config), sizeof(mpm_material), sizeof(mpm_stats), sizeof(mpm_scene_desc));
-    printf("%zu %zu %zu %zu\n", offsetof(mpm_config, max_particles), offsetof(mpm_config, transfer),
-           offsetof(mpm_config, flip_beta_max), offsetof(mpm_material, alpha0));
+    printf("%zu %zu %zu %zu %zu\n", offsetof(mpm_config, max_particles), offsetof(mpm_config, transfer),
+           offsetof(mpm_config, flip_beta_max), offsetof(mpm_config, flip_compress_margin),
+           offsetof(mpm_material, alpha0));
     return 0;
 }
 """)
@@ -183,4 +189,4 @@ int main(void) {
     assert sizes == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Material), ctypes.sizeof(_lib.Stats),
                      ctypes.sizeof(_lib.SceneDesc)]
     assert offs == [_lib.Config.max_particles.offset, _lib.Config.transfer.offset, _lib.Config.flip_beta_max.offset,
-                    _lib.Material.alpha0.offset]
+                    _lib.Config.flip_compress_margin.offset, _lib.Material.alpha0.offset]

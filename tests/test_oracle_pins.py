@@ -502,20 +502,23 @@ def test_substep_is_phase_composition(orc):
 
 # ------------------------------------------------------------------ ASFLIP
 
+@pytest.mark.parametrize("margin", [0.0, 1e-4])
 @pytest.mark.parametrize("J_F", [1.0, 0.9, 1.1, 0.99995, 0.9998])
-def test_asflip_two_coincident_particles_closed_form(orc, J_F):
+def test_asflip_two_coincident_particles_closed_form(orc, J_F, margin):
     """Two particles at one point, zero stress (E = 0), no gravity, no wall:
     every node of their common stencil carries their mean velocity vbar,
     before and after the grid update, so APIC would give both vbar.  ASFLIP
     (Fei et al. 2021) keeps alpha times each particle's deviation v - vbar in
     its velocity and beta alpha times it in its motion, beta = beta_min when
-    the particle is compressed, J = det F < 1 - 1e-4, and beta_max otherwise
-    (three distinct weights, so that a swapped or dropped one fails; J within
-    1e-4 below 1 counts as not compressed)."""
+    the particle is compressed, J = det F < 1 - margin, and beta_max otherwise
+    (three distinct weights, so that a swapped or dropped one fails).  With
+    the default margin 0 the test is J < 1: J = 1 exactly is not compressed,
+    J = 0.99995 is; a margin of 1e-4 moves J = 0.99995 to the other branch
+    and leaves J = 0.9998 compressed."""
     dx = 1 / 32
     alpha, bmin, bmax = 0.9, 0.3, 0.7
     cfg = orc.config(32, dx, gravity=(0.0, 0.0, 0.0), transfer=orc.ASFLIP, flip_alpha=alpha,
-                     flip_beta_min=bmin, flip_beta_max=bmax)
+                     flip_beta_min=bmin, flip_beta_max=bmax, flip_compress_margin=margin)
     mat = orc.material(orc.ELASTIC, E=0.0)
     xp = np.array([0.503, 0.49, 0.51])
     v = np.array([[0.3, -0.1, 0.2], [-0.1, 0.25, 0.0]])
@@ -524,7 +527,10 @@ def test_asflip_two_coincident_particles_closed_form(orc, J_F):
     dt = 1e-3
     assert orc.substep(cfg, mat, s, dt) == 0
     vbar = v.mean(0)
-    beta = bmin if J_F < 1 - 1e-4 else bmax
+    compressed = {(1.0, 0.0): False, (0.9, 0.0): True, (1.1, 0.0): False, (0.99995, 0.0): True,
+                  (0.9998, 0.0): True, (1.0, 1e-4): False, (0.9, 1e-4): True, (1.1, 1e-4): False,
+                  (0.99995, 1e-4): False, (0.9998, 1e-4): True}[(J_F, margin)]
+    beta = bmin if compressed else bmax
     np.testing.assert_allclose(s.v, vbar + alpha * (v - vbar), atol=1e-13)
     np.testing.assert_allclose(s.x, xp + dt * (vbar + beta * alpha * (v - vbar)), atol=1e-15)
     np.testing.assert_allclose(s.C, 0, atol=1e-10)

@@ -5,9 +5,10 @@ every allocation and offers no allocator hook, or a real-time frame callback
 where an allocation could stall the device.  The test calls it through the C
 ABI twice in a row (the second call on a different, smaller input, so stale
 scratch from the first call must not leak into the result) and checks each
-result against the allocating entry point mpm_radix_sort_pairs: a sort is
-integer work, so the comparison is bit-exact.  This file is collected last
-on purpose so a failure here cannot hide any other test.
+result against the allocating entry point mpm_radix_sort_pairs and against
+numpy's stable argsort: a sort is integer work, so both comparisons are
+bit-exact.  This file is collected last on purpose so a failure here cannot
+hide any other test.
 """
 import ctypes
 
@@ -63,8 +64,11 @@ def test_noalloc_sort_matches_allocating_sort_twice(lib):
         rk, rv = _reference_sort(lib, keys, vals, bits)
         torch.cuda.synchronize()
         assert torch.equal(ko, rk) and torch.equal(vo, rv)
-        kk = ko.cpu().numpy().view(np.uint32).astype(np.int64)
-        assert np.all(np.diff(kk) >= 0)
+        # and, independently of the library's sort code, against numpy's stable sort
+        k_in = keys.cpu().numpy().view(np.uint32)
+        idx = np.argsort(k_in, kind="stable")
+        np.testing.assert_array_equal(ko.cpu().numpy().view(np.uint32), k_in[idx])
+        np.testing.assert_array_equal(vo.cpu().numpy(), vals.cpu().numpy()[idx])
 
 
 def test_noalloc_sort_rejects_oversize_input(lib):
