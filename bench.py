@@ -52,14 +52,33 @@ VOL = DX ** 3 / 8
 BYTES_P2G = 88
 BYTES_G2P = 177
 BYTES_GRID_NODE = 48
+# The same accounting in the layout-free form the measurement plan states per particle-substep
+# (FP32, each state channel moved once): P2G reads x, v, C, F, Jp = 100 B; the separate
+# substep moves 260 B (P2G 100 + G2P reads x, F, Jp 52 and writes x, v, C, F, Jp 100 + the
+# grid's ~8 B per particle at 8 particles per cell); the fused G2P2G moves 112 B (reads and
+# writes x, F, Jp 52 B each + ~8 B of grid).
+SURVEY_BYTES_P2G = 100
+SURVEY_BYTES_SUBSTEP = 260
+SURVEY_BYTES_SUBSTEP_FUSED = 112
 
 
-def workload_config(n):
+def workload_config(n, world=1):
+    """The `config` of both arms' JSON lines (the same keys and values)."""
     return {"workload": "snow blocks: 6 random boxes, %d particles at 8/cell, 256^3 grid of 4^3 blocks, "
                         "Stomakhin snow, slip walls, dt=5e-5" % n,
             "particles": n, "grid": [RES, RES, RES], "dt": DT, "material": "snow (E=1.4e5, nu=0.2, rho=400)",
             "substeps_per_frame": round(SUBSTEPS_PER_FRAME, 3),
-            "l2": "inputs larger than L2: particle state %.0f MB + grid, no flush" % (n * 133 / 1e6)}
+            "l2": "inputs larger than L2: particle state %.0f MB + grid, no flush" % (n * 133 / 1e6),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def host_cores():
+    """Host cores this process may run on, and the machine's count."""
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        usable = None
+    return {"host_cores_usable": usable, "host_cores_total": os.cpu_count()}
 
 
 # ---------------------------------------------------------------- clocks
@@ -170,8 +189,9 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(len(x)), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": workload_config(len(x), world), "impl": "reference",
+            "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                                 **host_cores()),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -210,30 +230,52 @@ def bench_batched(steps=100, warmup=5):
     descs = [dict(res=b["res"], dx=1.0 / b["res"], material=b["material"]) for b in bs]
     out = {"workload": "256 scenes, %d particles, grids 32^3-128^3, 4 materials (seed 4)" % total,
            "particles": total, "substeps": steps}
+    # autotuned launch shape: per-phase launches (P2G chunk 1/4/8 particles per thread, CTAs of
+    # 2/4/8 warps) or the persistent cooperative launch (chunk 1/4/8), all replayed from graphs
+    shapes = [(False, k, w) for k in (1, 4, 8) for w in (2, 4, 8)] + [(True, k, 4) for k in (1, 4, 8)]
+    name = lambda sh: "%s chunk %d%s" % ("persistent" if sh[0] else "per-phase", sh[1],
+                                          "" if sh[0] else ", %d warps" % sh[2])
     with mpm.BatchSimulator(descs, mats, graphs=True) as bsim:
         for i, b in enumerate(bs):
             bsim.add_particles(i, b["x"])
         bsim.run(warmup, dts)
         tune = {}
-        for k in (1, 4, 8):
-            bsim.set_p2g_chunk(k)
-            bsim.run(2, dts)
-            tune[k] = _events_time(bsim.stream, lambda: bsim.run(10, dts)) / 10
+        for rnd in range(2):
+            for sh in shapes:
+                bsim.set_persistent(sh[0])
+                bsim.set_p2g_chunk(sh[1])
+                bsim.set_cta_warps(sh[2])
+                bsim.run(2, dts)
+                t = _events_time(bsim.stream, lambda: bsim.run(10, dts)) / 10
+                tune[sh] = min(tune.get(sh, float("inf")), t)
         best = min(tune, key=tune.get)
-        bsim.set_p2g_chunk(best)
-        bsim.run(2, dts)
+        bsim.set_persistent(best[0])
+        bsim.set_p2g_chunk(best[1])
+        bsim.set_cta_warps(best[2])
+        bsim.run(8, dts)   # re-captures the graphs of every flag-ring slot before the timed run
         ms = _events_time(bsim.stream, lambda: bsim.run(steps, dts))
         bsim.sync()
         st = bsim.stats()
+    per_phase = min(v for sh, v in tune.items() if not sh[0])
+    persistent = min(v for sh, v in tune.items() if sh[0])
     out.update({"value": total * steps / (ms / 1e3), "unit": UNIT, "ms_per_substep": ms / steps,
-                "p2g_chunk": best, "chunk_ms": {str(k): v for k, v in tune.items()}, "remaps": st["remaps"],
-                "graphs": True})
-    # per-scene launches of the plain path on the same stream
+                "launch_shape": {"persistent": best[0], "p2g_chunk": best[1], "cta_warps": best[2]},
+                "shape_ms": {name(sh): v for sh, v in tune.items()},
+                "per_phase_best_ms": per_phase, "persistent_best_ms": persistent,
+                "persistent_over_per_phase_time": persistent / per_phase,
+                "remaps": st["remaps"], "graphs": True})
+    best = best[1]
+    # per-scene launches of the plain path on the same stream, with the kernels the single
+    # scene runs: the register-run P2G of the batched path's chunk length (4 or 8 particles)
+    # and the 64-register G2P specialised to each scene's material kind
+    per_scene_p2g = 4 if best == 8 else 3
+    per_scene_g2p = 4
+    out["per_scene_kernels"] = {"p2g_variant": per_scene_p2g, "g2p_variant": per_scene_g2p}
     stream = torch.cuda.Stream()
     sims = []
     for b in bs:
         sim = mpm.Simulator(b["res"], 1.0 / b["res"], [mats[b["material"]]], boundary=mpm.SLIP, stream=stream,
-                            p2g_variant=3, g2p_variant=0)
+                            p2g_variant=per_scene_p2g, g2p_variant=per_scene_g2p)
         sim.add_particles(b["x"])
         sims.append(sim)
 
@@ -351,6 +393,87 @@ def bench_ablations(substeps=100):
     out["p2g_float4_reductions_per_node"] = timed(p2g=0)
     out["p2g_shared_memory_node_tile"] = timed(p2g=2)
     out["p2g_register_runs_of_4"] = out["free_zone_full_sort"]
+    # the paper's warp-level reduction (Sec. 4.2.2): lanes grouped by cell, and runs of lanes only
+    out["p2g_warp_reduction_cell_groups"] = timed(p2g=9)
+    out["p2g_warp_reduction_runs_of_lanes"] = timed(p2g=10)
+    out["p2g_runs_into_warp_tile"] = timed(p2g=11)
+    return out
+
+
+def bench_layout_ablations(substeps=200):
+    """The paper's layout studies (Sec. 6.2) on the snow-blocks scene in the
+    bench configuration: SoA against AoSoA packets of 32 (P2G register runs
+    of 8 and the 64-register G2P, 4 warps per CTA), and G2P with the B-spline
+    weights in registers against the weights in shared memory; ms per launch
+    of each phase (CUDA events around each phase), best of two rounds."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x, _ = scenes.snow_blocks()
+    stream = torch.cuda.Stream()
+    out = {"workload": "snow blocks 1340960 particles, P2G chunk8 + G2P occ, %d substeps per setting" % substeps,
+           "unit": "ms per launch"}
+    with mpm.Simulator(RES, DX, [mpm.material(mpm.SNOW, **SNOW)], boundary=mpm.SLIP, stream=stream, p2g_variant=4,
+                       g2p_variant=4, resort_interval=RESORT_INTERVAL) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        sim.run(50, DT)
+
+        def phases(tag):
+            sim.run(5, DT)
+            sim.profile_enable(True)
+            sim.profile_read()
+            sim.run(substeps, DT)
+            ph = sim.profile_read()
+            sim.profile_enable(False)
+            for k in ("p2g", "g2p"):
+                t, nl = ph[k]
+                key = "%s_%s" % (k, tag)
+                out[key] = min(out.get(key, float("inf")), t / nl if nl else float("inf"))
+
+        for rnd in range(2):
+            sim.set_layout(False)
+            phases("soa")
+            sim.set_layout(True)
+            phases("aosoa")
+            sim.set_layout(False)
+            sim.set_g2p_variant(7)
+            phases("weights_in_shared_memory")
+            sim.set_g2p_variant(4)
+        sim.sync()
+    out["aosoa_over_soa_p2g"] = out["p2g_aosoa"] / out["p2g_soa"]
+    out["aosoa_over_soa_g2p"] = out["g2p_aosoa"] / out["g2p_soa"]
+    out["smem_weights_over_registers_g2p"] = out["g2p_weights_in_shared_memory"] / out["g2p_soa"]
+    return out
+
+
+def bench_cta_warps(substeps=200):
+    """Warps per CTA (the paper's study of Sec. 6.2) for the register-run P2G
+    (runs of 8) and the 64-register G2P, at the same registers per thread,
+    on the snow-blocks scene in the bench configuration: ms per launch of
+    each phase (CUDA events around each phase), 2, 4 and 8 warps."""
+    import torch
+    from paper_2111_00699_gb300 import mpm, scenes
+    x, _ = scenes.snow_blocks()
+    stream = torch.cuda.Stream()
+    out = {"workload": "snow blocks 1340960 particles, P2G chunk8 + G2P occ, %d substeps per setting" % substeps,
+           "unit": "ms per launch"}
+    with mpm.Simulator(RES, DX, [mpm.material(mpm.SNOW, **SNOW)], boundary=mpm.SLIP, stream=stream, p2g_variant=4,
+                       g2p_variant=4, resort_interval=RESORT_INTERVAL) as sim:
+        sim.add_particles(torch.from_numpy(x).cuda())
+        sim.run(50, DT)
+        for rnd in range(2):
+            for w in (2, 4, 8):
+                sim.set_cta_warps(w)
+                sim.run(5, DT)
+                sim.profile_enable(True)
+                sim.profile_read()
+                sim.run(substeps, DT)
+                ph = sim.profile_read()
+                sim.profile_enable(False)
+                for k in ("p2g", "g2p"):
+                    t, nl = ph[k]
+                    key = "%s_%d_warps" % (k, w)
+                    out[key] = min(out.get(key, float("inf")), t / nl if nl else float("inf"))
+        sim.sync()
     return out
 
 
@@ -499,20 +622,22 @@ def _variant_name(kind, v):
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
                         "chunk4": "k_p2g_chunk<4, false>", "chunk8": "k_p2g_chunk<8, false>", "stage4": "k_p2g_stage<4>",
-                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>", "slab4": "k_p2g_slab<4>"},
+                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>", "slab4": "k_p2g_slab<4>",
+                        "warp": "k_p2g_warp<true>", "warprun": "k_p2g_warp<false>", "wtile8": "k_p2g_wtile<8>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         # the bench scene has one material (snow, kind 2): the kernel specialised to it
-                        "occ": "k_g2p_occ<8, 2>", "stage": "k_g2p_stage",
-                        "occ10": "k_g2p_occ<10>"}}
+                        "occ": "k_g2p_occ<8, 2, 128, false>", "stage": "k_g2p_stage",
+                        "occ10": "k_g2p_occ<10, -1, 128, false>", "occsw": "k_g2p_occ<8, 2, 128, true>"}}
 
 
-FUSED_SCATTER_VARIANTS = (0, 3, 4, 7)
+FUSED_SCATTER_VARIANTS = (0, 3, 4, 7, 9, 10)
 FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chunk<4, false>",
                       4: "k_g2p2g_chunk<8, false>", 5: "k_g2p2g_chunk<4, false>", 6: "k_g2p2g_chunk<8, false>",
-                      7: "k_g2p2g_chunk<4, true>"}
+                      7: "k_g2p2g_chunk<4, true>", 8: "k_g2p2g", 9: "k_g2p2g_warp<true>", 10: "k_g2p2g_warp<false>",
+                      11: "k_g2p2g_chunk<8, false>"}
 
 
-KERNEL_SOURCES = ("substep.cu", "device_math.cuh", "async_copy.cuh", "internal.h")
+KERNEL_SOURCES = ("transfer.cuh", "p2g.cu", "g2p.cu", "g2p2g.cu", "device_math.cuh", "async_copy.cuh", "internal.h")
 
 
 def kernel_source_hash():
@@ -546,7 +671,8 @@ WORKLOADS = (("batched", bench_batched), ("fountain", bench_fountain),
              ("snow_adaptive", bench_snow_adaptive),
              ("nacc_snow", bench_nacc_snow),
              ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
-             ("ablations", bench_ablations), ("fast_math", bench_fast_math))
+             ("ablations", bench_ablations), ("cta_warps", bench_cta_warps), ("layout", bench_layout_ablations),
+             ("fast_math", bench_fast_math))
 
 
 def main():
@@ -562,9 +688,10 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8, 7 sacc4, 8 slab4); -1 = autotune")
+                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
-                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10); -1 = autotune")
+                    help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10, "
+                         "7 occsw); -1 = autotune")
     ap.add_argument("--profile-substeps", type=int, default=0,
                     help="profiler mode: run this many substeps of the snow scene with the given variants "
                          "(default chunk4 P2G, occ G2P), print one status line and exit; no timing")
@@ -630,6 +757,10 @@ def main():
     # ---- device-resident throughput (the `value`) ----
     from paper_2111_00699_gb300 import tune
     sim = fresh_sim()
+    # clocks are sampled (every 200 ms) from here to the end of the timed region: the autotuning
+    # and warm-up substeps just before it run the same kernels under the same load, and a timed
+    # region of a few ms would otherwise hold no sample at all
+    clk = ClockSampler(local).__enter__()
     tuned = {"best": args.p2g_variant, "best_name": _variant_name("P2G", args.p2g_variant), "ms": None}
     tuned_g = {"best": args.g2p_variant, "best_name": _variant_name("G2P", args.g2p_variant), "ms": None}
     warm = args.warmup
@@ -645,6 +776,9 @@ def main():
         warm -= 120
     else:
         sim.set_g2p_variant(args.g2p_variant)
+    # warps per CTA of the register-run P2G and the 64-register G2P
+    tuned_w = tune.tune_cta_warps(sim, DT, steps=20, rounds=2)  # advances 132 substeps
+    warm -= 132
     # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene;
     # the fused kernel's scatter follows the P2G variant (direct, chunk4, chunk8)
     fused_ms, fused_scatter_ms = {}, {}
@@ -678,11 +812,11 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        sim.run(args.steps, DT)
-        ev1.record(stream)
-        ev1.synchronize()
+    ev0.record(stream)
+    sim.run(args.steps, DT)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk.__exit__(None, None, None)
     sim.sync()
     barrier()
     torch.cuda.synchronize()
@@ -726,10 +860,27 @@ def main():
                    "g2p": (FUSED_KERNEL_NAMES[p2g_final] if use_fused
                            else KERNEL_NAMES["G2P"][tuned_g["best_name"]]),
                    "grid": "k_grid"}[dom]
+    # the same kernel on the layout-free byte count (P2G: x, v, C, F, Jp = 100 B per particle)
+    survey_bytes = {"p2g": SURVEY_BYTES_P2G * n_now}.get(dom)
+    achieved_survey = survey_bytes / (avg[dom] / 1e3) / 1e9 if (survey_bytes and avg[dom] > 0) else None
+    # the whole substep (timed region): own layout and the layout-free count
+    sub_own = (algo["p2g"] if not use_fused else 0) + algo["g2p"] + algo["grid"]
+    sub_survey = (SURVEY_BYTES_SUBSTEP_FUSED if use_fused else SURVEY_BYTES_SUBSTEP) * n
+    substep = {"ms": ms_per_step, "bytes_own": sub_own, "bytes_survey": sub_survey,
+               "achieved_own_gbs": sub_own / (ms_per_step / 1e3) / 1e9,
+               "achieved_survey_gbs": sub_survey / (ms_per_step / 1e3) / 1e9,
+               "frac_own": sub_own / (ms_per_step / 1e3) / 1e9 / hbm,
+               "frac_survey": sub_survey / (ms_per_step / 1e3) / 1e9 / hbm,
+               "survey_bytes_per_particle": SURVEY_BYTES_SUBSTEP_FUSED if use_fused else SURVEY_BYTES_SUBSTEP,
+               "ms_per_frame_at_frac_0p5_survey": sub_survey / (0.5 * hbm * 1e9) * 1e3 * SUBSTEPS_PER_FRAME}
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_note,
                 "algorithmic_bytes_per_launch": algo[dom], "avg_launch_ms": avg[dom],
+                "achieved_survey": achieved_survey,
+                "frac_survey": achieved_survey / hbm if achieved_survey is not None else None,
+                "survey_bytes_per_launch": survey_bytes,
                 "traffic": _traffic_for(kernel_name, src_hash),
+                "substep": substep,
                 "phases_ms_per_launch": {k: round(v, 5) for k, v in avg.items()},
                 "phase_launches": {k: v[1] for k, v in phases.items()}}
 
@@ -738,6 +889,7 @@ def main():
     if args.e2e_frames > 0:
         sim = fresh_sim(p2g_final, tuned_g["best"])
         sim.set_g2p2g(bool(use_fused))
+        sim.set_cta_warps(tuned_w["best"])
         host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
                 for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
         sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
@@ -778,13 +930,14 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, sample = oracle_throughput(x, seconds=15.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = dict({"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}, **host_cores())
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_frame": ms_per_step * SUBSTEPS_PER_FRAME,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": dict(workload_config(n), parallelism="replicas" if world > 1 else "single"),
-            "clocks": clk.summary(), "p2g_variant": tuned, "g2p_variant": tuned_g,
+            "data": "synthetic", "config": workload_config(n, world),
+            "clocks": dict(clk.summary(), window="autotuning, warm-up and timed substeps"),
+            "p2g_variant": tuned, "g2p_variant": tuned_g, "cta_warps": tuned_w,
             "transfer": {"mode": "g2p2g" if use_fused else "separate", "ms_per_substep": fused_ms,
                          "g2p2g_scatter_ms": fused_scatter_ms, "p2g_variant_used": _variant_name("P2G", p2g_final)}, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu, "workloads": workloads}

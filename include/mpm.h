@@ -97,6 +97,7 @@ typedef struct {
                               update and one kernel doing G2P and the next P2G, whose
                               scatter follows p2g_variant (3/4: register runs of 4/8
                               particles, 7: runs of 4 accumulated in shared memory,
+                              9/10: the warp-level reduction of p2g_variant 9/10, 11: as 4,
                               else one thread per particle);
                               0: separate P2G, grid update, G2P */
     int32_t p2g_variant;   /* tuning: 0 direct float4 atomics, 1 cell-strided lanes,
@@ -105,13 +106,21 @@ typedef struct {
                               each CTA's 512/1024 particles staged in shared memory by
                               bulk asynchronous copies, 7 as 3 with the accumulators in
                               thread-private shared memory, 8 as 3 split over three threads
-                              per particle run, one per z-slab of 9 nodes (see the autotuner) */
+                              per particle run, one per z-slab of 9 nodes, 9 thread per
+                              particle with the warp-level reduction of Sec. 4.2.2 (lanes
+                              grouped by base cell, a shuffle tree per group, one float4
+                              reduction per group and node), 10 the same over runs of equal
+                              cells on consecutive lanes only (the paper's no-sort case),
+                              11 as 4 with the runs flushed into a shared-memory node tile
+                              private to each warp and one reduction per touched node
+                              (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64
                               registers, 5 the same with each CTA's particle inputs and
                               2x2x2-block grid tile staged by bulk asynchronous copies,
-                              6 thread per particle at 48 registers */
+                              6 thread per particle at 48 registers, 7 as 4 with the nine
+                              B-spline weights in shared memory (weight spilling, Sec. 3.2) */
     int32_t no_sort;       /* ablation (Sec. 6 sorting study): 1 = a rebuild maps the blocks
                               but leaves the particles in their storage order (no sort, no
                               permutation; mpm_read_order then returns MPM_EINVAL); results
@@ -261,6 +270,18 @@ mpm_status mpm_batch_substep(mpm_batch* b, const float* dt);
 mpm_status mpm_batch_use_graphs(mpm_batch* b, int on);
 /* Tuning: particles per thread in the batched P2G (1, 4 or 8). */
 mpm_status mpm_batch_set_p2g_chunk(mpm_batch* b, int k);
+/* Tuning: warps per CTA (2, 4 or 8) of the per-phase P2G and G2P launches. */
+mpm_status mpm_batch_set_cta_warps(mpm_batch* b, int warps);
+/* Persistent form (on = 1): the whole substep of all scenes is one
+ * cooperative launch of as many CTAs as the device holds at once; the CTAs
+ * take tiles of particles (P2G chunks of mpm_batch_set_p2g_chunk particles
+ * per thread, G2P one per thread) and of active grid nodes from a device
+ * counter per phase, and meet at a grid-wide barrier between P2G, the grid
+ * update and G2P.  A barrier wait gives up after about a second; the next
+ * syncing call then returns MPM_ETIMEOUT.  Replayed from CUDA graphs like
+ * the per-phase form.  Off (0, the default): one launch per phase.  Results
+ * are identical up to float summation order. */
+mpm_status mpm_batch_set_persistent(mpm_batch* b, int on);
 /* Host copies of one scene's state in that scene's insertion order; any
  * pointer may be NULL.  Syncs; returns the sticky device error, if any. */
 mpm_status mpm_batch_read_state(mpm_batch* b, int scene, float* x, float* v, float* C, float* F, float* Jp);
@@ -335,6 +356,21 @@ mpm_status mpm_debug_p2g(mpm_ctx* ctx, float dt, float* grid_out, int on_device)
 mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant);
 /* Same for the G2P gather variant (mpm_config.g2p_variant). */
 mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
+/* Particle store layout (the paper's SoA / AoSoA study, Sec. 6.2): 0 = SoA,
+ * one array per state channel (the default); 1 = AoSoA, packets of 32
+ * particles with each channel's 32 floats contiguous inside the packet, so a
+ * warp's particles keep their whole state in one 4 KB span.  The current
+ * particles are converted on the stream.  AoSoA runs P2G variants 3 and 4,
+ * G2P variant 4, 4 warps per CTA and separate APIC transfers only: switching
+ * to it from another configuration, or to another configuration under it,
+ * returns MPM_EINVAL.  Results are identical up to float summation order. */
+mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa);
+/* Warps per CTA of the register-run P2G (p2g_variant 3 and 4) and of the
+ * 64-register G2P (g2p_variant 4): 2, 4 (the default) or 8, at the same
+ * registers per thread (the paper's warps-per-block study, Sec. 6.2).  The
+ * other variants keep their own CTA sizes.  Results are identical up to float
+ * summation order.  MPM_EINVAL for other values. */
+mpm_status mpm_set_cta_warps(mpm_ctx* ctx, int warps);
 /* Switch between separate phases (0) and the fused G2P2G transfer (1)
  * between substeps (mpm_config.use_g2p2g).  MPM_EINVAL for on = 1 when the
  * context uses MPM_ASFLIP.  The fused kernel scatters the next substep's

@@ -24,8 +24,9 @@ STICKY, SLIP = 0, 1
 APIC, ASFLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
-P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4", "slab4")
-G2P_VARIANTS = ("direct", "chunk4", "chunk8", "tile", "occ", "stage", "occ10")
+P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4", "slab4", "warp",
+                "warprun", "wtile8")
+G2P_VARIANTS = ("direct", "chunk4", "chunk8", "tile", "occ", "stage", "occ10", "occsw")
 
 
 class Material(ctypes.Structure):
@@ -86,6 +87,8 @@ _PROTOS = {
     "mpm_read_blocks": (I, [P, P, I64, P]),
     "mpm_debug_p2g": (I, [P, F, P, I]),
     "mpm_set_p2g_variant": (I, [P, I]),
+    "mpm_set_cta_warps": (I, [P, I]),
+    "mpm_set_layout": (I, [P, I]),
     "mpm_set_g2p_variant": (I, [P, I]),
     "mpm_set_g2p2g": (I, [P, I]),
     "mpm_use_graphs": (I, [P, I]),
@@ -100,6 +103,8 @@ _PROTOS = {
     "mpm_batch_substep": (I, [P, P]),
     "mpm_batch_use_graphs": (I, [P, I]),
     "mpm_batch_set_p2g_chunk": (I, [P, I]),
+    "mpm_batch_set_cta_warps": (I, [P, I]),
+    "mpm_batch_set_persistent": (I, [P, I]),
     "mpm_batch_read_state": (I, [P, I, P, P, P, P, P]),
     "mpm_batch_sync": (I, [P]),
     "mpm_batch_get_stats": (I, [P, P]),

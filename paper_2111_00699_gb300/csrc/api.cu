@@ -70,6 +70,7 @@ struct mpm_ctx {
     size_t pbuf_bytes = 0;
     PartView pv[2]{};
     int cur = 0;
+    int aosoa = 0;   // particle store layout of both buffers (PartView::aosoa)
 
     // block table (direct-mapped by Morton code) and physical blocks
     int64_t n_slots = 0;
@@ -215,11 +216,12 @@ inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 size_t part_bytes(int64_t cap) { return (size_t)cap * (kChannels * 4 + 1 + 4) + 512; }
 
-PartView make_view(void* base, int64_t cap)
+PartView make_view(void* base, int64_t cap, int aosoa)
 {
     PartView v;
     v.soa = (float*)base;
     v.cap = cap;
+    v.aosoa = aosoa;
     char* p = (char*)base + (size_t)cap * kChannels * 4;
     v.id = (int32_t*)p;
     v.mat = (uint8_t*)(p + (size_t)cap * 4);
@@ -305,11 +307,15 @@ mpm_status ensure_particle_capacity(mpm_ctx* ctx, int64_t need)
         dfree(ctx, nbuf[1], nb);
         return fail(ctx, MPM_ENOMEM, "particle allocation failed");
     }
-    PartView nv = make_view(nbuf[0], ncap);
+    PartView nv = make_view(nbuf[0], ncap, ctx->aosoa);
     if (ctx->n > 0) {
         const PartView& ov = ctx->pv[ctx->cur];
-        for (int c = 0; c < kChannels; ++c)
-            CK(cudaMemcpyAsync(nv.ch(c), ov.ch(c), (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (ctx->aosoa)   // whole packets: their layout does not depend on the capacity
+            CK(cudaMemcpyAsync(nv.soa, ov.soa, (size_t)((ctx->n + 31) / 32) * 32 * kChannels * 4,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+        else
+            for (int c = 0; c < kChannels; ++c)
+                CK(cudaMemcpyAsync(nv.ch(c), ov.ch(c), (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(nv.id, ov.id, (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         CK(cudaMemcpyAsync(nv.mat, ov.mat, (size_t)ctx->n, cudaMemcpyDeviceToDevice, ctx->stream));
     }
@@ -319,7 +325,7 @@ mpm_status ensure_particle_capacity(mpm_ctx* ctx, int64_t need)
     ctx->pbuf[1] = nbuf[1];
     ctx->pbuf_bytes = nb;
     ctx->pv[0] = nv;
-    ctx->pv[1] = make_view(nbuf[1], ncap);
+    ctx->pv[1] = make_view(nbuf[1], ncap, ctx->aosoa);
     ctx->cur = 0;
     ctx->cap = ncap;
     // sort buffers follow the particle capacity
@@ -567,6 +573,7 @@ mpm_status mpm_create(const mpm_config* cfg, const mpm_material* mats, int n_mat
     sp.flip_beta_min = cfg->transfer == MPM_ASFLIP ? cfg->flip_beta_min : 0.f;
     sp.flip_beta_max = cfg->transfer == MPM_ASFLIP ? cfg->flip_beta_max : 0.f;
     sp.flip_margin = cfg->transfer == MPM_ASFLIP ? cfg->flip_compress_margin : 0.f;
+    sp.cta_warps = 4;
     int L = 0;
     while ((4 << L) < maxres)
         ++L;
@@ -1243,7 +1250,48 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant)
 {
     if (!ctx || variant < 0 || variant >= kP2GVariants)
         return MPM_EINVAL;
+    if (ctx->aosoa && variant != P2G_CHUNK4 && variant != P2G_CHUNK8)
+        return fail(ctx, MPM_EINVAL, "mpm_set_p2g_variant: the AoSoA layout has P2G variants 3 and 4 only");
     ctx->cfg.p2g_variant = variant;
+    drop_graphs(ctx);
+    return MPM_OK;
+}
+
+mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa)
+{
+    if (!ctx || (aosoa != 0 && aosoa != 1))
+        return MPM_EINVAL;
+    if (aosoa == ctx->aosoa)
+        return MPM_OK;
+    if (aosoa && ((ctx->cfg.p2g_variant != P2G_CHUNK4 && ctx->cfg.p2g_variant != P2G_CHUNK8) ||
+                  ctx->cfg.g2p_variant != G2P_OCC || ctx->cfg.use_g2p2g || ctx->cfg.transfer != MPM_APIC ||
+                  ctx->sp.cta_warps != 4))
+        return fail(ctx, MPM_EINVAL,
+                    "mpm_set_layout: AoSoA needs P2G variant 3 or 4, G2P variant 4, separate APIC transfers and "
+                    "4 warps per CTA");
+    // convert the current particles into the other buffer, then make it current
+    PartView dst = ctx->pv[1 - ctx->cur];
+    dst.aosoa = aosoa;
+    if (ctx->n > 0) {
+        launch_relayout(ctx->pv[ctx->cur], dst, ctx->n, ctx->stream);
+        ctx->launches += 1;
+    }
+    ctx->aosoa = aosoa;
+    ctx->pv[0].aosoa = aosoa;
+    ctx->pv[1].aosoa = aosoa;
+    ctx->cur = 1 - ctx->cur;
+    drop_graphs(ctx);
+    CK(cudaGetLastError());
+    return MPM_OK;
+}
+
+mpm_status mpm_set_cta_warps(mpm_ctx* ctx, int warps)
+{
+    if (!ctx || (warps != 2 && warps != 4 && warps != 8))
+        return MPM_EINVAL;
+    if (ctx->aosoa && warps != 4)
+        return fail(ctx, MPM_EINVAL, "mpm_set_cta_warps: the AoSoA layout runs 4 warps per CTA only");
+    ctx->sp.cta_warps = warps;
     drop_graphs(ctx);
     return MPM_OK;
 }
@@ -1254,6 +1302,8 @@ mpm_status mpm_set_g2p2g(mpm_ctx* ctx, int on)
         return MPM_EINVAL;
     if (on && ctx->cfg.transfer == MPM_ASFLIP)
         return fail(ctx, MPM_EINVAL, "mpm_set_g2p2g: the fused transfer has no ASFLIP form");
+    if (on && ctx->aosoa)
+        return fail(ctx, MPM_EINVAL, "mpm_set_g2p2g: the fused transfer has no AoSoA form");
     if (ctx->cfg.use_g2p2g && !on && ctx->primed) {
         // back to separate phases: the next P2G needs a zero grid and the stress
         if (ctx->n_pblocks > 0)
@@ -1273,6 +1323,8 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant)
 {
     if (!ctx || variant < 0 || variant >= kG2PVariants)
         return MPM_EINVAL;
+    if (ctx->aosoa && variant != G2P_OCC)
+        return fail(ctx, MPM_EINVAL, "mpm_set_g2p_variant: the AoSoA layout has G2P variant 4 only");
     ctx->cfg.g2p_variant = variant;
     drop_graphs(ctx);
     return MPM_OK;

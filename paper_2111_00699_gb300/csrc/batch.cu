@@ -260,103 +260,152 @@ __device__ __forceinline__ bool b_load(const SceneParams& sc, const BatchView& b
     return true;
 }
 
+// The chunk of K consecutive particles starting at p0 (< n): register runs
+// per base cell, as the single-scene k_p2g_chunk, with the scene id part of
+// the run key.
 template <int K>
-__global__ void __launch_bounds__(kT) bk_p2g(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ err)
+__device__ __forceinline__ void bk_p2g_chunk(const BatchView& bv, const PartView& pv, int64_t n, int64_t p0,
+                                             uint32_t* __restrict__ err)
 {
-    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
-    if (p0 >= n)
-        return;
-    float4 acc[27];
-#pragma unroll
-    for (int i = 0; i < 27; ++i)
-        acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int cb[3] = {0, 0, 0}, cs = -1;
-    SceneParams sc;
-#pragma unroll 1
-    for (int j = 0; j < K; ++j) {
-        int64_t p = p0 + j;
-        if (p >= n)
-            break;
-        int s = bv.sid[p];
-        const SceneParams sp = bv.scenes[s];
+    if constexpr (K == 1) {
+        // one particle: its 27 contributions go straight to the grid (no accumulators)
+        const SceneParams sc = bv.scenes[bv.sid[p0]];
         BParticle q;
-        if (!b_load(sp, bv, pv, p, q, err))
-            continue;
-        bool change = cs >= 0 && (s != cs || q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2]);
-        if (change) {
+        if (!b_load(sc, bv, pv, p0, q, err))
+            return;
+        int lo[3] = {q.b[0], q.b[1], q.b[2]}, hi[3] = {q.b[0] + 2, q.b[1] + 2, q.b[2] + 2};
+        if (!b_stencil_mapped(sc, bv, lo, hi)) {
+            atomicOr(err, ST_MISSED);
+            return;
+        }
+        const StencilIndex si = scene_stencil_index(sc, q.b);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float dxo = (float)i - q.f[0], dyo = (float)jj - q.f[1], dzo = (float)k - q.f[2];
+                    const float wt = q.w[0][i] * q.w[1][jj] * q.w[2][k];
+                    float4 v;
+                    v.x = wt * (q.mv[0] + q.A[0] * dxo + q.A[1] * dyo + q.A[2] * dzo);
+                    v.y = wt * (q.mv[1] + q.A[3] * dxo + q.A[4] * dyo + q.A[5] * dzo);
+                    v.z = wt * (q.mv[2] + q.A[6] * dxo + q.A[7] * dyo + q.A[8] * dzo);
+                    v.w = wt * q.mp;
+                    atomicAdd(&bv.cur[si(i, jj, k)], v);
+                }
+        return;
+    } else {
+        float4 acc[27];
+    #pragma unroll
+        for (int i = 0; i < 27; ++i)
+            acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cb[3] = {0, 0, 0}, cs = -1;
+        SceneParams sc;
+    #pragma unroll 1
+        for (int j = 0; j < K; ++j) {
+            int64_t p = p0 + j;
+            if (p >= n)
+                break;
+            int s = bv.sid[p];
+            const SceneParams sp = bv.scenes[s];
+            BParticle q;
+            if (!b_load(sp, bv, pv, p, q, err))
+                continue;
+            bool change = cs >= 0 && (s != cs || q.b[0] != cb[0] || q.b[1] != cb[1] || q.b[2] != cb[2]);
+            if (change) {
+                int lo[3] = {cb[0], cb[1], cb[2]}, hi[3] = {cb[0] + 2, cb[1] + 2, cb[2] + 2};
+                if (b_stencil_mapped(sc, bv, lo, hi)) {
+                    const StencilIndex si = scene_stencil_index(sc, cb);
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k)
+    #pragma unroll
+                        for (int jj = 0; jj < 3; ++jj)
+    #pragma unroll
+                            for (int i = 0; i < 3; ++i)
+                                atomicAdd(&bv.cur[si(i, jj, k)], acc[i + 3 * jj + 9 * k]);
+                } else {
+                    atomicOr(err, ST_MISSED);
+                }
+    #pragma unroll
+                for (int i = 0; i < 27; ++i)
+                    acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            cs = s;
+            sc = sp;
+            cb[0] = q.b[0];
+            cb[1] = q.b[1];
+            cb[2] = q.b[2];
+            float dxo[3], dyo[3], dzo[3];
+    #pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                dxo[i] = (float)i - q.f[0];
+                dyo[i] = (float)i - q.f[1];
+                dzo[i] = (float)i - q.f[2];
+            }
+    #pragma unroll
+            for (int k = 0; k < 3; ++k)
+    #pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                    float wyz = q.w[1][jj] * q.w[2][k];
+                    float bx = q.mv[0] + q.A[1] * dyo[jj] + q.A[2] * dzo[k];
+                    float by = q.mv[1] + q.A[4] * dyo[jj] + q.A[5] * dzo[k];
+                    float bz = q.mv[2] + q.A[7] * dyo[jj] + q.A[8] * dzo[k];
+    #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        float wt = q.w[0][i] * wyz;
+                        float4& a = acc[i + 3 * jj + 9 * k];
+                        a.x += wt * (bx + q.A[0] * dxo[i]);
+                        a.y += wt * (by + q.A[3] * dxo[i]);
+                        a.z += wt * (bz + q.A[6] * dxo[i]);
+                        a.w += wt * q.mp;
+                    }
+                }
+        }
+        if (cs >= 0) {
             int lo[3] = {cb[0], cb[1], cb[2]}, hi[3] = {cb[0] + 2, cb[1] + 2, cb[2] + 2};
             if (b_stencil_mapped(sc, bv, lo, hi)) {
                 const StencilIndex si = scene_stencil_index(sc, cb);
-#pragma unroll
+    #pragma unroll
                 for (int k = 0; k < 3; ++k)
-#pragma unroll
+    #pragma unroll
                     for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
+    #pragma unroll
                         for (int i = 0; i < 3; ++i)
                             atomicAdd(&bv.cur[si(i, jj, k)], acc[i + 3 * jj + 9 * k]);
             } else {
                 atomicOr(err, ST_MISSED);
             }
-#pragma unroll
-            for (int i = 0; i < 27; ++i)
-                acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        cs = s;
-        sc = sp;
-        cb[0] = q.b[0];
-        cb[1] = q.b[1];
-        cb[2] = q.b[2];
-        float dxo[3], dyo[3], dzo[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            dxo[i] = (float)i - q.f[0];
-            dyo[i] = (float)i - q.f[1];
-            dzo[i] = (float)i - q.f[2];
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj) {
-                float wyz = q.w[1][jj] * q.w[2][k];
-                float bx = q.mv[0] + q.A[1] * dyo[jj] + q.A[2] * dzo[k];
-                float by = q.mv[1] + q.A[4] * dyo[jj] + q.A[5] * dzo[k];
-                float bz = q.mv[2] + q.A[7] * dyo[jj] + q.A[8] * dzo[k];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    float wt = q.w[0][i] * wyz;
-                    float4& a = acc[i + 3 * jj + 9 * k];
-                    a.x += wt * (bx + q.A[0] * dxo[i]);
-                    a.y += wt * (by + q.A[3] * dxo[i]);
-                    a.z += wt * (bz + q.A[6] * dxo[i]);
-                    a.w += wt * q.mp;
-                }
-            }
-    }
-    if (cs >= 0) {
-        int lo[3] = {cb[0], cb[1], cb[2]}, hi[3] = {cb[0] + 2, cb[1] + 2, cb[2] + 2};
-        if (b_stencil_mapped(sc, bv, lo, hi)) {
-            const StencilIndex si = scene_stencil_index(sc, cb);
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-                        atomicAdd(&bv.cur[si(i, jj, k)], acc[i + 3 * jj + 9 * k]);
-        } else {
-            atomicOr(err, ST_MISSED);
         }
     }
+}
+
+// CTAs of T threads at the same registers per thread for each T (168 with
+// the register runs, 80 for one particle per thread).
+template <int K, int T>
+__global__ void __launch_bounds__(T, (K == 1 ? 6 : 3) * kT / T) bk_p2g(BatchView bv, PartView pv, int64_t n,
+                                                                      uint32_t* __restrict__ err)
+{
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
+    if (p0 < n)
+        bk_p2g_chunk<K>(bv, pv, n, p0, err);
+}
+
+template <int K>
+__global__ void __maxnreg__(K == 1 ? 80 : 168) bk_p2g_w8(BatchView bv, PartView pv, int64_t n,
+                                                         uint32_t* __restrict__ err)
+{
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
+    if (p0 < n)
+        bk_p2g_chunk<K>(bv, pv, n, p0, err);
 }
 
 // Grid update over the active blocks of all scenes; the count lives on the
 // device (set by the last remap), so the launch covers a capacity bound and
 // surplus threads exit.
-__global__ void bk_grid(BatchView bv, const int32_t* __restrict__ ascene)
+__device__ __forceinline__ void bk_grid_node(const BatchView& bv, const int32_t* __restrict__ ascene, int64_t idx)
 {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t na = *bv.n_active;
-    for (; idx < na * 64; idx += (int64_t)gridDim.x * blockDim.x) {
+    {
         int ai = (int)(idx >> 6);
         int l = (int)(idx & 63);
         int64_t slot = bv.active[ai];
@@ -394,6 +443,14 @@ __global__ void bk_grid(BatchView bv, const int32_t* __restrict__ ascene)
     }
 }
 
+__global__ void bk_grid(BatchView bv, const int32_t* __restrict__ ascene)
+{
+    const int64_t na = *bv.n_active;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na * 64;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        bk_grid_node(bv, ascene, idx);
+}
+
 __global__ void bk_active_scene(const SceneParams* __restrict__ scenes, int n_scenes, const int32_t* __restrict__ active,
                                 const int32_t* __restrict__ n_active, int32_t* __restrict__ ascene)
 {
@@ -412,15 +469,10 @@ __global__ void bk_active_scene(const SceneParams* __restrict__ scenes, int n_sc
     ascene[i] = lo;
 }
 
-// Thread per particle, capped at 72 registers (7 CTAs of 128 per SM): with
-// every material's constitutive code in one kernel this cap measured faster
-// than 64 (8 CTAs) or 80 (6 CTAs) registers on the 256-scene batch.
-__global__ void __launch_bounds__(kT, 7) bk_g2p(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ flags,
-                                              uint32_t* __restrict__ err)
+// G2P of particle p with the constitutive update of its scene's material.
+__device__ __forceinline__ void bk_g2p_particle(const BatchView& bv, const PartView& pv, int64_t p,
+                                                uint32_t* __restrict__ flags, uint32_t* __restrict__ err)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n)
-        return;
     const int s = bv.sid[p];
     const SceneParams sc = bv.scenes[s];
     float x[3], f[3], w[3][3];
@@ -519,6 +571,130 @@ __global__ void __launch_bounds__(kT, 7) bk_g2p(BatchView bv, PartView pv, int64
     }
 }
 
+// Thread per particle, capped at 72 registers (7 CTAs of 128 per SM; the same
+// cap for CTAs of 64 or 256 threads): with every material's constitutive code
+// in one kernel this cap measured faster than 64 (8 CTAs) or 80 (6 CTAs)
+// registers on the 256-scene batch.
+template <int T>
+__global__ void __launch_bounds__(T, 7 * kT / T) bk_g2p(BatchView bv, PartView pv, int64_t n,
+                                                       uint32_t* __restrict__ flags, uint32_t* __restrict__ err)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n)
+        bk_g2p_particle(bv, pv, p, flags, err);
+}
+
+__global__ void __maxnreg__(72) bk_g2p_w8(BatchView bv, PartView pv, int64_t n, uint32_t* __restrict__ flags,
+                                          uint32_t* __restrict__ err)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n)
+        bk_g2p_particle(bv, pv, p, flags, err);
+}
+
+// ---- the persistent form: one launch per substep ------------------------------
+// A cooperative launch (every CTA resident at once) runs the three phases of
+// the substep over all scenes: CTAs take work items (tiles of particles, or
+// of active grid nodes) from a device counter per phase, so that tiles of
+// uneven scenes spread over the SMs, and meet at a grid-wide barrier between
+// the phases.  The barrier's wait is bounded: after kBarrierSpin polls a CTA
+// records ST_TIMEOUT and returns (the others then time out at their next
+// barrier), and the host reports MPM_ETIMEOUT.  The counters are zeroed
+// before each launch.
+struct PersistCtl {
+    unsigned count, gen;   // grid barrier: arrivals, generation
+    unsigned q[3];         // next tile of each phase
+    unsigned pad[3];
+};
+
+constexpr int kBarrierSpin = 1 << 22;   // polls of ~256 ns: ~1 s
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(PersistCtl* c, uint32_t* err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_gpu(&c->gen);
+        __threadfence();
+        if (atomicAdd(&c->count, 1u) == gridDim.x - 1) {
+            atomicExch(&c->count, 0u);
+            __threadfence();
+            atomicAdd(&c->gen, 1u);
+        } else {
+            int it = 0;
+            while (ld_acquire_gpu(&c->gen) == g) {
+                if (++it > kBarrierSpin) {
+                    ok = 0;
+                    atomicOr(err, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The next tile of a phase for this CTA (uniform across the CTA).
+__device__ __forceinline__ int64_t next_tile(unsigned* q)
+{
+    __shared__ unsigned s_t;
+    __syncthreads();   // the previous tile's s_t has been read by every thread
+    if (threadIdx.x == 0)
+        s_t = atomicAdd(q, 1u);
+    __syncthreads();
+    return (int64_t)s_t;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kT, K == 1 ? 7 : 3) bk_persist(BatchView bv, PartView pv, int64_t n,
+                                                               const int32_t* __restrict__ ascene,
+                                                               uint32_t* __restrict__ flags, int words,
+                                                               uint32_t* __restrict__ err, PersistCtl* ctl)
+{
+    // this substep's flag words (cleared here instead of by a memset)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+        flags[i] = 0u;
+    // P2G: tiles of kT chunks of K particles
+    const int64_t chunks = (n + K - 1) / K;
+    for (int64_t t = next_tile(&ctl->q[0]); t * kT < chunks; t = next_tile(&ctl->q[0])) {
+        const int64_t c = t * kT + threadIdx.x;
+        if (c < chunks)
+            bk_p2g_chunk<K>(bv, pv, n, c * K, err);
+    }
+    if (!grid_barrier(ctl, err))
+        return;
+    // grid update: tiles of 8 kT nodes
+    const int64_t nodes = (int64_t)*bv.n_active * 64;
+    for (int64_t t = next_tile(&ctl->q[1]); t * 8 * kT < nodes; t = next_tile(&ctl->q[1])) {
+#pragma unroll 1
+        for (int r = 0; r < 8; ++r) {
+            const int64_t idx = (t * 8 + r) * kT + threadIdx.x;
+            if (idx < nodes)
+                bk_grid_node(bv, ascene, idx);
+        }
+    }
+    if (!grid_barrier(ctl, err))
+        return;
+    // G2P: tiles of kT particles
+    for (int64_t t = next_tile(&ctl->q[2]); t * kT < n; t = next_tile(&ctl->q[2])) {
+        const int64_t p = t * kT + threadIdx.x;
+        if (p < n)
+            bk_g2p_particle(bv, pv, p, flags, err);
+    }
+}
+
 }  // namespace
 }  // namespace mpm
 
@@ -565,6 +741,10 @@ struct mpm_batch {
     bool graphs = false;
     cudaGraphExec_t gexec[mpm::kBatchFlagRing] = {};
     int p2g_k = 4;
+    int cta_warps = 4;            // CTA size of the per-phase P2G and G2P launches (2, 4 or 8 warps)
+    bool persistent = false;      // one cooperative launch per substep instead of one per phase
+    mpm::PersistCtl* ctl = nullptr;
+    int persist_grid[3] = {0, 0, 0};   // CTAs of the cooperative launch, per chunk length 1 / 4 / 8
     int64_t launches = 0, remaps = 0, graph_launches = 0;
     std::string err;
     std::vector<std::pair<void*, size_t>> owned;
@@ -730,23 +910,92 @@ mpm_status build(mpm_batch* b)
     return MPM_OK;
 }
 
-void enqueue_step(mpm_batch* b, int slot)
+template <int T>
+void enqueue_phases(mpm_batch* b, const BatchView& bv, uint32_t* flags, cudaStream_t s)
+{
+    const int64_t n = b->n;
+    const PartView& pv = b->pv[b->cur];
+    if constexpr (T == 256) {
+        if (b->p2g_k == 8)
+            bk_p2g_w8<8><<<nblk((n + 7) / 8, T), T, 0, s>>>(bv, pv, n, b->dstat);
+        else if (b->p2g_k == 1)
+            bk_p2g_w8<1><<<nblk(n, T), T, 0, s>>>(bv, pv, n, b->dstat);
+        else
+            bk_p2g_w8<4><<<nblk((n + 3) / 4, T), T, 0, s>>>(bv, pv, n, b->dstat);
+    } else {
+        if (b->p2g_k == 8)
+            bk_p2g<8, T><<<nblk((n + 7) / 8, T), T, 0, s>>>(bv, pv, n, b->dstat);
+        else if (b->p2g_k == 1)
+            bk_p2g<1, T><<<nblk(n, T), T, 0, s>>>(bv, pv, n, b->dstat);
+        else
+            bk_p2g<4, T><<<nblk((n + 3) / 4, T), T, 0, s>>>(bv, pv, n, b->dstat);
+    }
+    bk_grid<<<152 * 8, 256, 0, s>>>(bv, b->ascene);
+    if constexpr (T == 256)
+        bk_g2p_w8<<<nblk(n, T), T, 0, s>>>(bv, pv, n, flags, b->dstat);
+    else
+        bk_g2p<T><<<nblk(n, T), T, 0, s>>>(bv, pv, n, flags, b->dstat);
+}
+
+// The cooperative launch of the persistent substep: as many CTAs of kT
+// threads as fit on the device at once (all co-resident, as the grid
+// barrier requires).
+template <int K>
+cudaError_t launch_persist(mpm_batch* b, const BatchView& bv, uint32_t* flags, cudaStream_t s)
+{
+    const int ki = K == 1 ? 0 : (K == 4 ? 1 : 2);
+    if (b->persist_grid[ki] == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bk_persist<K>, kT, 0);
+        if (e != cudaSuccess)
+            return e;
+        if (per_sm < 1)
+            return cudaErrorCooperativeLaunchTooLarge;
+        b->persist_grid[ki] = per_sm * sms;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->persist_grid[ki]);
+    cfg.blockDim = dim3(kT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bk_persist<K>, bv, b->pv[b->cur], b->n, (const int32_t*)b->ascene, flags,
+                              b->words, b->dstat, b->ctl);
+}
+
+cudaError_t enqueue_step(mpm_batch* b, int slot)
 {
     cudaStream_t s = b->stream;
     BatchView bv = batch_view(b);
-    cudaMemsetAsync(&b->dstat[1 + slot * b->words], 0, (size_t)b->words * 4, s);
-    int64_t n = b->n;
-    if (b->p2g_k == 8)
-        bk_p2g<8><<<nblk((n + 7) / 8, kT), kT, 0, s>>>(bv, b->pv[b->cur], n, b->dstat);
-    else if (b->p2g_k == 1)
-        bk_p2g<1><<<nblk(n, kT), kT, 0, s>>>(bv, b->pv[b->cur], n, b->dstat);
-    else
-        bk_p2g<4><<<nblk((n + 3) / 4, kT), kT, 0, s>>>(bv, b->pv[b->cur], n, b->dstat);
-    bk_grid<<<152 * 8, 256, 0, s>>>(bv, b->ascene);
-    bk_g2p<<<nblk(n, kT), kT, 0, s>>>(bv, b->pv[b->cur], n, &b->dstat[1 + slot * b->words], b->dstat);
-    cudaMemcpyAsync(&b->hstat[slot * b->words], &b->dstat[1 + slot * b->words], (size_t)b->words * 4,
-                    cudaMemcpyDeviceToHost, s);
-    b->launches += 3;
+    uint32_t* flags = &b->dstat[1 + slot * b->words];
+    cudaError_t e = cudaSuccess;
+    if (b->persistent) {
+        // the kernel clears this substep's flag words itself
+        e = cudaMemsetAsync(b->ctl, 0, sizeof(PersistCtl), s);
+        if (e == cudaSuccess)
+            e = b->p2g_k == 8 ? launch_persist<8>(b, bv, flags, s)
+                              : (b->p2g_k == 1 ? launch_persist<1>(b, bv, flags, s) : launch_persist<4>(b, bv, flags, s));
+        b->launches += 1;
+    } else {
+        e = cudaMemsetAsync(flags, 0, (size_t)b->words * 4, s);
+        if (b->cta_warps == 2)
+            enqueue_phases<64>(b, bv, flags, s);
+        else if (b->cta_warps == 8)
+            enqueue_phases<256>(b, bv, flags, s);
+        else
+            enqueue_phases<kT>(b, bv, flags, s);
+        b->launches += 3;
+    }
+    cudaError_t e2 = cudaMemcpyAsync(&b->hstat[slot * b->words], flags, (size_t)b->words * 4, cudaMemcpyDeviceToHost, s);
+    return e != cudaSuccess ? e : e2;
 }
 
 void drop_graphs(mpm_batch* b)
@@ -969,17 +1218,19 @@ mpm_status mpm_batch_substep(mpm_batch* b, const float* dt)
         cudaGraph_t graph;
         if (!b->gexec[gi]) {
             BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            enqueue_step(b, slot);
-            BCK(cudaStreamEndCapture(b->stream, &graph));
+            const cudaError_t ce = enqueue_step(b, slot);
+            const cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+            BCK(ce);
+            BCK(ee);
             cudaError_t e = cudaGraphInstantiate(&b->gexec[gi], graph, 0);
             cudaGraphDestroy(graph);
             BCK(e);
         }
         BCK(cudaGraphLaunch(b->gexec[gi], b->stream));
         b->graph_launches += 1;
-        b->launches += 3;
+        b->launches += b->persistent ? 1 : 3;
     } else {
-        enqueue_step(b, slot);
+        BCK(enqueue_step(b, slot));
     }
     BCK(cudaEventRecord(b->ev[slot], b->stream));
     BCK(cudaGetLastError());
@@ -999,6 +1250,31 @@ mpm_status mpm_batch_use_graphs(mpm_batch* b, int on)
     if (!on)
         drop_graphs(b);
     b->graphs = on != 0;
+    return MPM_OK;
+}
+
+mpm_status mpm_batch_set_cta_warps(mpm_batch* b, int warps)
+{
+    if (!b || (warps != 2 && warps != 4 && warps != 8))
+        return MPM_EINVAL;
+    if (warps != b->cta_warps)
+        drop_graphs(b);
+    b->cta_warps = warps;
+    return MPM_OK;
+}
+
+mpm_status mpm_batch_set_persistent(mpm_batch* b, int on)
+{
+    if (!b || (on != 0 && on != 1))
+        return MPM_EINVAL;
+    if (on && !b->ctl) {
+        b->ctl = (PersistCtl*)balloc(b, sizeof(PersistCtl));
+        if (!b->ctl)
+            return MPM_ENOMEM;
+    }
+    if ((on != 0) != b->persistent)
+        drop_graphs(b);
+    b->persistent = on != 0;
     return MPM_OK;
 }
 
@@ -1043,6 +1319,10 @@ mpm_status mpm_batch_read_state(mpm_batch* b, int scene, float* x, float* v, flo
     }
     uint32_t errw = 0;
     BCK(cudaMemcpy(&errw, b->dstat, 4, cudaMemcpyDeviceToHost));
+    if (errw & ST_TIMEOUT) {
+        b->err = "a grid-wide barrier of the persistent substep gave up waiting";
+        return MPM_ETIMEOUT;
+    }
     if (errw & ST_ENONFINITE)
         return MPM_ENONFINITE;
     if (errw & (ST_EDOMAIN | ST_MISSED))
@@ -1057,6 +1337,10 @@ mpm_status mpm_batch_sync(mpm_batch* b)
     BCK(cudaStreamSynchronize(b->stream));
     uint32_t errw = 0;
     BCK(cudaMemcpy(&errw, b->dstat, 4, cudaMemcpyDeviceToHost));
+    if (errw & ST_TIMEOUT) {
+        b->err = "a grid-wide barrier of the persistent substep gave up waiting";
+        return MPM_ETIMEOUT;
+    }
     if (errw & ST_ENONFINITE)
         return MPM_ENONFINITE;
     if (errw & (ST_EDOMAIN | ST_MISSED))

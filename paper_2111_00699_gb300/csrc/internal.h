@@ -33,7 +33,10 @@ enum P2GVariant : int {
     P2G_STAGE8 = 6,   // same with 8 particles per thread (1024 per CTA)
     P2G_SACC4 = 7,    // CHUNK4 with the 27 node accumulators in (thread-private) shared memory
     P2G_SLAB4 = 8,    // CHUNK4 split over three threads, one per z-slab of 9 nodes
-    kP2GVariants = 9
+    P2G_WARP = 9,     // thread per particle, lanes grouped by base cell, shuffle-tree reduction per group (Sec. 4.2.2)
+    P2G_WARPRUN = 10, // WARP with groups limited to runs on consecutive lanes (the paper's "no sort" case)
+    P2G_WTILE8 = 11,  // CHUNK8 flushing its runs into a warp-private shared-memory node tile, one reduction per node
+    kP2GVariants = 12
 };
 
 // Particle capacity is a multiple of this, so that a staged tile of
@@ -49,7 +52,8 @@ enum G2PVariant : int {
     G2P_OCC = 4,      // thread per particle capped at 64 registers (occupancy)
     G2P_STAGE = 5,    // OCC with particle inputs and a 2x2x2-block grid tile staged by bulk async copies
     G2P_OCC10 = 6,    // thread per particle capped at 48 registers (10 CTAs of 128 per SM)
-    kG2PVariants = 7
+    G2P_OCCSW = 7,    // OCC with the B-spline weights in shared memory (the paper's weight spilling)
+    kG2PVariants = 8
 };
 
 // Device status word bits.
@@ -81,16 +85,42 @@ struct SimParams {
     int transfer;            // MPM_APIC or MPM_ASFLIP
     float flip_alpha, flip_beta_min, flip_beta_max, flip_margin;
     int n_mats;
+    int cta_warps;           // warps per CTA of the register-run P2G and the 64-register G2P: 2, 4 or 8
     MatParams mat[kMaxMaterials];
 };
 
+// The particle store: kChannels x cap floats in one of two layouts.
+//  - SoA (aosoa = 0): one array of cap floats per channel; channel c of
+//    particle p at c * cap + p.
+//  - AoSoA (aosoa = 1): packets of 32 particles, each packet holding its 32
+//    floats of channel 0, then of channel 1, ...; channel c of particle p at
+//    ((p / 32) * kChannels + c) * 32 + p % 32.  A warp's 32 consecutive
+//    particles then read one 128-byte line per channel as in SoA, but all
+//    their channels lie in one 4 KB span (the paper's AoSoA, Sec. 6.2).
+// ch() is the SoA channel pointer (SoA only); at() serves both layouts.
 struct PartView {
     float* soa;     // kChannels x cap floats
-    int64_t cap;
+    int64_t cap;    // a multiple of kCapQuantum (so of 32)
     uint8_t* mat;
     int32_t* id;
+    int aosoa;
     __host__ __device__ float* ch(int c) const { return soa + (int64_t)c * cap; }
+    __host__ __device__ int64_t idx(int c, int64_t p) const
+    {
+        return aosoa ? (((p >> 5) * kChannels + c) << 5) + (p & 31) : (int64_t)c * cap + p;
+    }
+    __host__ __device__ float& at(int c, int64_t p) const { return soa[idx(c, p)]; }
 };
+
+// Channel c of particle p with the layout fixed at compile time (the
+// kernels instantiated per layout).
+template <bool kAoS>
+__device__ __forceinline__ float& pch(const PartView& pv, int c, int64_t p)
+{
+    if (kAoS)
+        return pv.soa[(((p >> 5) * kChannels + c) << 5) + (p & 31)];
+    return pv.soa[(int64_t)c * pv.cap + p];
+}
 
 struct GridView {
     float4* cur;          // (p or v, m) per node, 64 nodes per physical block
@@ -129,6 +159,7 @@ void launch_mark_pblocks(const uint32_t* skeys, int64_t n, int L, int32_t* flags
 void launch_build_table(const int32_t* flags, const int32_t* ranks, int64_t n_slots, int32_t* table,
                         int32_t* pslot, int32_t* n_pblocks, cudaStream_t s);
 void launch_permute(const PartView& src, const PartView& dst, const int32_t* perm, int64_t n, cudaStream_t s);
+void launch_relayout(const PartView& src, const PartView& dst, int64_t n, cudaStream_t s);
 constexpr int kResortWindow = 1024;
 void launch_resort_window(const SimParams& sp, const PartView& src, const PartView& dst, int64_t n, cudaStream_t s);
 void launch_interior(const SimParams& sp, const int32_t* table, const int32_t* pslot, int32_t n_pblocks,
@@ -142,7 +173,7 @@ void launch_grid_to_dense(const SimParams& sp, const float4* grid, const int32_t
 // *word (zeroed by the caller) <- max over particles of |v|^2, as float bits
 void launch_max_speed2(const PartView& pv, int64_t n, uint32_t* word, cudaStream_t s);
 
-// substep.cu
+// p2g.cu, g2p.cu, g2p2g.cu
 void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                 uint32_t* err, int variant, cudaStream_t s);
 void launch_prepare_stress(const SimParams& sp, const PartView& pv, int64_t n, cudaStream_t s);

@@ -30,7 +30,7 @@ __device__ __forceinline__ uint32_t particle_key(const SimParams& sp, const Part
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float x = pv.ch(CH_X + a)[p];
+        float x = pv.at(CH_X + a, p);
         b[a] = base_of(x, sp.inv_dx);
         ok = ok && isfinite(x) && b[a] >= 0 && b[a] + 2 < sp.res[a] && (b[a] >> 2) < (1 << sp.L);
     }
@@ -116,13 +116,13 @@ __global__ void __launch_bounds__(kResortThreads) k_resort_window(SimParams sp, 
         for (int c = 0; c < 8; ++c)
 #pragma unroll
             for (int k = 0; k < kPer; ++k)
-                v[c][k] = src_i[k] >= 0 ? src.ch(c0 + c)[p0 + src_i[k]] : 0.0f;
+                v[c][k] = src_i[k] >= 0 ? src.at(c0 + c, p0 + src_i[k]) : 0.0f;
 #pragma unroll
         for (int c = 0; c < 8; ++c)
 #pragma unroll
             for (int k = 0; k < kPer; ++k)
                 if (src_i[k] >= 0)
-                    dst.ch(c0 + c)[p0 + tid + k * kResortThreads] = v[c][k];
+                    dst.at(c0 + c, p0 + tid + k * kResortThreads) = v[c][k];
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -209,9 +209,22 @@ __global__ void k_permute(PartView src, PartView dst, const int32_t* __restrict_
     int64_t j = perm[i];
 #pragma unroll 2
     for (int c = 0; c < kChannels; ++c)
-        dst.ch(c)[i] = src.ch(c)[j];
+        dst.at(c, i) = src.at(c, j);
     dst.mat[i] = src.mat[j];
     dst.id[i] = src.id[j];
+}
+
+// The same particles in another store layout (src and dst differ in aosoa).
+__global__ void k_relayout(PartView src, PartView dst, int64_t n)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+#pragma unroll 4
+    for (int c = 0; c < kChannels; ++c)
+        dst.at(c, i) = src.at(c, i);
+    dst.mat[i] = src.mat[i];
+    dst.id[i] = src.id[i];
 }
 
 __global__ void k_append(PartView pv, int64_t n0, int64_t n, const float* __restrict__ x,
@@ -223,19 +236,19 @@ __global__ void k_append(PartView pv, int64_t n0, int64_t n, const float* __rest
     int64_t p = n0 + i;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        pv.ch(CH_X + a)[p] = x[3 * i + a];
-        pv.ch(CH_V + a)[p] = v ? v[3 * i + a] : 0.0f;
+        pv.at(CH_X + a, p) = x[3 * i + a];
+        pv.at(CH_V + a, p) = v ? v[3 * i + a] : 0.0f;
     }
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-        pv.ch(CH_C + e)[p] = 0.0f;
-        pv.ch(CH_F + e)[p] = 0.0f;   // F - I
+        pv.at(CH_C + e, p) = 0.0f;
+        pv.at(CH_F + e, p) = 0.0f;   // F - I
     }
-    pv.ch(CH_JP)[p] = 0.0f;          // Jp - 1 (J - 1 for fluids)
-    pv.ch(CH_VOL)[p] = vol ? vol[i] : default_vol;
+    pv.at(CH_JP, p) = 0.0f;          // Jp - 1 (J - 1 for fluids)
+    pv.at(CH_VOL, p) = vol ? vol[i] : default_vol;
 #pragma unroll
     for (int e = 0; e < 6; ++e)
-        pv.ch(CH_TAU + e)[p] = 0.0f;   // stress of F = I, Jp = J = 1 is zero for every model
+        pv.at(CH_TAU + e, p) = 0.0f;   // stress of F = I, Jp = J = 1 is zero for every model
     pv.mat[p] = (uint8_t)material;
     pv.id[p] = (int32_t)p;
 }
@@ -256,7 +269,7 @@ __global__ void k_gather_out(PartView pv, int64_t n, int first, int width, int b
         return;
     int64_t q = pv.id[i];
     for (int e = 0; e < width; ++e)
-        out[q * width + e] = pv.ch(first + e)[i] + unit_bias(e, bias_step);
+        out[q * width + e] = pv.at(first + e, i) + unit_bias(e, bias_step);
 }
 
 __global__ void k_scatter_in(PartView pv, int64_t n, int first, int width, int bias_step, const float* __restrict__ in)
@@ -266,7 +279,7 @@ __global__ void k_scatter_in(PartView pv, int64_t n, int first, int width, int b
         return;
     int64_t q = pv.id[i];
     for (int e = 0; e < width; ++e)
-        pv.ch(first + e)[i] = in[q * width + e] - unit_bias(e, bias_step);
+        pv.at(first + e, i) = in[q * width + e] - unit_bias(e, bias_step);
 }
 
 __global__ void k_grid_to_dense(SimParams sp, const float4* __restrict__ grid, const int32_t* __restrict__ pslot,
@@ -309,6 +322,12 @@ void launch_build_table(const int32_t* flags, const int32_t* ranks, int64_t n_sl
                         int32_t* pslot, int32_t* n_pblocks, cudaStream_t s)
 {
     k_table<<<blocks_for(n_slots), kBlock, 0, s>>>(flags, ranks, n_slots, table, pslot, n_pblocks);
+}
+
+void launch_relayout(const PartView& src, const PartView& dst, int64_t n, cudaStream_t s)
+{
+    if (n > 0)
+        k_relayout<<<blocks_for(n), kBlock, 0, s>>>(src, dst, n);
 }
 
 void launch_permute(const PartView& src, const PartView& dst, const int32_t* perm, int64_t n, cudaStream_t s)
@@ -384,7 +403,7 @@ __global__ void k_max_speed2(PartView pv, int64_t n, uint32_t* __restrict__ word
 {
     uint32_t best = 0u;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const float a = pv.ch(CH_V)[p], b = pv.ch(CH_V + 1)[p], c = pv.ch(CH_V + 2)[p];
+        const float a = pv.at(CH_V, p), b = pv.at(CH_V + 1, p), c = pv.at(CH_V + 2, p);
         best = max(best, __float_as_uint(a * a + b * b + c * c));
     }
     const unsigned m = __reduce_max_sync(0xffffffffu, best);

@@ -241,6 +241,14 @@ class Simulator:
     def set_p2g_variant(self, variant: int):
         _check(load().mpm_set_p2g_variant(self._ctx, int(variant)), self._ctx)
 
+    def set_cta_warps(self, warps: int):
+        """Warps per CTA (2, 4 or 8) of the register-run P2G and the 64-register G2P."""
+        _check(load().mpm_set_cta_warps(self._ctx, int(warps)), self._ctx)
+
+    def set_layout(self, aosoa: bool):
+        """Particle store layout: False SoA (default), True AoSoA in packets of 32."""
+        _check(load().mpm_set_layout(self._ctx, 1 if aosoa else 0), self._ctx)
+
     def set_g2p2g(self, on: bool):
         _check(load().mpm_set_g2p2g(self._ctx, 1 if on else 0), self._ctx)
 
@@ -360,6 +368,14 @@ class BatchSimulator:
 
     def set_p2g_chunk(self, k: int):
         self._err(load().mpm_batch_set_p2g_chunk(self._b, int(k)))
+
+    def set_cta_warps(self, warps: int):
+        """Warps per CTA (2, 4 or 8) of the per-phase P2G and G2P launches."""
+        self._err(load().mpm_batch_set_cta_warps(self._b, int(warps)))
+
+    def set_persistent(self, on: bool = True):
+        """One cooperative launch per substep (grid barriers between the phases)."""
+        self._err(load().mpm_batch_set_persistent(self._b, 1 if on else 0))
 
     def sync(self):
         self._err(load().mpm_batch_sync(self._b))

@@ -59,3 +59,24 @@ def tune_p2g(sim, dt: float, steps: int = 50, rounds: int = 2, refine_top: int =
 def tune_g2p(sim, dt: float, steps: int = 50, rounds: int = 2) -> dict:
     """Same for the G2P gather variants."""
     return _tune(sim, dt, _lib.G2P_VARIANTS, sim.set_g2p_variant, "g2p", steps, rounds)
+
+
+def tune_cta_warps(sim, dt: float, steps: int = 50, rounds: int = 2) -> dict:
+    """Time P2G + G2P per substep in CTAs of 2, 4 and 8 warps (the register-run
+    P2G and the 64-register G2P take the setting) and keep the fastest.
+    Returns {"best": warps, "ms": {warps: ms of P2G + G2P per substep}}."""
+    ms = {w: float("inf") for w in (2, 4, 8)}
+    sim.profile_enable(True)
+    for _ in range(rounds):
+        for w in ms:
+            sim.set_cta_warps(w)
+            sim.run(2, dt)
+            sim.profile_read()
+            sim.run(steps, dt)
+            ph = sim.profile_read()
+            t = sum(ph[k][0] for k in ("p2g", "g2p")) / max(1, ph["p2g"][1])
+            ms[w] = min(ms[w], t)
+    sim.profile_enable(False)
+    best = min(ms, key=ms.get)
+    sim.set_cta_warps(best)
+    return {"best": best, "ms": ms}

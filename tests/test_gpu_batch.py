@@ -48,23 +48,32 @@ def _batch_case(n_scenes=8, seed=40, n_max=6000, v_scale=0.3):
     return bs, vs
 
 
-def _run_batch(M, bs, vs, steps, graphs, chunk=4):
+def _run_batch(M, bs, vs, steps, graphs, chunk=4, persistent=False, warps=4):
     gm, _ = _mats(M)
     descs = [dict(res=b["res"], dx=1.0 / b["res"], material=b["material"]) for b in bs]
     dts = np.array([DT[b["material"]] for b in bs], np.float32)
     with M.BatchSimulator(descs, gm, graphs=graphs, p2g_chunk=chunk) as bsim:
         for i, (b, v) in enumerate(zip(bs, vs)):
             bsim.add_particles(i, b["x"], v)
+        bsim.set_persistent(persistent)
+        bsim.set_cta_warps(warps)
         bsim.run(steps, dts)
         out = [bsim.read_state(i) for i in range(len(bs))]
         st = bsim.stats()
     return out, st, dts
 
 
-@pytest.mark.parametrize("graphs,chunk", [(False, 4), (True, 4), (True, 1), (True, 8)])
-def test_batched_scenes_match_oracle(M, graphs, chunk):
+@pytest.mark.parametrize("graphs,chunk,persistent,warps", [(False, 4, False, 4), (True, 4, False, 4),
+                                                            (True, 1, False, 4), (True, 8, False, 4),
+                                                            (True, 4, False, 2), (True, 8, False, 8),
+                                                            (False, 4, True, 4), (True, 1, True, 4),
+                                                            (True, 4, True, 4), (True, 8, True, 4)])
+def test_batched_scenes_match_oracle(M, graphs, chunk, persistent, warps):
+    """Per-phase launches in CTAs of 2, 4 or 8 warps, and the persistent form
+    (one cooperative launch per substep with grid barriers), each with P2G
+    register runs of 1, 4 or 8 particles."""
     bs, vs = _batch_case()
-    out, st, dts = _run_batch(M, bs, vs, 10, graphs, chunk)
+    out, st, dts = _run_batch(M, bs, vs, 10, graphs, chunk, persistent, warps)
     _, om = _mats(M)
     assert st["substeps"] == 10
     if graphs:
@@ -77,7 +86,8 @@ def test_batched_scenes_match_oracle(M, graphs, chunk):
         assert np.abs(g["Jp"] - s.Jp).max() <= 1e-4, i
 
 
-def test_batched_per_scene_remap(M):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batched_per_scene_remap(M, persistent):
     """One fast scene must remap repeatedly while a resting scene does not,
     and both must keep parity."""
     gm, om = _mats(M)
@@ -89,6 +99,7 @@ def test_batched_per_scene_remap(M):
     with M.BatchSimulator(descs, gm) as bsim:
         bsim.add_particles(0, xa, va)
         bsim.add_particles(1, xb, vb)
+        bsim.set_persistent(persistent)
         bsim.run(60, 1e-4)
         ga, gb = bsim.read_state(0), bsim.read_state(1)
         st = bsim.stats()
@@ -110,15 +121,17 @@ def test_batched_rejects_bad_input(M):
         assert e.value.status == 4
 
 
-def test_batched_full_size_sampled_scenes(M):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batched_full_size_sampled_scenes(M, persistent):
     """The full batched workload as bench.py times it (256 scenes, 4.8M
-    particles, seed 4, CUDA graphs, P2G runs of 8), 10 substeps from rest;
-    two scenes per material (the smallest and the largest) are compared with
-    the oracle run on that scene alone."""
+    particles, seed 4, CUDA graphs, P2G runs of 8), 10 substeps from rest,
+    per-phase launches or the persistent launch; two scenes per material
+    (the smallest and the largest) are compared with the oracle run on that
+    scene alone."""
     bs = scenes.batched_scenes(4)
     assert len(bs) == 256
     vs = [np.zeros((len(b["x"]), 3), np.float32) for b in bs]
-    out, st, dts = _run_batch(M, bs, vs, 10, True, 8)
+    out, st, dts = _run_batch(M, bs, vs, 10, True, 8, persistent)
     assert st["graph_launches"] == 10
     _, om = _mats(M)
     picks = []
