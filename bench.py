@@ -621,20 +621,21 @@ def _variant_name(kind, v):
 
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
-                        "chunk4": "k_p2g_chunk<4, false>", "chunk8": "k_p2g_chunk<8, false>", "stage4": "k_p2g_stage<4>",
-                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, true>", "slab4": "k_p2g_slab<4>",
-                        "warp": "k_p2g_warp<true>", "warprun": "k_p2g_warp<false>", "wtile8": "k_p2g_wtile<8>"},
+                        "chunk4": "k_p2g_chunk<4, 0, 0>", "chunk8": "k_p2g_chunk<8, 0, 0>", "stage4": "k_p2g_stage<4>",
+                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, 1, 0>", "slab4": "k_p2g_slab<4>",
+                        "warp": "k_p2g_warp<1>", "warprun": "k_p2g_warp<0>", "wtile8": "k_p2g_wtile<8>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
-                        # the bench scene has one material (snow, kind 2): the kernel specialised to it
-                        "occ": "k_g2p_occ<8, 2, 128, false>", "stage": "k_g2p_stage",
-                        "occ10": "k_g2p_occ<10, -1, 128, false>", "occsw": "k_g2p_occ<8, 2, 128, true>"}}
+                        # the bench scene has one material (snow, kind 2): the kernels specialised to it
+                        "occ": "k_g2p_occ<8, 2, 128, 0, 0>", "stage": "k_g2p_stage",
+                        "occ10": "k_g2p_occ<10, -1, 128, 0, 0>", "occsw": "k_g2p_occ<8, 2, 128, 1, 0>"}}
+# (names as ncu prints them: template booleans as 0 / 1)
 
 
 FUSED_SCATTER_VARIANTS = (0, 3, 4, 7, 9, 10)
-FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chunk<4, false>",
-                      4: "k_g2p2g_chunk<8, false>", 5: "k_g2p2g_chunk<4, false>", 6: "k_g2p2g_chunk<8, false>",
-                      7: "k_g2p2g_chunk<4, true>", 8: "k_g2p2g", 9: "k_g2p2g_warp<true>", 10: "k_g2p2g_warp<false>",
-                      11: "k_g2p2g_chunk<8, false>"}
+FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chunk<4, 0>",
+                      4: "k_g2p2g_chunk<8, 0>", 5: "k_g2p2g_chunk<4, 0>", 6: "k_g2p2g_chunk<8, 0>",
+                      7: "k_g2p2g_chunk<4, 1>", 8: "k_g2p2g", 9: "k_g2p2g_warp<1>", 10: "k_g2p2g_warp<0>",
+                      11: "k_g2p2g_chunk<8, 0>"}
 
 
 KERNEL_SOURCES = ("transfer.cuh", "p2g.cu", "g2p.cu", "g2p2g.cu", "device_math.cuh", "async_copy.cuh", "internal.h")
@@ -695,6 +696,10 @@ def main():
     ap.add_argument("--profile-substeps", type=int, default=0,
                     help="profiler mode: run this many substeps of the snow scene with the given variants "
                          "(default chunk4 P2G, occ G2P), print one status line and exit; no timing")
+    ap.add_argument("--aosoa", type=int, default=0, choices=[0, 1],
+                    help="profiler mode: 1 = AoSoA particle store (P2G variant 3/4, G2P 4/7)")
+    ap.add_argument("--cta-warps", type=int, default=4, choices=[2, 4, 8],
+                    help="profiler mode: warps per CTA of the register-run P2G and the 64-register G2P")
     ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
                     help="1: fused G2P2G transfer, 0: separate phases; default: the faster one")
     args = ap.parse_args()
@@ -745,11 +750,14 @@ def main():
         gv = args.g2p_variant if args.g2p_variant >= 0 else 4
         sim = fresh_sim(pv, gv)
         sim.set_g2p2g(bool(args.g2p2g))
+        sim.set_cta_warps(args.cta_warps)
+        sim.set_layout(bool(args.aosoa))
         sim.run(args.profile_substeps, DT)
         sim.sync()
         if rank == 0:
             print(json.dumps({"profile_substeps": args.profile_substeps, "p2g_variant": _variant_name("P2G", pv),
                               "g2p_variant": _variant_name("G2P", gv), "g2p2g": bool(args.g2p2g),
+                              "aosoa": bool(args.aosoa), "cta_warps": args.cta_warps,
                               "stats": sim.stats()}))
         sim.close()
         return
@@ -776,19 +784,25 @@ def main():
         warm -= 120
     else:
         sim.set_g2p_variant(args.g2p_variant)
-    # warps per CTA of the register-run P2G and the 64-register G2P
+    # warps per CTA of the register-run P2G and the 64-register G2P, then the particle store layout
     tuned_w = tune.tune_cta_warps(sim, DT, steps=20, rounds=2)  # advances 132 substeps
     warm -= 132
+    tuned_l = tune.tune_layout(sim, DT, tuned_w["best"], steps=20, rounds=2)   # advances 88 substeps
+    warm -= 88
     # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene;
     # the fused kernel's scatter follows the P2G variant (direct, chunk4, chunk8)
     fused_ms, fused_scatter_ms = {}, {}
     p2g_separate = tuned["best"] if tuned["best"] >= 0 else 3
+    aosoa = tuned_l["best"] == "aosoa"
     for _ in range(2):
         sim.set_g2p2g(False)
         sim.set_p2g_variant(p2g_separate)
+        sim.set_layout(aosoa)
+        sim.set_cta_warps(tuned_l["cta_warps"])
         sim.run(3, DT)
         fused_ms.setdefault("separate", []).append(_events_time(stream, lambda: sim.run(20, DT)) / 20)
         warm -= 23
+        sim.set_layout(False)   # the fused kernels run on the SoA store
         for v in FUSED_SCATTER_VARIANTS:
             sim.set_p2g_variant(v)
             sim.set_g2p2g(True)
@@ -803,6 +817,9 @@ def main():
     p2g_final = fused_best if use_fused else p2g_separate
     sim.set_g2p2g(bool(use_fused))
     sim.set_p2g_variant(p2g_final)
+    if not use_fused:
+        sim.set_layout(aosoa)
+        sim.set_cta_warps(tuned_l["cta_warps"])
     warm = max(3, warm)
     sim.run(warm, DT)
     sim.sync()
@@ -860,6 +877,14 @@ def main():
                    "g2p": (FUSED_KERNEL_NAMES[p2g_final] if use_fused
                            else KERNEL_NAMES["G2P"][tuned_g["best_name"]]),
                    "grid": "k_grid"}[dom]
+    if aosoa and not use_fused and kernel_name.endswith(" 0>"):
+        kernel_name = kernel_name[:-len(" 0>")] + " 1>"   # the AoSoA instantiation
+    w = tuned_l["cta_warps"]
+    if not use_fused and w != 4:   # the instantiations for CTAs of 2 or 8 warps
+        if kernel_name.startswith("k_p2g_chunk<") and kernel_name.endswith(", 0, 0>"):
+            kernel_name = "k_p2g_chunk_w%d<%s>" % (w, kernel_name[len("k_p2g_chunk<"):].split(",")[0])
+        elif kernel_name.startswith("k_g2p_occ<8, "):
+            kernel_name = kernel_name.replace(", 128, ", ", %d, " % (32 * w))
     # the same kernel on the layout-free byte count (P2G: x, v, C, F, Jp = 100 B per particle)
     survey_bytes = {"p2g": SURVEY_BYTES_P2G * n_now}.get(dom)
     achieved_survey = survey_bytes / (avg[dom] / 1e3) / 1e9 if (survey_bytes and avg[dom] > 0) else None
@@ -889,7 +914,9 @@ def main():
     if args.e2e_frames > 0:
         sim = fresh_sim(p2g_final, tuned_g["best"])
         sim.set_g2p2g(bool(use_fused))
-        sim.set_cta_warps(tuned_w["best"])
+        if not use_fused:
+            sim.set_cta_warps(tuned_l["cta_warps"])
+            sim.set_layout(aosoa)
         host = {k: torch.empty(s, dtype=torch.float32).pin_memory()
                 for k, s in (("x", (n, 3)), ("v", (n, 3)), ("C", (n, 9)), ("F", (n, 9)), ("Jp", (n,)))}
         sim.read_state_into(x=host["x"], v=host["v"], C=host["C"].view(n, 3, 3), F=host["F"].view(n, 3, 3),
@@ -937,7 +964,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": workload_config(n, world),
             "clocks": dict(clk.summary(), window="autotuning, warm-up and timed substeps"),
-            "p2g_variant": tuned, "g2p_variant": tuned_g, "cta_warps": tuned_w,
+            "p2g_variant": tuned, "g2p_variant": tuned_g, "cta_warps": tuned_w, "layout": tuned_l,
             "transfer": {"mode": "g2p2g" if use_fused else "separate", "ms_per_substep": fused_ms,
                          "g2p2g_scatter_ms": fused_scatter_ms, "p2g_variant_used": _variant_name("P2G", p2g_final)}, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu, "workloads": workloads}

@@ -214,7 +214,10 @@ mpm_status realloc_buf(mpm_ctx* ctx, T*& p, size_t& have, size_t want)
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-size_t part_bytes(int64_t cap) { return (size_t)cap * (kChannels * 4 + 1 + 4) + 512; }
+// The float store sized for either layout (AoSoA packets carry one unused
+// line each), then the ids and the material bytes.
+size_t store_bytes(int64_t cap) { return (size_t)(cap / 32) * kPacketFloats * 4; }
+size_t part_bytes(int64_t cap) { return store_bytes(cap) + (size_t)cap * (1 + 4) + 512; }
 
 PartView make_view(void* base, int64_t cap, int aosoa)
 {
@@ -222,7 +225,7 @@ PartView make_view(void* base, int64_t cap, int aosoa)
     v.soa = (float*)base;
     v.cap = cap;
     v.aosoa = aosoa;
-    char* p = (char*)base + (size_t)cap * kChannels * 4;
+    char* p = (char*)base + store_bytes(cap);
     v.id = (int32_t*)p;
     v.mat = (uint8_t*)(p + (size_t)cap * 4);
     return v;
@@ -311,7 +314,7 @@ mpm_status ensure_particle_capacity(mpm_ctx* ctx, int64_t need)
     if (ctx->n > 0) {
         const PartView& ov = ctx->pv[ctx->cur];
         if (ctx->aosoa)   // whole packets: their layout does not depend on the capacity
-            CK(cudaMemcpyAsync(nv.soa, ov.soa, (size_t)((ctx->n + 31) / 32) * 32 * kChannels * 4,
+            CK(cudaMemcpyAsync(nv.soa, ov.soa, (size_t)((ctx->n + 31) / 32) * kPacketFloats * 4,
                                cudaMemcpyDeviceToDevice, ctx->stream));
         else
             for (int c = 0; c < kChannels; ++c)
@@ -1264,10 +1267,11 @@ mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa)
     if (aosoa == ctx->aosoa)
         return MPM_OK;
     if (aosoa && ((ctx->cfg.p2g_variant != P2G_CHUNK4 && ctx->cfg.p2g_variant != P2G_CHUNK8) ||
-                  ctx->cfg.g2p_variant != G2P_OCC || ctx->cfg.use_g2p2g || ctx->cfg.transfer != MPM_APIC ||
+                  (ctx->cfg.g2p_variant != G2P_OCC && ctx->cfg.g2p_variant != G2P_OCCSW) || ctx->cfg.use_g2p2g ||
+                  ctx->cfg.transfer != MPM_APIC ||
                   ctx->sp.cta_warps != 4))
         return fail(ctx, MPM_EINVAL,
-                    "mpm_set_layout: AoSoA needs P2G variant 3 or 4, G2P variant 4, separate APIC transfers and "
+                    "mpm_set_layout: AoSoA needs P2G variant 3 or 4, G2P variant 4 or 7, separate APIC transfers and "
                     "4 warps per CTA");
     // convert the current particles into the other buffer, then make it current
     PartView dst = ctx->pv[1 - ctx->cur];
@@ -1323,8 +1327,8 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant)
 {
     if (!ctx || variant < 0 || variant >= kG2PVariants)
         return MPM_EINVAL;
-    if (ctx->aosoa && variant != G2P_OCC)
-        return fail(ctx, MPM_EINVAL, "mpm_set_g2p_variant: the AoSoA layout has G2P variant 4 only");
+    if (ctx->aosoa && variant != G2P_OCC && variant != G2P_OCCSW)
+        return fail(ctx, MPM_EINVAL, "mpm_set_g2p_variant: the AoSoA layout has G2P variants 4 and 7 only");
     ctx->cfg.g2p_variant = variant;
     drop_graphs(ctx);
     return MPM_OK;

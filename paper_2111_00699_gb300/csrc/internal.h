@@ -93,21 +93,26 @@ struct SimParams {
 //  - SoA (aosoa = 0): one array of cap floats per channel; channel c of
 //    particle p at c * cap + p.
 //  - AoSoA (aosoa = 1): packets of 32 particles, each packet holding its 32
-//    floats of channel 0, then of channel 1, ...; channel c of particle p at
-//    ((p / 32) * kChannels + c) * 32 + p % 32.  A warp's 32 consecutive
-//    particles then read one 128-byte line per channel as in SoA, but all
-//    their channels lie in one 4 KB span (the paper's AoSoA, Sec. 6.2).
+//    floats of channel 0, then of channel 1, ..., then 32 unused floats;
+//    channel c of particle p at (p / 32) * kPacketFloats + 32 c + p % 32.  A
+//    warp's 32 consecutive particles then read one 128-byte line per
+//    channel as in SoA, but all their channels lie in one 4 KB span (the
+//    paper's AoSoA, Sec. 6.2).  The unused line makes consecutive packets
+//    4224 bytes apart, so that the same channel of neighbouring packets does
+//    not fall into one L1 set (4 KB strides alias).
 // ch() is the SoA channel pointer (SoA only); at() serves both layouts.
+constexpr int kPacketFloats = 32 * kChannels + 32;
+
 struct PartView {
-    float* soa;     // kChannels x cap floats
+    float* soa;     // the store: (cap / 32) * kPacketFloats floats (SoA uses the first kChannels * cap)
     int64_t cap;    // a multiple of kCapQuantum (so of 32)
     uint8_t* mat;
     int32_t* id;
-    int aosoa;
+    int aosoa = 0;
     __host__ __device__ float* ch(int c) const { return soa + (int64_t)c * cap; }
     __host__ __device__ int64_t idx(int c, int64_t p) const
     {
-        return aosoa ? (((p >> 5) * kChannels + c) << 5) + (p & 31) : (int64_t)c * cap + p;
+        return aosoa ? (p >> 5) * kPacketFloats + 32 * c + (p & 31) : (int64_t)c * cap + p;
     }
     __host__ __device__ float& at(int c, int64_t p) const { return soa[idx(c, p)]; }
 };
@@ -118,7 +123,7 @@ template <bool kAoS>
 __device__ __forceinline__ float& pch(const PartView& pv, int c, int64_t p)
 {
     if (kAoS)
-        return pv.soa[(((p >> 5) * kChannels + c) << 5) + (p & 31)];
+        return pv.soa[(p >> 5) * kPacketFloats + 32 * c + (p & 31)];
     return pv.soa[(int64_t)c * pv.cap + p];
 }
 

@@ -80,3 +80,40 @@ def tune_cta_warps(sim, dt: float, steps: int = 50, rounds: int = 2) -> dict:
     best = min(ms, key=ms.get)
     sim.set_cta_warps(best)
     return {"best": best, "ms": ms}
+
+
+def _p2g_g2p_ms(sim, dt, steps):
+    sim.run(2, dt)
+    sim.profile_read()
+    sim.run(steps, dt)
+    ph = sim.profile_read()
+    return sum(ph[k][0] for k in ("p2g", "g2p")) / max(1, ph["p2g"][1])
+
+
+def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) -> dict:
+    """SoA (at `warps` warps per CTA) against the AoSoA store (which runs 4
+    warps per CTA), timing P2G + G2P per substep; keeps the faster.  Needs
+    the register-run P2G (variant 3 or 4) and the 64-register G2P (4 or 7)
+    already selected; otherwise the store stays SoA.  Returns {"best":
+    "soa" | "aosoa", "ms": {...}, "cta_warps": the warps kept}."""
+    ms = {"soa": float("inf"), "aosoa": float("inf")}
+    sim.profile_enable(True)
+    try:
+        for _ in range(rounds):
+            sim.set_layout(False)
+            sim.set_cta_warps(warps)
+            ms["soa"] = min(ms["soa"], _p2g_g2p_ms(sim, dt, steps))
+            sim.set_cta_warps(4)
+            sim.set_layout(True)
+            ms["aosoa"] = min(ms["aosoa"], _p2g_g2p_ms(sim, dt, steps))
+    except Exception as exc:   # the selected variants have no AoSoA form
+        sim.profile_enable(False)
+        sim.set_layout(False)
+        sim.set_cta_warps(warps)
+        return {"best": "soa", "ms": ms, "cta_warps": warps, "skipped": str(exc)}
+    sim.profile_enable(False)
+    best = min(ms, key=ms.get)
+    if best == "soa":
+        sim.set_layout(False)
+        sim.set_cta_warps(warps)
+    return {"best": best, "ms": ms, "cta_warps": warps if best == "soa" else 4}
