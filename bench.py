@@ -235,24 +235,27 @@ def bench_batched(steps=100, warmup=5):
     shapes = [(False, k, w) for k in (1, 4, 8) for w in (2, 4, 8)] + [(True, k, 4) for k in (1, 4, 8)]
     name = lambda sh: "%s chunk %d%s" % ("persistent" if sh[0] else "per-phase", sh[1],
                                           "" if sh[0] else ", %d warps" % sh[2])
-    with mpm.BatchSimulator(descs, mats, graphs=True) as bsim:
+
+    def fresh(sh):
+        bsim = mpm.BatchSimulator(descs, mats, graphs=True)
         for i, b in enumerate(bs):
             bsim.add_particles(i, b["x"])
+        bsim.set_persistent(sh[0])
+        bsim.set_p2g_chunk(sh[1])
+        bsim.set_cta_warps(sh[2])
         bsim.run(warmup, dts)
-        tune = {}
-        for rnd in range(2):
-            for sh in shapes:
-                bsim.set_persistent(sh[0])
-                bsim.set_p2g_chunk(sh[1])
-                bsim.set_cta_warps(sh[2])
-                bsim.run(2, dts)
-                t = _events_time(bsim.stream, lambda: bsim.run(10, dts)) / 10
-                tune[sh] = min(tune.get(sh, float("inf")), t)
-        best = min(tune, key=tune.get)
-        bsim.set_persistent(best[0])
-        bsim.set_p2g_chunk(best[1])
-        bsim.set_cta_warps(best[2])
-        bsim.run(8, dts)   # re-captures the graphs of every flag-ring slot before the timed run
+        return bsim
+
+    # each shape on a fresh batch, over the same substeps of the scenes' motion (from rest):
+    # the cost of a substep changes as the blocks land and deform
+    tune = {}
+    for sh in shapes:
+        with fresh(sh) as bsim:
+            tune[sh] = _events_time(bsim.stream, lambda: bsim.run(20, dts)) / 20
+    best = min(tune, key=tune.get)
+    # the timed run: a fresh batch in the chosen shape, covering the same substeps as the
+    # per-scene run below
+    with fresh(best) as bsim:
         ms = _events_time(bsim.stream, lambda: bsim.run(steps, dts))
         bsim.sync()
         st = bsim.stats()
@@ -623,7 +626,8 @@ def _variant_name(kind, v):
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
                         "chunk4": "k_p2g_chunk<4, 0, 0>", "chunk8": "k_p2g_chunk<8, 0, 0>", "stage4": "k_p2g_stage<4>",
                         "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, 1, 0>", "slab4": "k_p2g_slab<4>",
-                        "warp": "k_p2g_warp<1>", "warprun": "k_p2g_warp<0>", "wtile8": "k_p2g_wtile<8>"},
+                        "warp": "k_p2g_warp<1>", "warprun": "k_p2g_warp<0>", "wtile8": "k_p2g_wtile<8>",
+                        "wxpose": "k_p2g_wxpose"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         # the bench scene has one material (snow, kind 2): the kernels specialised to it
                         "occ": "k_g2p_occ<8, 2, 128, 0, 0>", "stage": "k_g2p_stage",
@@ -689,7 +693,7 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8); -1 = autotune")
+                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10, "
                          "7 occsw); -1 = autotune")

@@ -112,8 +112,10 @@ typedef struct {
                               reduction per group and node), 10 the same over runs of equal
                               cells on consecutive lanes only (the paper's no-sort case),
                               11 as 4 with the runs flushed into a shared-memory node tile
-                              private to each warp and one reduction per touched node
-                              (see the autotuner) */
+                              private to each warp and one reduction per touched node,
+                              12 thread per particle with lanes grouped by base cell whose
+                              members sum the group's node values through shared memory, one
+                              float4 reduction per group and node (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64

@@ -36,7 +36,8 @@ enum P2GVariant : int {
     P2G_WARP = 9,     // thread per particle, lanes grouped by base cell, shuffle-tree reduction per group (Sec. 4.2.2)
     P2G_WARPRUN = 10, // WARP with groups limited to runs on consecutive lanes (the paper's "no sort" case)
     P2G_WTILE8 = 11,  // CHUNK8 flushing its runs into a warp-private shared-memory node tile, one reduction per node
-    kP2GVariants = 12
+    P2G_WXPOSE = 12,  // thread per particle, lanes grouped by base cell, group sums through shared memory
+    kP2GVariants = 13
 };
 
 // Particle capacity is a multiple of this, so that a staged tile of

@@ -374,6 +374,82 @@ __global__ void __launch_bounds__(kTransferThreads, 8) k_p2g_warp(SimParams sp, 
     warp_scatter(gv, gv.cur, q, ok, g, err);
 }
 
+// ---- group sums through shared memory ---------------------------------------
+// P2G_WXPOSE: a warp takes 32 consecutive particles, one per lane (the loads
+// are one full line per channel, with no reuse to keep in L1), and groups
+// the lanes whose particles share a base cell (__match_any_sync).  A lane
+// alone in its group adds its 27 contributions to the grid directly.  The
+// lanes of a group write theirs to a warp-private buffer, one z-slab of the
+// stencil (9 nodes) at a time, and then split the slab's nodes among them:
+// the member of rank r sums node r, r + s, ... over the s members and issues
+// the one float4 reduction of that node.  The sums are plain shared-memory
+// loads and adds (no shuffle tree, no shared atomics); each group's nodes
+// reach L2 once, as with the paper's warp-level reduction.
+constexpr int kXSlots = 9;   // nodes per pass (one z-slab); row stride 36 words: no bank conflicts
+
+__global__ void __launch_bounds__(kTransferThreads, 8) k_p2g_wxpose(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                   float dt, uint32_t* __restrict__ err)
+{
+    __shared__ float4 xbuf[kTransferThreads * kXSlots];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    if (w0 >= n)
+        return;   // whole warps
+    const int64_t p = w0 + lane;
+    P2GParticle q;
+    const bool ok = p < n && load_p2g_particle(sp, pv, p, dt, q, err);
+    if (!ok)
+        clear_p2g_particle(q);
+    const uint32_t eq = __match_any_sync(kFull, cell_key(q.b, ok, lane));
+    const int gs = __popc(eq);
+    const int rank = __popc(eq & ((1u << lane) - 1u));
+    const bool single = gs == 1;
+    StencilIndex si;
+    bool mapped = ok;
+    if (ok && !stencil_index(gv, q.b, si)) {
+        atomicOr(err, ST_MISSED);
+        mapped = false;
+    }
+    float4* rows = xbuf + (threadIdx.x & ~31) * kXSlots;   // this warp's 32 rows of 9 nodes
+    const float scale = ok ? 1.0f : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p2g_contributions_centred(q, [&](int nidx, float wt, float vx, float vy, float vz, float m) {
+            if (nidx / 9 != k)
+                return;   // another slab's node (resolved at compile time)
+            const float ws = wt * scale;
+            const float4 v = make_float4(ws * vx, ws * vy, ws * vz, ws * m);
+            if (single) {
+                if (mapped)
+                    atomicAdd(&gv.cur[si(nidx % 3, (nidx / 3) % 3, k)], v);
+            } else {
+                rows[lane * kXSlots + nidx % 9] = v;
+            }
+        });
+        __syncwarp();
+        if (!single) {
+#pragma unroll 1
+            for (int t = rank; t < kXSlots; t += gs) {
+                float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                uint32_t mm = eq;
+#pragma unroll 1
+                while (mm) {
+                    const int m = __ffs(mm) - 1;
+                    mm &= mm - 1u;
+                    const float4 v = rows[m * kXSlots + t];
+                    acc.x += v.x;
+                    acc.y += v.y;
+                    acc.z += v.z;
+                    acc.w += v.w;
+                }
+                if (mapped)
+                    atomicAdd(&gv.cur[si(t % 3, t / 3, k)], acc);
+            }
+        }
+        __syncwarp();   // the slab's sums are read before the next slab overwrites the rows
+    }
+}
+
 // ---- register runs into a warp-private node tile -----------------------------
 // P2G_WTILE8: the register runs of k_p2g_chunk<8>, flushed into a node tile
 // in shared memory private to the warp instead of into global memory; the
@@ -662,6 +738,8 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
         k_p2g_warp<true><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_WARPRUN)
         k_p2g_warp<false><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else if (variant == P2G_WXPOSE)
+        k_p2g_wxpose<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_WTILE8) {
         smem_opt_in<k_p2g_wtile<8>>(kWTileBytes);
         k_p2g_wtile<8><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, kWTileBytes, s>>>(sp, pv, gv, n,

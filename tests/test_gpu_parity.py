@@ -223,7 +223,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", list(range(12)))
+@pytest.mark.parametrize("variant", list(range(13)))
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -248,7 +248,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", list(range(12)))
+@pytest.mark.parametrize("variant", list(range(13)))
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -653,7 +653,7 @@ def test_host_buffers_and_side_stream(M):
     assert linf(host["v"].numpy(), s.v) <= 1e-4 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 9, 10, 11])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 9, 10, 11, 12])
 def test_p2g_sparse_cloud_tile_fallback(M, variant):
     """Particles spread over the whole domain: each 256-particle tile's box is
     far larger than the shared-memory tile, so the tile variants take their
@@ -692,7 +692,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
 
 
 @pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4), (3, 5),
-                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7)])
+                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
