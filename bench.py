@@ -624,10 +624,10 @@ def _variant_name(kind, v):
 
 
 KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "tile": "k_p2g_tile",
-                        "chunk4": "k_p2g_chunk<4, 0, 0>", "chunk8": "k_p2g_chunk<8, 0, 0>", "stage4": "k_p2g_stage<4>",
-                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, 1, 0>", "slab4": "k_p2g_slab<4>",
+                        "chunk4": "k_p2g_chunk<4, 0, 0, 0>", "chunk8": "k_p2g_chunk<8, 0, 0, 0>", "stage4": "k_p2g_stage<4>",
+                        "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, 1, 0, 0>", "slab4": "k_p2g_slab<4>",
                         "warp": "k_p2g_warp<1>", "warprun": "k_p2g_warp<0>", "wtile8": "k_p2g_wtile<8>",
-                        "wxpose": "k_p2g_wxpose"},
+                        "wxpose": "k_p2g_wxpose", "chunk8x2": "k_p2g_chunk<8, 0, 0, 1>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         # the bench scene has one material (snow, kind 2): the kernels specialised to it
                         "occ": "k_g2p_occ<8, 2, 128, 0, 0>", "stage": "k_g2p_stage",
@@ -640,6 +640,27 @@ FUSED_KERNEL_NAMES = {0: "k_g2p2g", 1: "k_g2p2g", 2: "k_g2p2g", 3: "k_g2p2g_chun
                       4: "k_g2p2g_chunk<8, 0>", 5: "k_g2p2g_chunk<4, 0>", 6: "k_g2p2g_chunk<8, 0>",
                       7: "k_g2p2g_chunk<4, 1>", 8: "k_g2p2g", 9: "k_g2p2g_warp<1>", 10: "k_g2p2g_warp<0>",
                       11: "k_g2p2g_chunk<8, 0>"}
+
+
+def p2g_kernel_name(variant, aosoa, warps):
+    """The P2G kernel a variant launches, as ncu names it, for the store layout
+    and the CTA size (the register-run forms have one instantiation each)."""
+    if variant in ("chunk4", "chunk8"):
+        k = variant[-1]
+        if warps == 2:
+            return "k_p2g_chunk_w2<%s, %d>" % (k, int(aosoa))
+        if warps == 8:
+            return "k_p2g_chunk_w8<%s>" % k
+        return "k_p2g_chunk<%s, 0, %d, 0>" % (k, int(aosoa))
+    return KERNEL_NAMES["P2G"][variant]
+
+
+def g2p_kernel_name(variant, aosoa, warps):
+    """The G2P kernel a variant launches on the snow scene (kind 2), as ncu names it."""
+    if variant in ("occ", "occsw"):
+        threads = 128 if (variant == "occsw" and not aosoa) else 32 * warps
+        return "k_g2p_occ<8, 2, %d, %d, %d>" % (threads, int(variant == "occsw"), int(aosoa))
+    return KERNEL_NAMES["G2P"][variant]
 
 
 KERNEL_SOURCES = ("transfer.cuh", "p2g.cu", "g2p.cu", "g2p2g.cu", "device_math.cuh", "async_copy.cuh", "internal.h")
@@ -693,7 +714,7 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose); -1 = autotune")
+                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose, 13 chunk8x2); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10, "
                          "7 occsw); -1 = autotune")
@@ -791,8 +812,8 @@ def main():
     # warps per CTA of the register-run P2G and the 64-register G2P, then the particle store layout
     tuned_w = tune.tune_cta_warps(sim, DT, steps=20, rounds=2)  # advances 132 substeps
     warm -= 132
-    tuned_l = tune.tune_layout(sim, DT, tuned_w["best"], steps=20, rounds=2)   # advances 88 substeps
-    warm -= 88
+    tuned_l = tune.tune_layout(sim, DT, tuned_w["best"], steps=20, rounds=2)   # advances 132 substeps
+    warm -= 132
     # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene;
     # the fused kernel's scatter follows the P2G variant (direct, chunk4, chunk8)
     fused_ms, fused_scatter_ms = {}, {}
@@ -801,8 +822,8 @@ def main():
     for _ in range(2):
         sim.set_g2p2g(False)
         sim.set_p2g_variant(p2g_separate)
-        sim.set_layout(aosoa)
         sim.set_cta_warps(tuned_l["cta_warps"])
+        sim.set_layout(aosoa)
         sim.run(3, DT)
         fused_ms.setdefault("separate", []).append(_events_time(stream, lambda: sim.run(20, DT)) / 20)
         warm -= 23
@@ -822,8 +843,8 @@ def main():
     sim.set_g2p2g(bool(use_fused))
     sim.set_p2g_variant(p2g_final)
     if not use_fused:
-        sim.set_layout(aosoa)
         sim.set_cta_warps(tuned_l["cta_warps"])
+        sim.set_layout(aosoa)
     warm = max(3, warm)
     sim.run(warm, DT)
     sim.sync()
@@ -877,18 +898,10 @@ def main():
     if use_fused:
         # per substep: grid update + k_g2p2g (reads x F Jp vol mat 57 B, writes x v C F Jp 100 B)
         algo["g2p"] = 157 * n_now
-    kernel_name = {"p2g": KERNEL_NAMES["P2G"][tuned["best_name"]],
+    kernel_name = {"p2g": p2g_kernel_name(tuned["best_name"], aosoa and not use_fused, tuned_l["cta_warps"]),
                    "g2p": (FUSED_KERNEL_NAMES[p2g_final] if use_fused
-                           else KERNEL_NAMES["G2P"][tuned_g["best_name"]]),
+                           else g2p_kernel_name(tuned_g["best_name"], aosoa, tuned_l["cta_warps"])),
                    "grid": "k_grid"}[dom]
-    if aosoa and not use_fused and kernel_name.endswith(" 0>"):
-        kernel_name = kernel_name[:-len(" 0>")] + " 1>"   # the AoSoA instantiation
-    w = tuned_l["cta_warps"]
-    if not use_fused and w != 4:   # the instantiations for CTAs of 2 or 8 warps
-        if kernel_name.startswith("k_p2g_chunk<") and kernel_name.endswith(", 0, 0>"):
-            kernel_name = "k_p2g_chunk_w%d<%s>" % (w, kernel_name[len("k_p2g_chunk<"):].split(",")[0])
-        elif kernel_name.startswith("k_g2p_occ<8, "):
-            kernel_name = kernel_name.replace(", 128, ", ", %d, " % (32 * w))
     # the same kernel on the layout-free byte count (P2G: x, v, C, F, Jp = 100 B per particle)
     survey_bytes = {"p2g": SURVEY_BYTES_P2G * n_now}.get(dom)
     achieved_survey = survey_bytes / (avg[dom] / 1e3) / 1e9 if (survey_bytes and avg[dom] > 0) else None

@@ -1269,10 +1269,10 @@ mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa)
     if (aosoa && ((ctx->cfg.p2g_variant != P2G_CHUNK4 && ctx->cfg.p2g_variant != P2G_CHUNK8) ||
                   (ctx->cfg.g2p_variant != G2P_OCC && ctx->cfg.g2p_variant != G2P_OCCSW) || ctx->cfg.use_g2p2g ||
                   ctx->cfg.transfer != MPM_APIC ||
-                  ctx->sp.cta_warps != 4))
+                  ctx->sp.cta_warps == 8))
         return fail(ctx, MPM_EINVAL,
                     "mpm_set_layout: AoSoA needs P2G variant 3 or 4, G2P variant 4 or 7, separate APIC transfers and "
-                    "4 warps per CTA");
+                    "2 or 4 warps per CTA");
     // convert the current particles into the other buffer, then make it current
     PartView dst = ctx->pv[1 - ctx->cur];
     dst.aosoa = aosoa;
@@ -1293,8 +1293,8 @@ mpm_status mpm_set_cta_warps(mpm_ctx* ctx, int warps)
 {
     if (!ctx || (warps != 2 && warps != 4 && warps != 8))
         return MPM_EINVAL;
-    if (ctx->aosoa && warps != 4)
-        return fail(ctx, MPM_EINVAL, "mpm_set_cta_warps: the AoSoA layout runs 4 warps per CTA only");
+    if (ctx->aosoa && warps == 8)
+        return fail(ctx, MPM_EINVAL, "mpm_set_cta_warps: the AoSoA layout runs 2 or 4 warps per CTA only");
     ctx->sp.cta_warps = warps;
     drop_graphs(ctx);
     return MPM_OK;

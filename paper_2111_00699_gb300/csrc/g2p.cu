@@ -557,10 +557,16 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
     if (n > 0)
     {
         if (pv.aosoa) {   // the AoSoA store has the 64-register forms only (the context allows no other)
-            if (variant == G2P_OCCSW)
+            if (sp.cta_warps == 2) {
+                if (variant == G2P_OCCSW)
+                    launch_g2p_occ_t<64, true, true>(sp, pv, gv, n, dt, flags, err, s);
+                else
+                    launch_g2p_occ_t<64, false, true>(sp, pv, gv, n, dt, flags, err, s);
+            } else if (variant == G2P_OCCSW) {
                 launch_g2p_occ_t<kTransferThreads, true, true>(sp, pv, gv, n, dt, flags, err, s);
-            else
+            } else {
                 launch_g2p_occ_t<kTransferThreads, false, true>(sp, pv, gv, n, dt, flags, err, s);
+            }
         }
         else if (sp.transfer == MPM_ASFLIP)
             k_g2p_asflip<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, flags, err);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kTileThreads) k_p2g_tile(SimParams sp, PartVie
 }
 
 
-template <int K, bool kSmem, bool kAoS = false>
+template <int K, bool kSmem, bool kAoS = false, bool kX2 = false>
 __device__ __forceinline__ void p2g_chunk_body(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n,
                                                float dt, uint32_t* __restrict__ err)
 {
@@ -165,29 +165,32 @@ __device__ __forceinline__ void p2g_chunk_body(const SimParams& sp, const PartVi
             cb[2] = q.b[2];
             open = true;
         }
-        acc_add(acc, q);
+        if constexpr (kX2)
+            acc_add_x2(acc, q);
+        else
+            acc_add(acc, q);
     }
     if (open)
         acc_flush(gv, gv.cur, acc, cb, err);
 }
 
-template <int K, bool kSmem, bool kAoS = false>
+template <int K, bool kSmem, bool kAoS = false, bool kX2 = false>
 __global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 3) k_p2g_chunk(SimParams sp, PartView pv, GridView gv,
                                                                               int64_t n, float dt,
                                                                               uint32_t* __restrict__ err)
 {
-    p2g_chunk_body<K, kSmem, kAoS>(sp, pv, gv, n, dt, err);
+    p2g_chunk_body<K, kSmem, kAoS, kX2>(sp, pv, gv, n, dt, err);
 }
 
 // The same register runs in CTAs of 2 or 8 warps instead of 4 (the paper's
 // warps-per-block study, Sec. 6.2), at the same register budget per thread
 // (168), so that only the CTA shape changes: 6 CTAs of 64 or one CTA of 256
 // threads per SM (12 and 8 warps; 4 warps give 3 CTAs, 12 warps).
-template <int K>
+template <int K, bool kAoS = false>
 __global__ void __launch_bounds__(64, 6) k_p2g_chunk_w2(SimParams sp, PartView pv, GridView gv, int64_t n, float dt,
                                                         uint32_t* __restrict__ err)
 {
-    p2g_chunk_body<K, false>(sp, pv, gv, n, dt, err);
+    p2g_chunk_body<K, false, kAoS>(sp, pv, gv, n, dt, err);
 }
 
 template <int K>
@@ -699,7 +702,16 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
     if (n <= 0)
         return;
     if (pv.aosoa) {
-        // the AoSoA store has register-run forms only (the context allows no other variant with it)
+        // the AoSoA store has register-run forms only (the context allows no other variant with it),
+        // in CTAs of 4 or 2 warps
+        if (sp.cta_warps == 2) {
+            const unsigned g = variant == P2G_CHUNK8 ? blocks_for((n + 7) / 8, 64) : blocks_for((n + 3) / 4, 64);
+            if (variant == P2G_CHUNK8)
+                k_p2g_chunk_w2<8, true><<<g, 64, 0, s>>>(sp, pv, gv, n, dt, err);
+            else
+                k_p2g_chunk_w2<4, true><<<g, 64, 0, s>>>(sp, pv, gv, n, dt, err);
+            return;
+        }
         if (variant == P2G_CHUNK8)
             k_p2g_chunk<8, false, true><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(
                 sp, pv, gv, n, dt, err);
@@ -738,6 +750,9 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
         k_p2g_warp<true><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_WARPRUN)
         k_p2g_warp<false><<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+    else if (variant == P2G_CHUNK8X2)
+        k_p2g_chunk<8, false, false, true><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(
+            sp, pv, gv, n, dt, err);
     else if (variant == P2G_WXPOSE)
         k_p2g_wxpose<<<blocks_for(n, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
     else if (variant == P2G_WTILE8) {

@@ -272,6 +272,43 @@ __device__ __forceinline__ void acc_add(NodeAcc& acc, const P2GParticle& q)
     });
 }
 
+// acc_add with Blackwell's paired FP32 arithmetic (__ffma2_rn: two fused
+// multiply-adds in one instruction): the accumulator float4 is two pairs,
+// (p_x, p_y) and (p_z, m), and the affine value's x and y rows are formed as
+// one pair.
+__device__ __forceinline__ void acc_add_x2(NodeAcc& acc, const P2GParticle& q)
+{
+    const float2 mvxy = make_float2(q.mv[0], q.mv[1]);
+    const float2 ax = make_float2(q.A[0], q.A[3]), ay = make_float2(q.A[1], q.A[4]), az = make_float2(q.A[2], q.A[5]);
+    float dxo[3], dyo[3], dzo[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dxo[i] = (float)i - q.f[0];
+        dyo[i] = (float)i - q.f[1];
+        dzo[i] = (float)i - q.f[2];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float wyz = q.w[1][j] * q.w[2][k];
+            const float2 bxy = __ffma2_rn(az, make_float2(dzo[k], dzo[k]),
+                                          __ffma2_rn(ay, make_float2(dyo[j], dyo[j]), mvxy));
+            const float bz = q.mv[2] + q.A[7] * dyo[j] + q.A[8] * dzo[k];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float wt = q.w[0][i] * wyz;
+                const float2 w2 = make_float2(wt, wt);
+                const float2 vxy = __ffma2_rn(ax, make_float2(dxo[i], dxo[i]), bxy);
+                const float vz = fmaf(q.A[6], dxo[i], bz);
+                float4& a = acc.a[i + 3 * j + 9 * k];
+                const float2 axy = __ffma2_rn(w2, vxy, make_float2(a.x, a.y));
+                const float2 azw = __ffma2_rn(w2, make_float2(vz, q.mp), make_float2(a.z, a.w));
+                a = make_float4(axy.x, axy.y, azw.x, azw.y);
+            }
+        }
+}
+
 // The same 27 accumulators held in shared memory, private to one thread:
 // node n at base[n * kTransferThreads] (a warp touches 32 consecutive float4
 // per node: no bank conflicts, no atomics).  Frees ~108 registers per thread

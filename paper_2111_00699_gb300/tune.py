@@ -91,21 +91,23 @@ def _p2g_g2p_ms(sim, dt, steps):
 
 
 def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) -> dict:
-    """SoA (at `warps` warps per CTA) against the AoSoA store (which runs 4
-    warps per CTA), timing P2G + G2P per substep; keeps the faster.  Needs
-    the register-run P2G (variant 3 or 4) and the 64-register G2P (4 or 7)
-    already selected; otherwise the store stays SoA.  Returns {"best":
-    "soa" | "aosoa", "ms": {...}, "cta_warps": the warps kept}."""
-    ms = {"soa": float("inf"), "aosoa": float("inf")}
+    """SoA (at `warps` warps per CTA) against the AoSoA store at 2 and at 4
+    warps per CTA (the warp counts it runs), timing P2G + G2P per substep;
+    keeps the fastest.  Needs the register-run P2G (variant 3 or 4) and the
+    64-register G2P (4 or 7) already selected; otherwise the store stays SoA.
+    Returns {"best": "soa" | "aosoa", "ms": {...}, "cta_warps": the warps kept}."""
+    ms = {"soa": float("inf"), "aosoa_2": float("inf"), "aosoa_4": float("inf")}
     sim.profile_enable(True)
     try:
         for _ in range(rounds):
             sim.set_layout(False)
             sim.set_cta_warps(warps)
             ms["soa"] = min(ms["soa"], _p2g_g2p_ms(sim, dt, steps))
-            sim.set_cta_warps(4)
-            sim.set_layout(True)
-            ms["aosoa"] = min(ms["aosoa"], _p2g_g2p_ms(sim, dt, steps))
+            for w in (2, 4):
+                sim.set_cta_warps(w)
+                sim.set_layout(True)
+                ms["aosoa_%d" % w] = min(ms["aosoa_%d" % w], _p2g_g2p_ms(sim, dt, steps))
+                sim.set_layout(False)
     except Exception as exc:   # the selected variants have no AoSoA form
         sim.profile_enable(False)
         sim.set_layout(False)
@@ -114,6 +116,9 @@ def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) ->
     sim.profile_enable(False)
     best = min(ms, key=ms.get)
     if best == "soa":
-        sim.set_layout(False)
         sim.set_cta_warps(warps)
-    return {"best": best, "ms": ms, "cta_warps": warps if best == "soa" else 4}
+        return {"best": "soa", "ms": ms, "cta_warps": warps}
+    w = int(best.split("_")[1])
+    sim.set_cta_warps(w)
+    sim.set_layout(True)
+    return {"best": "aosoa", "ms": ms, "cta_warps": w}

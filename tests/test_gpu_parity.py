@@ -223,7 +223,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", list(range(13)))
+@pytest.mark.parametrize("variant", list(range(14)))
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -248,7 +248,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", list(range(13)))
+@pytest.mark.parametrize("variant", list(range(14)))
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -692,7 +692,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
 
 
 @pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4), (3, 5),
-                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7)])
+                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7), (13, 4)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
@@ -755,7 +755,7 @@ def test_aosoa_layout_keeps_parity(M):
         g = _run_both(M, sim, [om], s, 3, 1e-4, cfg)
         sim.set_layout(True)
         for bad in (lambda: sim.set_p2g_variant(0), lambda: sim.set_g2p_variant(0), lambda: sim.set_g2p2g(True),
-                    lambda: sim.set_cta_warps(2)):
+                    lambda: sim.set_cta_warps(8)):
             with pytest.raises(M.MpmError):
                 bad()
         g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
@@ -768,15 +768,52 @@ def test_aosoa_layout_keeps_parity(M):
                       np.concatenate([s.F, np.tile(np.eye(3), (len(x2), 1, 1))]),
                       np.concatenate([s.Jp, np.ones(len(x2))]), vol)
         sim.set_p2g_variant(3)
+        sim.set_cta_warps(2)   # the AoSoA kernels in CTAs of 2 warps
         g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
         assert linf(g["x"], s.x) <= 1e-4
         assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+        sim.set_cta_warps(4)
         sim.set_layout(False)
         sim.set_p2g_variant(0)
         g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
         assert linf(g["x"], s.x) <= 1e-4
         assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
         assert linf(g["C"], s.C) <= 1e-4 * np.abs(s.C).max()
+
+
+@pytest.mark.parametrize("kind", ["snow", "fluid", "sand", "nacc"])
+def test_aosoa_material_kinds(M, kind):
+    """The AoSoA store with the kernels specialised to one material kind (G2P
+    with the weights in shared memory, P2G register runs of 4): 10 substeps
+    against the oracle, random velocities and strains so that the return maps
+    act."""
+    kw = dict(snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
+              fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
+              sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0),
+              nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9,
+                        alpha0=-0.01))[kind]
+    k = kw.pop("kind")
+    gm, om = mats_pair(M, k, **kw)
+    dt = 5e-5 if k == M.SNOW else 1e-4
+    x, _ = scenes.blocks(23, 15000, 64, 2)
+    vol = (1 / 64) ** 3 / 8
+    rng = np.random.default_rng(9)
+    n = len(x)
+    v = (0.3 * rng.normal(size=(n, 3))).astype(np.float32)
+    F = (np.eye(3) + 0.01 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    cfg = orc.config(64, 1 / 64, orc.SLIP)
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, p2g_variant=3, g2p_variant=7) as sim:
+        sim.add_particles(x, v=v)
+        if k != M.FLUID:
+            sim.write_state(F=torch.from_numpy(F).cuda())
+        sim.set_layout(True)
+        s = oracle_state_from(sim.read_state(), vol)
+        g = _run_both(M, sim, [om], s, 10, dt, cfg)
+    assert linf(g["x"], s.x) <= 1e-4
+    assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
+    if k != M.FLUID:
+        assert linf(g["F"], s.F) <= 1e-4
+    assert linf(g["Jp"], s.Jp) <= 1e-4
 
 
 # ------------------------------------------------------------- emission (a7)
