@@ -333,26 +333,46 @@ def bench_small_elastic(substeps=100, reps=5):
     fixed-corotated E 1e4, nu 0.2, rho 1, dt 1e-4, sticky walls, 100
     substeps.  The whole state fits in L2, so the figure is microseconds per
     substep (launch and latency bound), for the separate phases and for the
-    fused G2P2G transfer (the paper's choice below ~100K particles)."""
+    fused G2P2G transfer (the paper's choice below ~100K particles), with the
+    default launch variants and with variants autotuned on this scene (at
+    8,192 particles a launch of 8-particle chunks fills 8 of the 152 SMs)."""
     import torch
-    from paper_2111_00699_gb300 import mpm, scenes
+    from paper_2111_00699_gb300 import mpm, scenes, tune
     x = torch.from_numpy(scenes.cube_uniform(0, 8192, 0.4, 0.6)).cuda()
     vol = torch.full((8192,), 0.008 / 8192, device="cuda")
     stream = torch.cuda.Stream()
+    mat = mpm.material(mpm.ELASTIC, E=1e4, nu=0.2, rho=1.0)
     out = {"workload": "small elastic, 8192 particles, 64^3, dt=1e-4, 100 substeps", "unit": "us/substep"}
-    for name, fused, graphs in (("separate", False, False), ("separate_graphs", False, True),
-                                ("g2p2g", True, False), ("g2p2g_graphs", True, True)):
+
+    def timed(p2g, g2p, fused, graphs, warps=4):
         best = None
         for _ in range(reps):
-            with mpm.Simulator(64, 1 / 64, [mpm.material(mpm.ELASTIC, E=1e4, nu=0.2, rho=1.0)],
-                               stream=stream, p2g_variant=3, g2p_variant=0, g2p2g=fused, graphs=graphs) as sim:
+            with mpm.Simulator(64, 1 / 64, [mat], stream=stream, p2g_variant=p2g, g2p_variant=g2p, g2p2g=fused,
+                               graphs=graphs) as sim:
+                sim.set_cta_warps(warps)
                 sim.add_particles(x, vol=vol)
                 sim.run(3, 1e-4)
                 ms = _events_time(stream, lambda: sim.run(substeps, 1e-4))
                 sim.sync()
             best = ms if best is None else min(best, ms)
-        out[name] = 1e3 * best / substeps
-    out["value"] = min(out["separate"], out["separate_graphs"], out["g2p2g"], out["g2p2g_graphs"])
+        return 1e3 * best / substeps
+
+    for name, fused, graphs in (("separate", False, False), ("separate_graphs", False, True),
+                                ("g2p2g", True, False), ("g2p2g_graphs", True, True)):
+        out[name] = timed(3, 0, fused, graphs)
+    # variants tuned on this scene (per-phase kernel times), then the substep from graphs
+    with mpm.Simulator(64, 1 / 64, [mat], stream=stream) as sim:
+        sim.add_particles(x, vol=vol)
+        sim.run(3, 1e-4)
+        tp = tune.tune_p2g(sim, 1e-4, steps=10, rounds=2)
+        tg = tune.tune_g2p(sim, 1e-4, steps=10, rounds=2)
+        tw = tune.tune_cta_warps(sim, 1e-4, steps=10, rounds=2)
+    out["tuned"] = {"p2g": tp["best_name"], "g2p": tg["best_name"], "cta_warps": tw["best"]}
+    out["separate_graphs_tuned"] = timed(tp["best"], tg["best"], False, True, tw["best"])
+    fused = {_variant_name("P2G", v): timed(v, 0, True, True) for v in FUSED_SCATTER_VARIANTS}
+    out["g2p2g_graphs_by_scatter"] = fused
+    out["g2p2g_graphs_tuned"] = min(fused.values())
+    out["value"] = min(v for k, v in out.items() if k.startswith(("separate", "g2p2g")) and isinstance(v, float))
     out["particle_substeps_per_s"] = 8192 / (out["value"] * 1e-6)
     return out
 
