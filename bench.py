@@ -680,6 +680,8 @@ def g2p_kernel_name(variant, aosoa, warps):
     if variant in ("occ", "occsw"):
         threads = 128 if (variant == "occsw" and not aosoa) else 32 * warps
         return "k_g2p_occ<8, 2, %d, %d, %d>" % (threads, int(variant == "occsw"), int(aosoa))
+    if variant == "occ10" and aosoa:
+        return "k_g2p_occ<10, 2, 128, 0, 1>"
     return KERNEL_NAMES["G2P"][variant]
 
 
@@ -839,6 +841,7 @@ def main():
     fused_ms, fused_scatter_ms = {}, {}
     p2g_separate = tuned["best"] if tuned["best"] >= 0 else 3
     aosoa = tuned_l["best"] == "aosoa"
+    g2p_final = tuned_l.get("aosoa_g2p_variant", tuned_g["best"]) if aosoa else tuned_g["best"]
     for _ in range(2):
         sim.set_g2p2g(False)
         sim.set_p2g_variant(p2g_separate)
@@ -920,7 +923,7 @@ def main():
         algo["g2p"] = 157 * n_now
     kernel_name = {"p2g": p2g_kernel_name(tuned["best_name"], aosoa and not use_fused, tuned_l["cta_warps"]),
                    "g2p": (FUSED_KERNEL_NAMES[p2g_final] if use_fused
-                           else g2p_kernel_name(tuned_g["best_name"], aosoa, tuned_l["cta_warps"])),
+                           else g2p_kernel_name(_variant_name("G2P", g2p_final), aosoa, tuned_l["cta_warps"])),
                    "grid": "k_grid"}[dom]
     # the same kernel on the layout-free byte count (P2G: x, v, C, F, Jp = 100 B per particle)
     survey_bytes = {"p2g": SURVEY_BYTES_P2G * n_now}.get(dom)
@@ -949,7 +952,7 @@ def main():
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if args.e2e_frames > 0:
-        sim = fresh_sim(p2g_final, tuned_g["best"])
+        sim = fresh_sim(p2g_final, g2p_final)
         sim.set_g2p2g(bool(use_fused))
         if not use_fused:
             sim.set_cta_warps(tuned_l["cta_warps"])

@@ -363,7 +363,7 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
  * particles with each channel's 32 floats contiguous inside the packet, so a
  * warp's particles keep their whole state in one 4 KB span.  The current
  * particles are converted on the stream.  AoSoA runs P2G variants 3 and 4,
- * G2P variants 4 and 7, 2 or 4 warps per CTA and separate APIC transfers only: switching
+ * G2P variants 4, 6 and 7, 2 or 4 warps per CTA and separate APIC transfers only: switching
  * to it from another configuration, or to another configuration under it,
  * returns MPM_EINVAL.  Results are identical up to float summation order. */
 mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa);

@@ -1267,11 +1267,12 @@ mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa)
     if (aosoa == ctx->aosoa)
         return MPM_OK;
     if (aosoa && ((ctx->cfg.p2g_variant != P2G_CHUNK4 && ctx->cfg.p2g_variant != P2G_CHUNK8) ||
-                  (ctx->cfg.g2p_variant != G2P_OCC && ctx->cfg.g2p_variant != G2P_OCCSW) || ctx->cfg.use_g2p2g ||
+                  (ctx->cfg.g2p_variant != G2P_OCC && ctx->cfg.g2p_variant != G2P_OCCSW &&
+                   ctx->cfg.g2p_variant != G2P_OCC10) || ctx->cfg.use_g2p2g ||
                   ctx->cfg.transfer != MPM_APIC ||
                   ctx->sp.cta_warps == 8))
         return fail(ctx, MPM_EINVAL,
-                    "mpm_set_layout: AoSoA needs P2G variant 3 or 4, G2P variant 4 or 7, separate APIC transfers and "
+                    "mpm_set_layout: AoSoA needs P2G variant 3 or 4, G2P variant 4, 6 or 7, separate APIC transfers and "
                     "2 or 4 warps per CTA");
     // convert the current particles into the other buffer, then make it current
     PartView dst = ctx->pv[1 - ctx->cur];
@@ -1327,8 +1328,8 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant)
 {
     if (!ctx || variant < 0 || variant >= kG2PVariants)
         return MPM_EINVAL;
-    if (ctx->aosoa && variant != G2P_OCC && variant != G2P_OCCSW)
-        return fail(ctx, MPM_EINVAL, "mpm_set_g2p_variant: the AoSoA layout has G2P variants 4 and 7 only");
+    if (ctx->aosoa && variant != G2P_OCC && variant != G2P_OCCSW && variant != G2P_OCC10)
+        return fail(ctx, MPM_EINVAL, "mpm_set_g2p_variant: the AoSoA layout has G2P variants 4, 6 and 7 only");
     ctx->cfg.g2p_variant = variant;
     drop_graphs(ctx);
     return MPM_OK;

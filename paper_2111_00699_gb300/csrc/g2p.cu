@@ -522,19 +522,20 @@ MatParams make_mat_params(const mpm_material& m)
 
 
 // G2P_OCC, specialised to the material kind when the scene has only one.
-template <int T, bool kSmemW = false, bool kAoS = false>
+template <int T, bool kSmemW = false, bool kAoS = false, int MinBlocks = 8>
 static void launch_g2p_occ_t(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n, float dt,
                              uint32_t* flags, uint32_t* err, cudaStream_t s)
 {
+    constexpr int B = MinBlocks;
     const unsigned g = blocks_for(n, T);
     switch (sp.n_mats == 1 ? sp.mat[0].kind : -1) {
-    case MPM_ELASTIC: k_g2p_occ<8, MPM_ELASTIC, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
-    case MPM_FLUID: k_g2p_occ<8, MPM_FLUID, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
-    case MPM_SNOW: k_g2p_occ<8, MPM_SNOW, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
-    case MPM_SAND: k_g2p_occ<8, MPM_SAND, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
-    case MPM_NACC: k_g2p_occ<8, MPM_NACC, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
-    case MPM_NHSAND: k_g2p_occ<8, MPM_NHSAND, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
-    default: k_g2p_occ<8, -1, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_ELASTIC: k_g2p_occ<B, MPM_ELASTIC, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_FLUID: k_g2p_occ<B, MPM_FLUID, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_SNOW: k_g2p_occ<B, MPM_SNOW, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_SAND: k_g2p_occ<B, MPM_SAND, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_NACC: k_g2p_occ<B, MPM_NACC, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    case MPM_NHSAND: k_g2p_occ<B, MPM_NHSAND, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
+    default: k_g2p_occ<B, -1, T, kSmemW, kAoS><<<g, T, 0, s>>>(sp, pv, gv, n, dt, flags, err); break;
     }
 }
 
@@ -556,8 +557,10 @@ void launch_g2p(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n > 0)
     {
-        if (pv.aosoa) {   // the AoSoA store has the 64-register forms only (the context allows no other)
-            if (sp.cta_warps == 2) {
+        if (pv.aosoa) {   // the AoSoA store has the thread-per-particle forms 4, 6 and 7 only
+            if (variant == G2P_OCC10)   // 48 registers, 10 CTAs of 128 per SM
+                launch_g2p_occ_t<kTransferThreads, false, true, 10>(sp, pv, gv, n, dt, flags, err, s);
+            else if (sp.cta_warps == 2) {
                 if (variant == G2P_OCCSW)
                     launch_g2p_occ_t<64, true, true>(sp, pv, gv, n, dt, flags, err, s);
                 else

@@ -121,4 +121,10 @@ def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) ->
     w = int(best.split("_")[1])
     sim.set_cta_warps(w)
     sim.set_layout(True)
-    return {"best": "aosoa", "ms": ms, "cta_warps": w}
+    # the G2P forms of the AoSoA store, re-timed on it (64 registers with the weights in
+    # registers or in shared memory, 48 registers): their spills differ from SoA's
+    g2p_ms = _time(sim, dt, _lib.G2P_VARIANTS, sim.set_g2p_variant, "g2p", steps, rounds, (4, 6, 7))
+    g2p_best = min((4, 6, 7), key=lambda v: g2p_ms[_lib.G2P_VARIANTS[v]])
+    sim.set_g2p_variant(g2p_best)
+    return {"best": "aosoa", "ms": ms, "cta_warps": w, "aosoa_g2p_ms": g2p_ms,
+            "aosoa_g2p": _lib.G2P_VARIANTS[g2p_best], "aosoa_g2p_variant": g2p_best}

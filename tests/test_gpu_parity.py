@@ -781,17 +781,18 @@ def test_aosoa_layout_keeps_parity(M):
         assert linf(g["C"], s.C) <= 1e-4 * np.abs(s.C).max()
 
 
-@pytest.mark.parametrize("kind", ["snow", "fluid", "sand", "nacc"])
-def test_aosoa_material_kinds(M, kind):
+@pytest.mark.parametrize("kind,g2p", [("snow", 7), ("fluid", 7), ("sand", 7), ("nacc", 7), ("snow", 6), ("elastic", 4)])
+def test_aosoa_material_kinds(M, kind, g2p):
     """The AoSoA store with the kernels specialised to one material kind (G2P
-    with the weights in shared memory, P2G register runs of 4): 10 substeps
-    against the oracle, random velocities and strains so that the return maps
-    act."""
+    at 64 registers with the weights in shared memory or in registers, or at
+    48 registers; P2G register runs of 4): 10 substeps against the oracle,
+    random velocities and strains so that the return maps act."""
     kw = dict(snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0, theta_c=2.5e-2, theta_s=7.5e-3, hardening=10.0),
               fluid=dict(kind=M.FLUID, E=1e4, gamma=7.0, rho=1000.0),
               sand=dict(kind=M.SAND, E=3.5e5, nu=0.3, rho=2200.0, friction_deg=30.0),
               nacc=dict(kind=M.NACC, E=5e4, nu=0.3, rho=400.0, hardening=5.0, friction_M=0.8, cohesion=0.9,
-                        alpha0=-0.01))[kind]
+                        alpha0=-0.01),
+              elastic=dict(kind=M.ELASTIC, E=1e4, nu=0.2, rho=1000.0))[kind]
     k = kw.pop("kind")
     gm, om = mats_pair(M, k, **kw)
     dt = 5e-5 if k == M.SNOW else 1e-4
@@ -802,7 +803,7 @@ def test_aosoa_material_kinds(M, kind):
     v = (0.3 * rng.normal(size=(n, 3))).astype(np.float32)
     F = (np.eye(3) + 0.01 * rng.normal(size=(n, 3, 3))).astype(np.float32)
     cfg = orc.config(64, 1 / 64, orc.SLIP)
-    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, p2g_variant=3, g2p_variant=7) as sim:
+    with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, p2g_variant=3, g2p_variant=g2p) as sim:
         sim.add_particles(x, v=v)
         if k != M.FLUID:
             sim.write_state(F=torch.from_numpy(F).cuda())
