@@ -647,7 +647,8 @@ KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "t
                         "chunk4": "k_p2g_chunk<4, 0, 0, 0>", "chunk8": "k_p2g_chunk<8, 0, 0, 0>", "stage4": "k_p2g_stage<4>",
                         "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, 1, 0, 0>", "slab4": "k_p2g_slab<4>",
                         "warp": "k_p2g_warp<1>", "warprun": "k_p2g_warp<0>", "wtile8": "k_p2g_wtile<8>",
-                        "wxpose": "k_p2g_wxpose", "chunk8x2": "k_p2g_chunk<8, 0, 0, 1>"},
+                        "wxpose": "k_p2g_wxpose", "chunk8x2": "k_p2g_chunk<8, 0, 0, 1>",
+                        "node": "k_p2g_node<4, 0>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         # the bench scene has one material (snow, kind 2): the kernels specialised to it
                         "occ": "k_g2p_occ<8, 2, 128, 0, 0>", "stage": "k_g2p_stage",
@@ -672,6 +673,8 @@ def p2g_kernel_name(variant, aosoa, warps):
         if warps == 8:
             return "k_p2g_chunk_w8<%s>" % k
         return "k_p2g_chunk<%s, 0, %d, 0>" % (k, int(aosoa))
+    if variant == "node":
+        return "k_p2g_node<4, %d>" % int(aosoa)
     return KERNEL_NAMES["P2G"][variant]
 
 
@@ -736,7 +739,7 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose, 13 chunk8x2); -1 = autotune")
+                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose, 13 chunk8x2, 14 node); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10, "
                          "7 occsw); -1 = autotune")

@@ -115,7 +115,11 @@ typedef struct {
                               private to each warp and one reduction per touched node,
                               12 thread per particle with lanes grouped by base cell whose
                               members sum the group's node values through shared memory, one
-                              float4 reduction per group and node (see the autotuner) */
+                              float4 reduction per group and node, 13 as 4 accumulating with
+                              paired FP32 fused multiply-adds, 14 a warp per run of particles
+                              with one lane per stencil node, taking the particles one at a
+                              time into one float4 per lane and reducing the 27 nodes at each
+                              change of cell (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64
@@ -362,7 +366,7 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
  * one array per state channel (the default); 1 = AoSoA, packets of 32
  * particles with each channel's 32 floats contiguous inside the packet, so a
  * warp's particles keep their whole state in one 4 KB span.  The current
- * particles are converted on the stream.  AoSoA runs P2G variants 3 and 4,
+ * particles are converted on the stream.  AoSoA runs P2G variants 3, 4 and 14,
  * G2P variants 4, 6 and 7, 2 or 4 warps per CTA and separate APIC transfers only: switching
  * to it from another configuration, or to another configuration under it,
  * returns MPM_EINVAL.  Results are identical up to float summation order. */

@@ -25,7 +25,7 @@ APIC, ASFLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
 P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4", "slab4", "warp",
-                "warprun", "wtile8", "wxpose", "chunk8x2")
+                "warprun", "wtile8", "wxpose", "chunk8x2", "node")
 G2P_VARIANTS = ("direct", "chunk4", "chunk8", "tile", "occ", "stage", "occ10", "occsw")
 
 

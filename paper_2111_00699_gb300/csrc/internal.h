@@ -38,7 +38,8 @@ enum P2GVariant : int {
     P2G_WTILE8 = 11,  // CHUNK8 flushing its runs into a warp-private shared-memory node tile, one reduction per node
     P2G_WXPOSE = 12,  // thread per particle, lanes grouped by base cell, group sums through shared memory
     P2G_CHUNK8X2 = 13, // CHUNK8 accumulating with paired FP32 fused multiply-adds
-    kP2GVariants = 14
+    P2G_NODE = 14,    // warp per run of particles, one lane per stencil node
+    kP2GVariants = 15
 };
 
 // Particle capacity is a multiple of this, so that a staged tile of

@@ -377,6 +377,24 @@ __global__ void __launch_bounds__(kTransferThreads, 8) k_p2g_warp(SimParams sp, 
     warp_scatter(gv, gv.cur, q, ok, g, err);
 }
 
+// ---- node-parallel runs ----------------------------------------------------
+// P2G_NODE: the work of a run spread over the stencil's nodes instead of its
+// particles (node_runs in transfer.cuh): a warp takes its particles one at a
+// time, lane l < 27 adding the particle's share of node l into one float4, so
+// a lane holds one accumulator (64 registers, 8 CTAs per SM, against 168 and
+// 3 for the register runs of one particle per thread), and a run ends in one
+// warp instruction of 27 float4 reductions.  The price is separability: each
+// lane forms its node's weight and value from scratch, about 21 arithmetic
+// instructions per particle and node lane, where a register run shares the
+// axis weights and row sums among a thread's 27 nodes (about 8 per node).
+template <int NB, bool kAoS>
+__global__ void __launch_bounds__(kTransferThreads, 8) k_p2g_node(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                  float dt, uint32_t* __restrict__ err)
+{
+    node_runs<NB>(gv, gv.cur, n, [&](int64_t p, P2GParticle& q) { return load_p2g_particle<kAoS>(sp, pv, p, dt, q, err); },
+                  err);
+}
+
 // ---- group sums through shared memory ---------------------------------------
 // P2G_WXPOSE: a warp takes 32 consecutive particles, one per lane (the loads
 // are one full line per channel, with no reuse to keep in L1), and groups
@@ -701,8 +719,18 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n <= 0)
         return;
+    if (variant == P2G_NODE) {
+        constexpr int NB = 4;
+        const unsigned blocks = (unsigned)((n + 32 * NB * kNodeWarps - 1) / (32 * NB * kNodeWarps));
+        if (pv.aosoa)
+            k_p2g_node<NB, true><<<blocks, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+        else
+            k_p2g_node<NB, false><<<blocks, kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+        return;
+    }
     if (pv.aosoa) {
-        // the AoSoA store has register-run forms only (the context allows no other variant with it),
+        // the AoSoA store has register-run forms only besides P2G_NODE (the context allows no other
+        // variant with it),
         // in CTAs of 4 or 2 warps
         if (sp.cta_warps == 2) {
             const unsigned g = variant == P2G_CHUNK8 ? blocks_for((n + 7) / 8, 64) : blocks_for((n + 3) / 4, 64);

@@ -376,6 +376,122 @@ __device__ __forceinline__ void acc_flush(const GridView& gv, float4* target, co
                 atomicAdd(&target[si(i, j, k)], acc.a[i + 3 * j + 9 * k]);
 }
 
+// ---- node-parallel runs (P2G_NODE and its fused form) -----------------------
+// A warp walks 32 * NB consecutive particles of the cell-sorted order, 32 at
+// a time: each lane prepares one particle of the batch with prep(p, q) into
+// a 16-float record in shared memory (fraction f, mass, and the node value's
+// affine form m v + A (n - f) = c + A n with c = m v - A f, n = (i, j, k) the
+// node's offset from the base cell); then the warp takes the batch's
+// particles in order, and lane l < 27 adds each particle's contribution to
+// stencil node (l % 3, l / 3 % 3, l / 9) -- its weight, three quadratic
+// B-spline factors each written as a polynomial in f with the lane's
+// coefficients, times (c + A n, m) -- into one float4.  At a change of base
+// cell the node lanes issue one float4 reduction each into `target` (27
+// reductions in one warp instruction) and look up the new cell's node
+// addresses, which arrive while the next run is summed.  Runs carry over
+// from batch to batch: a warp reduces once per distinct cell of its range.
+constexpr int kNodeWarps = kTransferThreads / 32;
+
+template <int NB, class Prep>
+__device__ __forceinline__ void node_runs(const GridView& gv, float4* target, int64_t n, Prep prep,
+                                          uint32_t* __restrict__ err)
+{
+    __shared__ float4 s_rec[kNodeWarps][4][32];   // [warp][quarter of the record][particle of the batch]
+    __shared__ int s_key[kNodeWarps][32];          // base cell, x | y << 10 | z << 20 (res <= 1024); -1: skip
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t begin = ((int64_t)blockIdx.x * kNodeWarps + w) * (32 * NB);
+    if (begin >= n)
+        return;
+    const int64_t end = begin + 32 * NB < n ? begin + 32 * NB : n;
+    const int ni = lane % 3, nj = (lane / 3) % 3, nk = lane / 9;   // lanes 27-31: nk = 3, no node
+    const bool node_lane = lane < 27;
+    const float fi = (float)ni, fj = (float)nj, fk = (float)nk;
+    // weight of offset index i at fraction f: N_i(f) = (c2 f + c1) f + c0, the quadratic B-spline
+    // pieces 0.5 (1.5 - f)^2, 0.75 - (f - 1)^2 and 0.5 (f - 0.5)^2 expanded in f
+    auto coef = [](int i, float& c2, float& c1, float& c0) {
+        c2 = i == 1 ? -1.0f : 0.5f;
+        c1 = i == 0 ? -1.5f : (i == 1 ? 2.0f : -0.5f);
+        c0 = i == 0 ? 1.125f : (i == 1 ? -0.25f : 0.125f);
+    };
+    float cx2, cx1, cx0, cy2, cy1, cy0, cz2, cz1, cz0;
+    coef(ni, cx2, cx1, cx0);
+    coef(nj, cy2, cy1, cy0);
+    coef(nk, cz2, cz1, cz0);
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int cur = -1;          // base cell of the open run, -1: none
+    int pblk = -1, loc = 0; // the lane's node: physical block (from the table) and index in it
+    auto flush = [&]() {
+        if (node_lane) {
+            if (pblk < 0)
+                atomicOr(err, ST_MISSED);
+            else
+                atomicAdd(&target[(int64_t)pblk * 64 + loc], acc);
+        }
+    };
+#pragma unroll 1
+    for (int64_t base = begin; base < end; base += 32) {
+        const int64_t p = base + lane;
+        int key = -1;
+        float4 r0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), r1 = r0, r2 = r0, r3 = r0;
+        if (p < end) {
+            P2GParticle q;
+            if (prep(p, q)) {
+                key = q.b[0] | (q.b[1] << 10) | (q.b[2] << 20);
+                float c[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    c[a] = q.mv[a] - (q.A[3 * a] * q.f[0] + q.A[3 * a + 1] * q.f[1] + q.A[3 * a + 2] * q.f[2]);
+                r0 = make_float4(q.f[0], q.f[1], q.f[2], q.mp);
+                r1 = make_float4(c[0], c[1], c[2], q.A[0]);
+                r2 = make_float4(q.A[1], q.A[2], q.A[3], q.A[4]);
+                r3 = make_float4(q.A[5], q.A[6], q.A[7], q.A[8]);
+            }
+        }
+        __syncwarp();   // the previous batch is read
+        s_rec[w][0][lane] = r0;
+        s_rec[w][1][lane] = r1;
+        s_rec[w][2][lane] = r2;
+        s_rec[w][3][lane] = r3;
+        s_key[w][lane] = key;
+        __syncwarp();
+        const int cnt = end - base < 32 ? (int)(end - base) : 32;
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) {
+            const int k = s_key[w][j];
+            if (k < 0)
+                continue;
+            if (k != cur) {
+                if (cur >= 0)
+                    flush();
+                cur = k;
+                acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (node_lane) {
+                    const int x = (k & 1023) + ni, y = ((k >> 10) & 1023) + nj, z = (k >> 20) + nk;
+                    const uint32_t slot = spread3((uint32_t)(x >> 2)) | (spread3((uint32_t)(y >> 2)) << 1) |
+                                          (spread3((uint32_t)(z >> 2)) << 2);
+                    pblk = __ldg(&gv.table[slot]);
+                    loc = (x & 3) + 4 * (y & 3) + 16 * (z & 3);
+                }
+            }
+            const float4 a = s_rec[w][0][j], b = s_rec[w][1][j], c = s_rec[w][2][j], d = s_rec[w][3][j];
+            const float wx = fmaf(fmaf(cx2, a.x, cx1), a.x, cx0);
+            const float wy = fmaf(fmaf(cy2, a.y, cy1), a.y, cy0);
+            const float wz = fmaf(fmaf(cz2, a.z, cz1), a.z, cz0);
+            const float wt = wx * wy * wz;
+            // A = (b.w, c.x, c.y; c.z, c.w, d.x; d.y, d.z, d.w), node value c + A n
+            const float vx = fmaf(c.y, fk, fmaf(c.x, fj, fmaf(b.w, fi, b.x)));
+            const float vy = fmaf(d.x, fk, fmaf(c.w, fj, fmaf(c.z, fi, b.y)));
+            const float vz = fmaf(d.w, fk, fmaf(d.z, fj, fmaf(d.y, fi, b.z)));
+            acc.x = fmaf(wt, vx, acc.x);
+            acc.y = fmaf(wt, vy, acc.y);
+            acc.z = fmaf(wt, vz, acc.z);
+            acc.w = fmaf(wt, a.w, acc.w);
+        }
+    }
+    if (cur >= 0)
+        flush();
+}
+
 constexpr int kStageWaitIter = 1 << 16;
 
 // ---- warp-level reduction before the global reductions (Sec. 4.2.2) ----------

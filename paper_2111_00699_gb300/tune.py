@@ -93,7 +93,7 @@ def _p2g_g2p_ms(sim, dt, steps):
 def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) -> dict:
     """SoA (at `warps` warps per CTA) against the AoSoA store at 2 and at 4
     warps per CTA (the warp counts it runs), timing P2G + G2P per substep;
-    keeps the fastest.  Needs the register-run P2G (variant 3 or 4) and the
+    keeps the fastest.  Needs the register-run P2G (variant 3, 4 or 14) and the
     64-register G2P (4 or 7) already selected; otherwise the store stays SoA.
     Returns {"best": "soa" | "aosoa", "ms": {...}, "cta_warps": the warps kept}."""
     ms = {"soa": float("inf"), "aosoa_2": float("inf"), "aosoa_4": float("inf")}

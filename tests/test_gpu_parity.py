@@ -223,7 +223,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", list(range(14)))
+@pytest.mark.parametrize("variant", list(range(15)))
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -248,7 +248,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", list(range(14)))
+@pytest.mark.parametrize("variant", list(range(15)))
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -692,7 +692,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
 
 
 @pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4), (3, 5),
-                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7), (13, 4)])
+                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7), (13, 4), (14, 4)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
@@ -742,7 +742,8 @@ def test_aosoa_layout_keeps_parity(M):
     """The AoSoA particle store (packets of 32): converted from SoA mid-run,
     10 substeps against the oracle, particles added under AoSoA (capacity
     growth and a rebuild), 10 more, converted back, 10 more; the state reads
-    back in insertion order throughout.  Forms AoSoA lacks are refused."""
+    back in insertion order throughout (the node-parallel P2G for 5 of the
+    substeps).  Forms AoSoA lacks are refused."""
     x, _ = scenes.blocks(17, 12000, 64, 2)
     gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
     rng = np.random.default_rng(6)
@@ -773,6 +774,10 @@ def test_aosoa_layout_keeps_parity(M):
         assert linf(g["x"], s.x) <= 1e-4
         assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
         sim.set_cta_warps(4)
+        sim.set_p2g_variant(14)   # the node-parallel runs on the AoSoA store
+        g = _run_both(M, sim, [om], s, 5, 1e-4, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
         sim.set_layout(False)
         sim.set_p2g_variant(0)
         g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
