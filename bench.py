@@ -648,7 +648,7 @@ KERNEL_NAMES = {"P2G": {"direct": "k_p2g_direct", "strided": "k_p2g_strided", "t
                         "stage8": "k_p2g_stage<8>", "sacc4": "k_p2g_chunk<4, 1, 0, 0>", "slab4": "k_p2g_slab<4>",
                         "warp": "k_p2g_warp<1>", "warprun": "k_p2g_warp<0>", "wtile8": "k_p2g_wtile<8>",
                         "wxpose": "k_p2g_wxpose", "chunk8x2": "k_p2g_chunk<8, 0, 0, 1>",
-                        "node": "k_p2g_node<4, 0>"},
+                        "node": "k_p2g_node<4, 0>", "chunk8s": "k_p2g_chunks<8, 0>"},
                 "G2P": {"direct": "k_g2p", "chunk4": "k_g2p_chunk<4>", "chunk8": "k_g2p_chunk<8>", "tile": "k_g2p_tile",
                         # the bench scene has one material (snow, kind 2): the kernels specialised to it
                         "occ": "k_g2p_occ<8, 2, 128, 0, 0>", "stage": "k_g2p_stage",
@@ -675,6 +675,8 @@ def p2g_kernel_name(variant, aosoa, warps):
         return "k_p2g_chunk<%s, 0, %d, 0>" % (k, int(aosoa))
     if variant == "node":
         return "k_p2g_node<4, %d>" % int(aosoa)
+    if variant == "chunk8s":
+        return "k_p2g_chunks<8, %d>" % int(aosoa)
     return KERNEL_NAMES["P2G"][variant]
 
 
@@ -739,7 +741,7 @@ def main():
     ap.add_argument("--e2e-frames", type=int, default=3)
     ap.add_argument("--p2g-variant", type=int, default=-1,
                     help="P2G scatter variant (0 direct, 1 strided, 2 tile, 3 chunk4, 4 chunk8, 5 stage4, "
-                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose, 13 chunk8x2, 14 node); -1 = autotune")
+                         "6 stage8, 7 sacc4, 8 slab4, 9 warp, 10 warprun, 11 wtile8, 12 wxpose, 13 chunk8x2, 14 node, 15 chunk8s); -1 = autotune")
     ap.add_argument("--g2p-variant", type=int, default=-1,
                     help="G2P gather variant (0 direct, 1 chunk4, 2 chunk8, 3 tile, 4 occ, 5 stage, 6 occ10, "
                          "7 occsw); -1 = autotune")
@@ -747,7 +749,9 @@ def main():
                     help="profiler mode: run this many substeps of the snow scene with the given variants "
                          "(default chunk4 P2G, occ G2P), print one status line and exit; no timing")
     ap.add_argument("--aosoa", type=int, default=0, choices=[0, 1],
-                    help="profiler mode: 1 = AoSoA particle store (P2G variant 3/4, G2P 4/7)")
+                    help="profiler mode: 1 = AoSoA particle store (P2G variant 3/4/14/15, G2P 4/6/7)")
+    ap.add_argument("--resort-interval", type=int, default=RESORT_INTERVAL,
+                    help="profiler mode: window re-sort every this many substeps (0: off)")
     ap.add_argument("--cta-warps", type=int, default=4, choices=[2, 4, 8],
                     help="profiler mode: warps per CTA of the register-run P2G and the 64-register G2P")
     ap.add_argument("--g2p2g", type=int, default=None, choices=[0, 1],
@@ -764,7 +768,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2111_00699_gb300 import build, mpm, scenes
+    from paper_2111_00699_gb300 import _lib, build, mpm, scenes
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -802,6 +806,7 @@ def main():
         sim.set_g2p2g(bool(args.g2p2g))
         sim.set_cta_warps(args.cta_warps)
         sim.set_layout(bool(args.aosoa))
+        sim.set_resort_interval(args.resort_interval)
         sim.run(args.profile_substeps, DT)
         sim.sync()
         if rank == 0:
@@ -839,10 +844,19 @@ def main():
     warm -= 132
     tuned_l = tune.tune_layout(sim, DT, tuned_w["best"], steps=20, rounds=2)   # advances 132 substeps
     warm -= 132
+    # the P2G variant with the window re-sort interval, on whole substeps: the tuned variant with
+    # re-sorts every 64 or 128 substeps against the drift-tolerant sorted chunks with and without
+    sorted_chunks = _lib.P2G_VARIANTS.index("chunk8s")
+    tuned_o = {"best": (tuned["best"], RESORT_INTERVAL), "ms": None}
+    if args.p2g_variant < 0:
+        tuned_o = tune.tune_order(sim, DT, [(tuned["best"], RESORT_INTERVAL), (tuned["best"], 2 * RESORT_INTERVAL),
+                                            (sorted_chunks, 0), (sorted_chunks, 2 * RESORT_INTERVAL)],
+                                   slice_steps=256, rounds=2)
+        warm -= 8 * 256
     # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene;
     # the fused kernel's scatter follows the P2G variant (direct, chunk4, chunk8)
     fused_ms, fused_scatter_ms = {}, {}
-    p2g_separate = tuned["best"] if tuned["best"] >= 0 else 3
+    p2g_separate = tuned_o["best"][0] if tuned_o["best"][0] >= 0 else 3
     aosoa = tuned_l["best"] == "aosoa"
     g2p_final = tuned_l.get("aosoa_g2p_variant", tuned_g["best"]) if aosoa else tuned_g["best"]
     for _ in range(2):
@@ -1008,6 +1022,8 @@ def main():
             "data": "synthetic", "config": workload_config(n, world),
             "clocks": dict(clk.summary(), window="autotuning, warm-up and timed substeps"),
             "p2g_variant": tuned, "g2p_variant": tuned_g, "cta_warps": tuned_w, "layout": tuned_l,
+            "order": {"p2g_variant": _variant_name("P2G", tuned_o["best"][0]), "resort_interval": tuned_o["best"][1],
+                      "ms_per_substep": tuned_o["ms"]},
             "transfer": {"mode": "g2p2g" if use_fused else "separate", "ms_per_substep": fused_ms,
                          "g2p2g_scatter_ms": fused_scatter_ms, "p2g_variant_used": _variant_name("P2G", p2g_final)}, "e2e": e2e, "gpu_launches": launches, "rebuilds_in_timed_region": rebuilds,
             "n_pblocks": n_pblocks, "roofline": roofline, "cpu_baseline": cpu, "workloads": workloads}

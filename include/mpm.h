@@ -119,7 +119,8 @@ typedef struct {
                               paired FP32 fused multiply-adds, 14 a warp per run of particles
                               with one lane per stencil node, taking the particles one at a
                               time into one float4 per lane and reducing the 27 nodes at each
-                              change of cell (see the autotuner) */
+                              change of cell, 15 as 4 with each thread's 8 particles taken
+                              in the order of their base cells (see the autotuner) */
     int32_t g2p_variant;   /* tuning: 0 thread per particle, 1/2 node velocities cached in
                               registers over runs of 4/8 particles, 3 grid tile staged
                               in shared memory per CTA, 4 thread per particle at 64
@@ -366,7 +367,7 @@ mpm_status mpm_set_g2p_variant(mpm_ctx* ctx, int variant);
  * one array per state channel (the default); 1 = AoSoA, packets of 32
  * particles with each channel's 32 floats contiguous inside the packet, so a
  * warp's particles keep their whole state in one 4 KB span.  The current
- * particles are converted on the stream.  AoSoA runs P2G variants 3, 4 and 14,
+ * particles are converted on the stream.  AoSoA runs P2G variants 3, 4, 14 and 15,
  * G2P variants 4, 6 and 7, 2 or 4 warps per CTA and separate APIC transfers only: switching
  * to it from another configuration, or to another configuration under it,
  * returns MPM_EINVAL.  Results are identical up to float summation order. */
@@ -377,6 +378,11 @@ mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa);
  * other variants keep their own CTA sizes.  Results are identical up to float
  * summation order.  MPM_EINVAL for other values. */
 mpm_status mpm_set_cta_warps(mpm_ctx* ctx, int warps);
+/* Change mpm_config.resort_interval between substeps (the window re-sort that
+ * restores P2G's runs of equal cells between the sorts of Sec. 4.2.2; 0 turns
+ * it off); used by the autotuner.  Results are identical up to float
+ * summation order.  MPM_EINVAL for a negative interval. */
+mpm_status mpm_set_resort_interval(mpm_ctx* ctx, int interval);
 /* Switch between separate phases (0) and the fused G2P2G transfer (1)
  * between substeps (mpm_config.use_g2p2g).  MPM_EINVAL for on = 1 when the
  * context uses MPM_ASFLIP.  The fused kernel scatters the next substep's

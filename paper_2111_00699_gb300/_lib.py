@@ -25,7 +25,7 @@ APIC, ASFLIP = 0, 1
 PHASES = 4
 SORT_NOALLOC_MAX_KEYS = 1 << 20
 P2G_VARIANTS = ("direct", "strided", "tile", "chunk4", "chunk8", "stage4", "stage8", "sacc4", "slab4", "warp",
-                "warprun", "wtile8", "wxpose", "chunk8x2", "node")
+                "warprun", "wtile8", "wxpose", "chunk8x2", "node", "chunk8s")
 G2P_VARIANTS = ("direct", "chunk4", "chunk8", "tile", "occ", "stage", "occ10", "occsw")
 
 
@@ -88,6 +88,7 @@ _PROTOS = {
     "mpm_debug_p2g": (I, [P, F, P, I]),
     "mpm_set_p2g_variant": (I, [P, I]),
     "mpm_set_cta_warps": (I, [P, I]),
+    "mpm_set_resort_interval": (I, [P, I]),
     "mpm_set_layout": (I, [P, I]),
     "mpm_set_g2p_variant": (I, [P, I]),
     "mpm_set_g2p2g": (I, [P, I]),

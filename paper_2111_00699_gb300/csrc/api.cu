@@ -1253,8 +1253,9 @@ mpm_status mpm_set_p2g_variant(mpm_ctx* ctx, int variant)
 {
     if (!ctx || variant < 0 || variant >= kP2GVariants)
         return MPM_EINVAL;
-    if (ctx->aosoa && variant != P2G_CHUNK4 && variant != P2G_CHUNK8 && variant != P2G_NODE)
-        return fail(ctx, MPM_EINVAL, "mpm_set_p2g_variant: the AoSoA layout has P2G variants 3, 4 and 14 only");
+    if (ctx->aosoa && variant != P2G_CHUNK4 && variant != P2G_CHUNK8 && variant != P2G_NODE &&
+        variant != P2G_CHUNK8S)
+        return fail(ctx, MPM_EINVAL, "mpm_set_p2g_variant: the AoSoA layout has P2G variants 3, 4, 14 and 15 only");
     ctx->cfg.p2g_variant = variant;
     drop_graphs(ctx);
     return MPM_OK;
@@ -1267,13 +1268,13 @@ mpm_status mpm_set_layout(mpm_ctx* ctx, int aosoa)
     if (aosoa == ctx->aosoa)
         return MPM_OK;
     if (aosoa && ((ctx->cfg.p2g_variant != P2G_CHUNK4 && ctx->cfg.p2g_variant != P2G_CHUNK8 &&
-                   ctx->cfg.p2g_variant != P2G_NODE) ||
+                   ctx->cfg.p2g_variant != P2G_NODE && ctx->cfg.p2g_variant != P2G_CHUNK8S) ||
                   (ctx->cfg.g2p_variant != G2P_OCC && ctx->cfg.g2p_variant != G2P_OCCSW &&
                    ctx->cfg.g2p_variant != G2P_OCC10) || ctx->cfg.use_g2p2g ||
                   ctx->cfg.transfer != MPM_APIC ||
                   ctx->sp.cta_warps == 8))
         return fail(ctx, MPM_EINVAL,
-                    "mpm_set_layout: AoSoA needs P2G variant 3, 4 or 14, G2P variant 4, 6 or 7, separate APIC transfers and "
+                    "mpm_set_layout: AoSoA needs P2G variant 3, 4, 14 or 15, G2P variant 4, 6 or 7, separate APIC transfers and "
                     "2 or 4 warps per CTA");
     // convert the current particles into the other buffer, then make it current
     PartView dst = ctx->pv[1 - ctx->cur];
@@ -1299,6 +1300,14 @@ mpm_status mpm_set_cta_warps(mpm_ctx* ctx, int warps)
         return fail(ctx, MPM_EINVAL, "mpm_set_cta_warps: the AoSoA layout runs 2 or 4 warps per CTA only");
     ctx->sp.cta_warps = warps;
     drop_graphs(ctx);
+    return MPM_OK;
+}
+
+mpm_status mpm_set_resort_interval(mpm_ctx* ctx, int interval)
+{
+    if (!ctx || interval < 0)
+        return MPM_EINVAL;
+    ctx->cfg.resort_interval = interval;   // read on the host before each substep; no graph holds it
     return MPM_OK;
 }
 

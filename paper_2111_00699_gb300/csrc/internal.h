@@ -39,7 +39,8 @@ enum P2GVariant : int {
     P2G_WXPOSE = 12,  // thread per particle, lanes grouped by base cell, group sums through shared memory
     P2G_CHUNK8X2 = 13, // CHUNK8 accumulating with paired FP32 fused multiply-adds
     P2G_NODE = 14,    // warp per run of particles, one lane per stencil node
-    kP2GVariants = 15
+    P2G_CHUNK8S = 15, // CHUNK8 with each thread's particles taken in base-cell order
+    kP2GVariants = 16
 };
 
 // Particle capacity is a multiple of this, so that a staged tile of

@@ -132,7 +132,58 @@ __global__ void __launch_bounds__(kTileThreads) k_p2g_tile(SimParams sp, PartVie
 }
 
 
-template <int K, bool kSmem, bool kAoS = false, bool kX2 = false>
+// With kSort, the order in which a thread takes its K particles, packed 4 bits
+// per step: sorted by base cell (a bitonic network over the K keys), so that
+// particles that drifted into a cell since the last sort join its run instead
+// of splitting it.  Without kSort the storage order is taken (and 0 returned).
+template <int K, bool kSort, bool kAoS>
+__device__ __forceinline__ uint32_t chunk_order(const SimParams& sp, const PartView& pv, int64_t p0, int64_t n)
+{
+    static_assert(K <= 8, "4 bits per step");
+    uint32_t order = 0;
+    if constexpr (kSort) {
+        uint32_t key[K];
+        int idx[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            idx[j] = j;
+            key[j] = 0xffffffffu;   // past the end: last
+            if (p0 + j < n) {
+                int b[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    b[a] = base_of(pch<kAoS>(pv, CH_X + a, p0 + j), sp.inv_dx);
+                key[j] = ((uint32_t)b[0] & 1023u) | (((uint32_t)b[1] & 1023u) << 10) | (((uint32_t)b[2] & 1023u) << 20);
+            }
+        }
+#pragma unroll
+        for (int size = 2; size <= K; size <<= 1)
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const int l = i ^ stride;
+                    if (l > i) {
+                        const bool up = (i & size) == 0;
+                        if ((key[i] > key[l]) == up) {
+                            const uint32_t tk = key[i];
+                            key[i] = key[l];
+                            key[l] = tk;
+                            const int ti = idx[i];
+                            idx[i] = idx[l];
+                            idx[l] = ti;
+                        }
+                    }
+                }
+        order = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            order |= (uint32_t)idx[j] << (4 * j);
+    }
+    return order;
+}
+
+template <int K, bool kSmem, bool kAoS = false, bool kX2 = false, bool kSort = false>
 __device__ __forceinline__ void p2g_chunk_body(const SimParams& sp, const PartView& pv, const GridView& gv, int64_t n,
                                                float dt, uint32_t* __restrict__ err)
 {
@@ -140,6 +191,7 @@ __device__ __forceinline__ void p2g_chunk_body(const SimParams& sp, const PartVi
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K;
     if (p0 >= n)
         return;
+    const uint32_t order = chunk_order<K, kSort, kAoS>(sp, pv, p0, n);
     typename std::conditional<kSmem, SmemAcc, NodeAcc>::type acc;
     if constexpr (kSmem)
         acc.base = sacc + threadIdx.x;
@@ -148,7 +200,7 @@ __device__ __forceinline__ void p2g_chunk_body(const SimParams& sp, const PartVi
     bool open = false;
 #pragma unroll 1
     for (int j = 0; j < K; ++j) {
-        int64_t p = p0 + j;
+        int64_t p = p0 + (kSort ? (int)((order >> (4 * j)) & 15u) : j);
         if (p >= n)
             break;
         P2GParticle q;
@@ -180,6 +232,19 @@ __global__ void __launch_bounds__(kTransferThreads, kSmem ? 4 : 3) k_p2g_chunk(S
                                                                               uint32_t* __restrict__ err)
 {
     p2g_chunk_body<K, kSmem, kAoS, kX2>(sp, pv, gv, n, dt, err);
+}
+
+// P2G_CHUNK8S: the register runs of 8 with each thread's chunk taken in the
+// order of its particles' base cells.  Between sorts particles drift across
+// cell faces, so the storage order interleaves a cell's particles with a few
+// that moved in from next door and each of those splits a run; sorting the 8
+// keys in registers (a bitonic network, about 100 instructions per chunk)
+// makes every cell of the chunk one run.
+template <int K, bool kAoS>
+__global__ void __launch_bounds__(kTransferThreads, 3) k_p2g_chunks(SimParams sp, PartView pv, GridView gv, int64_t n,
+                                                                    float dt, uint32_t* __restrict__ err)
+{
+    p2g_chunk_body<K, false, kAoS, false, true>(sp, pv, gv, n, dt, err);
 }
 
 // The same register runs in CTAs of 2 or 8 warps instead of 4 (the paper's
@@ -719,6 +784,13 @@ void launch_p2g(const SimParams& sp, const PartView& pv, const GridView& gv, int
 {
     if (n <= 0)
         return;
+    if (variant == P2G_CHUNK8S) {
+        if (pv.aosoa)
+            k_p2g_chunks<8, true><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+        else
+            k_p2g_chunks<8, false><<<blocks_for((n + 7) / 8, kTransferThreads), kTransferThreads, 0, s>>>(sp, pv, gv, n, dt, err);
+        return;
+    }
     if (variant == P2G_NODE) {
         constexpr int NB = 4;
         const unsigned blocks = (unsigned)((n + 32 * NB * kNodeWarps - 1) / (32 * NB * kNodeWarps));

@@ -245,6 +245,10 @@ class Simulator:
         """Warps per CTA (2, 4 or 8) of the register-run P2G and the 64-register G2P."""
         _check(load().mpm_set_cta_warps(self._ctx, int(warps)), self._ctx)
 
+    def set_resort_interval(self, interval: int):
+        """Window re-sort every `interval` substeps between rebuilds (0: off)."""
+        _check(load().mpm_set_resort_interval(self._ctx, int(interval)), self._ctx)
+
     def set_layout(self, aosoa: bool):
         """Particle store layout: False SoA (default), True AoSoA in packets of 32."""
         _check(load().mpm_set_layout(self._ctx, 1 if aosoa else 0), self._ctx)

@@ -93,7 +93,7 @@ def _p2g_g2p_ms(sim, dt, steps):
 def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) -> dict:
     """SoA (at `warps` warps per CTA) against the AoSoA store at 2 and at 4
     warps per CTA (the warp counts it runs), timing P2G + G2P per substep;
-    keeps the fastest.  Needs the register-run P2G (variant 3, 4 or 14) and the
+    keeps the fastest.  Needs the register-run P2G (variant 3, 4, 14 or 15) and the
     64-register G2P (4 or 7) already selected; otherwise the store stays SoA.
     Returns {"best": "soa" | "aosoa", "ms": {...}, "cta_warps": the warps kept}."""
     ms = {"soa": float("inf"), "aosoa_2": float("inf"), "aosoa_4": float("inf")}
@@ -128,3 +128,43 @@ def tune_layout(sim, dt: float, warps: int, steps: int = 50, rounds: int = 2) ->
     sim.set_g2p_variant(g2p_best)
     return {"best": "aosoa", "ms": ms, "cta_warps": w, "aosoa_g2p_ms": g2p_ms,
             "aosoa_g2p": _lib.G2P_VARIANTS[g2p_best], "aosoa_g2p_variant": g2p_best}
+
+
+def _substep_ms(sim, dt, steps):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sim.sync()
+    e0.record(sim.stream)
+    sim.run(steps, dt)
+    e1.record(sim.stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune_order(sim, dt: float, candidates, slice_steps: int = 256, rounds: int = 2) -> dict:
+    """Whole-substep time of each (P2G variant, window re-sort interval) pair
+    in `candidates`, and keep the fastest.  The re-sort restores P2G's runs of
+    equal cells between rebuilds at a cost of its own, and the variants differ
+    in how they suffer from the drift it undoes, so the pair is timed on whole
+    substeps over slices longer than the intervals.  The slices run in the
+    order A B C ... then ... C B A, so that every pair's slices sit at the same
+    mean time of the run and the scene's evolution favours none.
+    Returns {"best": (variant, interval), "best_name", "ms": {name: ms per substep}}."""
+    def name(c):
+        return "%s, re-sort every %d" % (_lib.P2G_VARIANTS[c[0]], c[1]) if c[1] else \
+            "%s, no re-sort" % _lib.P2G_VARIANTS[c[0]]
+    cands = list(dict.fromkeys(candidates))
+    seq = []
+    for r in range(rounds):
+        seq += cands if r % 2 == 0 else cands[::-1]
+    ms = {c: [] for c in cands}
+    for c in seq:
+        sim.set_p2g_variant(c[0])
+        sim.set_resort_interval(c[1])
+        ms[c].append(_substep_ms(sim, dt, slice_steps))
+    avg = {c: sum(v) / len(v) for c, v in ms.items()}
+    best = min(cands, key=avg.get)
+    sim.set_p2g_variant(best[0])
+    sim.set_resort_interval(best[1])
+    return {"best": best, "best_name": name(best), "ms": {name(c): avg[c] for c in cands}}

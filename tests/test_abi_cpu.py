@@ -89,7 +89,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     bad.g2p_variant = 8
     assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad = _lib.Config.from_buffer_copy(cfg)
-    bad.p2g_variant = 15
+    bad.p2g_variant = 16
     assert lib.mpm_create(ctypes.byref(bad), mats, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL
     bad_mat = (_lib.Material * 1)(_lib.material(7))
     assert lib.mpm_create(ctypes.byref(cfg), bad_mat, 1, None, None, ctypes.byref(ctx)) == _lib.MPM_EINVAL

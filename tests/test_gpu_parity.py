@@ -223,7 +223,7 @@ def _p2g_parity(M, sim, gm_list, om_list, x, vol, dt, res, mat_ids=None, tol=1e-
     assert abs(g[..., 0].sum() - mass_p) <= 1e-6 * mass_p
 
 
-@pytest.mark.parametrize("variant", list(range(15)))
+@pytest.mark.parametrize("variant", list(range(16)))
 def test_p2g_grid_small_elastic(M, variant):
     x = scenes.cube_uniform(0, 8192, 0.4, 0.6)
     vol = 0.008 / 8192
@@ -682,6 +682,9 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
         res = tune.tune_g2p(sim, 1e-4, steps=2, rounds=1)
         assert res["best"] in range(len(_lib.G2P_VARIANTS)) and len(res["ms"]) == len(_lib.G2P_VARIANTS)
         assert all(v > 0 for v in res["ms"].values())
+        res = tune.tune_order(sim, 1e-4, [(4, 2), (15, 0), (4, 2)], slice_steps=3, rounds=2)
+        assert res["best"] in ((4, 2), (15, 0)) and len(res["ms"]) == 2
+        assert all(v > 0 for v in res["ms"].values())
         ran = sim.stats()["substeps"]
         s = orc.State(x.astype(np.float64), vol=vol)
         for _ in range(ran):
@@ -692,7 +695,7 @@ def test_autotuner_picks_a_variant_and_keeps_parity(M):
 
 
 @pytest.mark.parametrize("p2g,g2p", [(0, 0), (1, 1), (2, 2), (3, 1), (4, 2), (4, 0), (3, 3), (4, 4), (5, 0), (6, 4), (3, 5),
-                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7), (13, 4), (14, 4)])
+                                     (5, 5), (7, 4), (3, 6), (8, 4), (9, 4), (10, 0), (11, 4), (4, 7), (12, 7), (13, 4), (14, 4), (15, 7)])
 def test_substeps_variant_combinations(M, p2g, g2p):
     """Every P2G / G2P launch variant computes the same substep (10 substeps
     of a moving, deforming elastic block against the oracle)."""
@@ -949,10 +952,11 @@ def test_graph_replay_matches_oracle(M):
 
 @pytest.mark.parametrize("graphs", [False, True])
 def test_window_resort_matches_oracle(M, graphs):
-    """Window re-sorts every 2 substeps (with and without graph replay, whose
-    graphs are keyed by the particle buffer a re-sort switches to): the
-    substeps match the oracle, the state reads back in insertion order, and
-    rebuilds still happen when a fast block leaves its mapped blocks."""
+    """Window re-sorts every 2 substeps, then none, then every 3 (with and
+    without graph replay, whose graphs are keyed by the particle buffer a
+    re-sort switches to): the substeps match the oracle, the state reads back
+    in insertion order, and rebuilds still happen when a fast block leaves its
+    mapped blocks."""
     x = scenes.cube_uniform(4, 3000, 0.3, 0.4)
     gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1000.0)
     rng = np.random.default_rng(13)
@@ -963,7 +967,14 @@ def test_window_resort_matches_oracle(M, graphs):
     with M.Simulator(64, 1 / 64, [gm], boundary=M.SLIP, stream=torch.cuda.Stream(), graphs=graphs,
                      resort_interval=2) as sim:
         sim.add_particles(x, v=v)
-        g = _run_both(M, sim, [om], s, 40, 1e-4, cfg)
+        g = _run_both(M, sim, [om], s, 20, 1e-4, cfg)
+        assert linf(g["x"], s.x) <= 1e-4
+        sim.set_resort_interval(0)   # off, then every 3 substeps
+        g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
+        sim.set_resort_interval(3)
+        g = _run_both(M, sim, [om], s, 10, 1e-4, cfg)
+        with pytest.raises(M.MpmError):
+            sim.set_resort_interval(-1)
         stats = sim.stats()
     assert linf(g["x"], s.x) <= 1e-4
     assert linf(g["v"], s.v) <= 1e-4 * np.abs(s.v).max()
