@@ -839,12 +839,7 @@ def main():
         warm -= 120
     else:
         sim.set_g2p_variant(args.g2p_variant)
-    # warps per CTA of the register-run P2G and the 64-register G2P, then the particle store layout
-    tuned_w = tune.tune_cta_warps(sim, DT, steps=20, rounds=2)  # advances 132 substeps
-    warm -= 132
-    tuned_l = tune.tune_layout(sim, DT, tuned_w["best"], steps=20, rounds=2)   # advances 132 substeps
-    warm -= 132
-    # the P2G variant with the window re-sort interval, on whole substeps: the tuned variant with
+    # then the P2G variant with the window re-sort interval, on whole substeps: the tuned variant with
     # re-sorts every 64 or 128 substeps against the drift-tolerant sorted chunks with and without
     sorted_chunks = _lib.P2G_VARIANTS.index("chunk8s")
     tuned_o = {"best": (tuned["best"], RESORT_INTERVAL), "ms": None}
@@ -853,6 +848,11 @@ def main():
                                             (sorted_chunks, 0), (sorted_chunks, 2 * RESORT_INTERVAL)],
                                    slice_steps=256, rounds=2)
         warm -= 8 * 256
+    # warps per CTA of the register-run P2G and the 64-register G2P, then the particle store layout
+    tuned_w = tune.tune_cta_warps(sim, DT, steps=20, rounds=2)  # advances 132 substeps
+    warm -= 132
+    tuned_l = tune.tune_layout(sim, DT, tuned_w["best"], steps=20, rounds=2)   # advances 132 substeps
+    warm -= 132
     # separate phases vs the fused G2P2G transfer (Sec. 4.1), timed on this scene;
     # the fused kernel's scatter follows the P2G variant (direct, chunk4, chunk8)
     fused_ms, fused_scatter_ms = {}, {}
@@ -938,7 +938,8 @@ def main():
     if use_fused:
         # per substep: grid update + k_g2p2g (reads x F Jp vol mat 57 B, writes x v C F Jp 100 B)
         algo["g2p"] = 157 * n_now
-    kernel_name = {"p2g": p2g_kernel_name(tuned["best_name"], aosoa and not use_fused, tuned_l["cta_warps"]),
+    kernel_name = {"p2g": p2g_kernel_name(_variant_name("P2G", p2g_separate), aosoa and not use_fused,
+                                          tuned_l["cta_warps"]),
                    "g2p": (FUSED_KERNEL_NAMES[p2g_final] if use_fused
                            else g2p_kernel_name(_variant_name("G2P", g2p_final), aosoa, tuned_l["cta_warps"])),
                    "grid": "k_grid"}[dom]
