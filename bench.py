@@ -839,15 +839,18 @@ def main():
         warm -= 120
     else:
         sim.set_g2p_variant(args.g2p_variant)
-    # then the P2G variant with the window re-sort interval, on whole substeps: the tuned variant with
-    # re-sorts every 64 or 128 substeps against the drift-tolerant sorted chunks with and without
+    # then the P2G variant with the window re-sort interval, on whole substeps: the tuned variant and
+    # the register runs of 8 with re-sorts every 64 (or 128) substeps against the drift-tolerant
+    # sorted chunks with and without
     sorted_chunks = _lib.P2G_VARIANTS.index("chunk8s")
+    chunk8 = _lib.P2G_VARIANTS.index("chunk8")
     tuned_o = {"best": (tuned["best"], RESORT_INTERVAL), "ms": None}
     if args.p2g_variant < 0:
-        tuned_o = tune.tune_order(sim, DT, [(tuned["best"], RESORT_INTERVAL), (tuned["best"], 2 * RESORT_INTERVAL),
-                                            (sorted_chunks, 0), (sorted_chunks, 2 * RESORT_INTERVAL)],
-                                   slice_steps=256, rounds=2)
-        warm -= 8 * 256
+        cands = list(dict.fromkeys([(tuned["best"], RESORT_INTERVAL), (chunk8, RESORT_INTERVAL),
+                                    (chunk8, 2 * RESORT_INTERVAL), (sorted_chunks, 0),
+                                    (sorted_chunks, 2 * RESORT_INTERVAL)]))
+        tuned_o = tune.tune_order(sim, DT, cands, slice_steps=256, rounds=2)
+        warm -= 2 * len(cands) * 256
     # warps per CTA of the register-run P2G and the 64-register G2P, then the particle store layout
     tuned_w = tune.tune_cta_warps(sim, DT, steps=20, rounds=2)  # advances 132 substeps
     warm -= 132
