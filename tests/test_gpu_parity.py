@@ -233,6 +233,20 @@ def test_p2g_grid_small_elastic(M, variant):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
+@pytest.mark.parametrize("variant", list(range(16)))
+def test_p2g_grid_ragged_tail(M, variant):
+    """A particle count that is no multiple of a chunk (4, 8), a warp, a
+    batch of the node-parallel form or a CTA: the last thread's, warp's and
+    CTA's ranges end early."""
+    n = 8192 - 3
+    x = scenes.cube_uniform(3, n, 0.4, 0.6)
+    vol = 0.008 / n
+    gm, om = mats_pair(M, M.ELASTIC, E=1e4, nu=0.2, rho=1.0)
+    with M.Simulator(64, 1 / 64, [gm], p2g_variant=variant) as sim:
+        sim.add_particles(x, vol=np.full(len(x), vol, np.float32))
+        _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
+
+
 @pytest.mark.parametrize("kind", ["snow", "fluid", "sand"])
 def test_p2g_grid_materials(M, kind):
     kw = dict(snow=dict(kind=M.SNOW, E=1.4e5, nu=0.2, rho=400.0), fluid=dict(kind=M.FLUID, E=1e4, rho=1000.0),
@@ -248,7 +262,7 @@ def test_p2g_grid_materials(M, kind):
         _p2g_parity(M, sim, [gm], [om], x, vol, 1e-4, 64)
 
 
-@pytest.mark.parametrize("variant", list(range(15)))
+@pytest.mark.parametrize("variant", list(range(16)))
 def test_p2g_grid_snow_full_size(M, variant):
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
@@ -653,7 +667,7 @@ def test_host_buffers_and_side_stream(M):
     assert linf(host["v"].numpy(), s.v) <= 1e-4 * np.abs(s.v).max()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 9, 10, 11, 12])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 9, 10, 11, 12, 13, 14, 15])
 def test_p2g_sparse_cloud_tile_fallback(M, variant):
     """Particles spread over the whole domain: each 256-particle tile's box is
     far larger than the shared-memory tile, so the tile variants take their
