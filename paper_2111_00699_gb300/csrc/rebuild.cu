@@ -60,46 +60,86 @@ __global__ void k_keys(SimParams sp, PartView pv, int64_t n, uint32_t* __restric
 // buffer.  Particles drift across cell faces long before they leave the
 // mapped blocks, and P2G merges only runs of consecutive particles in one
 // cell; this restores the runs without a global sort or a host round trip.
-// Ties keep no particular order (bitonic sort), which changes only the
-// order of floating-point sums.
+// Equal keys keep their storage order (the sort key is (key, slot)).
+//
+// The sort is a bitonic network over (key << 32 | slot) with 4 elements per
+// thread in registers: the compare-exchanges at strides 1 and 2 stay inside a
+// thread, those at strides 4 to 64 pair lanes of one warp (shuffles), and
+// only the 6 steps at strides 128 to 512 go through shared memory and a
+// barrier (against 55 barrier steps for a network held in shared memory).
 constexpr int kResortThreads = 256;
+constexpr int kResortPer = kResortWindow / kResortThreads;   // elements per thread
 
-__global__ void __launch_bounds__(kResortThreads) k_resort_window(SimParams sp, PartView src, PartView dst, int64_t n)
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int mask)
 {
-    __shared__ uint32_t key[kResortWindow];
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, mask);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), mask);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__global__ void __launch_bounds__(kResortThreads, 4) k_resort_window(SimParams sp, PartView src, PartView dst, int64_t n)
+{
+    static_assert(kResortPer == 4 && kResortThreads % 32 == 0, "4 elements per thread");
+    __shared__ uint64_t xch[kResortWindow];
     __shared__ uint16_t idx[kResortWindow];
     const int tid = threadIdx.x;
     const int64_t p0 = (int64_t)blockIdx.x * kResortWindow;
-    for (int i = tid; i < kResortWindow; i += kResortThreads) {
+    uint64_t v[kResortPer];
+#pragma unroll
+    for (int e = 0; e < kResortPer; ++e) {
+        const int i = kResortPer * tid + e;
         const int64_t p = p0 + i;
         uint32_t k = 0xffffffffu;                       // padding past n sorts last
         if (p < n)
             k = min(particle_key(sp, src, p), 0xfffffffeu);
-        key[i] = k;
-        idx[i] = (uint16_t)i;
+        v[e] = ((uint64_t)k << 32) | (uint32_t)i;
     }
-    __syncthreads();
-    // bitonic sort of (key, idx), ascending
+    // element i = 4 tid + e is compared with i ^ stride; blocks of `size` with (i & size) == 0 ascend
+#pragma unroll
     for (int size = 2; size <= kResortWindow; size <<= 1) {
+#pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = tid; t < kResortWindow / 2; t += kResortThreads) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const uint32_t a = key[lo], b = key[hi];
-                const bool swap = up ? (a > b || (a == b && idx[lo] > idx[hi]))
-                                     : (a < b || (a == b && idx[lo] < idx[hi]));
-                if (swap) {
-                    key[lo] = b;
-                    key[hi] = a;
-                    const uint16_t t2 = idx[lo];
-                    idx[lo] = idx[hi];
-                    idx[hi] = t2;
+            if (stride < kResortPer) {
+#pragma unroll
+                for (int e = 0; e < kResortPer; ++e) {
+                    const int l = e ^ stride;
+                    if (l > e) {
+                        const bool up = ((kResortPer * tid + e) & size) == 0;
+                        if ((v[e] > v[l]) == up) {
+                            const uint64_t t = v[e];
+                            v[e] = v[l];
+                            v[l] = t;
+                        }
+                    }
+                }
+            } else {
+                const int tmask = stride / kResortPer;          // partner thread: tid ^ tmask
+                const bool keep_min = ((tid & tmask) == 0) == (((kResortPer * tid) & size) == 0);
+                if (tmask < 32) {
+#pragma unroll
+                    for (int e = 0; e < kResortPer; ++e) {
+                        const uint64_t o = shfl_xor_u64(v[e], tmask);
+                        v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                    }
+                } else {
+                    __syncthreads();   // the previous exchange is read
+#pragma unroll
+                    for (int e = 0; e < kResortPer; ++e)
+                        xch[kResortPer * tid + e] = v[e];
+                    __syncthreads();
+#pragma unroll
+                    for (int e = 0; e < kResortPer; ++e) {
+                        const uint64_t o = xch[kResortPer * (tid ^ tmask) + e];
+                        v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                    }
                 }
             }
-            __syncthreads();
         }
     }
+#pragma unroll
+    for (int e = 0; e < kResortPer; ++e)
+        idx[kResortPer * tid + e] = (uint16_t)(uint32_t)v[e];
+    __syncthreads();
     const int m = (int)min((int64_t)kResortWindow, n - p0);
     // permutation: each thread moves its 4 slots; 8 channels' loads in flight at a time
     constexpr int kPer = kResortWindow / kResortThreads;
@@ -111,18 +151,18 @@ __global__ void __launch_bounds__(kResortThreads) k_resort_window(SimParams sp, 
     }
 #pragma unroll 1
     for (int c0 = 0; c0 < kChannels; c0 += 8) {
-        float v[8][kPer];
+        float val[8][kPer];
 #pragma unroll
         for (int c = 0; c < 8; ++c)
 #pragma unroll
             for (int k = 0; k < kPer; ++k)
-                v[c][k] = src_i[k] >= 0 ? src.at(c0 + c, p0 + src_i[k]) : 0.0f;
+                val[c][k] = src_i[k] >= 0 ? src.at(c0 + c, p0 + src_i[k]) : 0.0f;
 #pragma unroll
         for (int c = 0; c < 8; ++c)
 #pragma unroll
             for (int k = 0; k < kPer; ++k)
                 if (src_i[k] >= 0)
-                    dst.at(c0 + c, p0 + tid + k * kResortThreads) = v[c][k];
+                    dst.at(c0 + c, p0 + tid + k * kResortThreads) = val[c][k];
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
