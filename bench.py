@@ -377,6 +377,35 @@ def bench_small_elastic(substeps=100, reps=5):
     return out
 
 
+def bench_ceilings(reps=5):
+    """The second ceiling of P2G: float4 reductions applied by L2 per second
+    (mpm_debug_red_rate) on a grid the size of the snow scene's (7,012 blocks
+    of 64 nodes, 7.2 MB, L2-resident), the whole device busy (152 SMs x 2,048
+    threads), 256 reductions per thread; per warp instruction 32 distinct
+    nodes in 4 lines, four lanes per node, a line per lane, and one node."""
+    import torch
+    from paper_2111_00699_gb300 import mpm
+    nodes = 7012 * 64
+    grid = torch.zeros((nodes, 4), dtype=torch.float32, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    threads, reds = sms * 2048, 256
+    stream = torch.cuda.Stream()
+    out = {"workload": "L2 float4 reductions: %d nodes (7.2 MB), %d threads x %d reductions" % (nodes, threads, reds),
+           "unit": "float4 reductions/s"}
+    for pattern, name in ((0, "distinct_nodes"), (1, "four_lanes_per_node"), (2, "one_line_per_lane"),
+                          (3, "one_node_per_warp")):
+        grid.zero_()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            mpm.debug_red_rate(grid, threads, reds, pattern, stream)
+        best = min(_events_time(stream, lambda: mpm.debug_red_rate(grid, threads, reds, pattern, stream))
+                   for _ in range(reps))
+        total = float(grid[:, 3].double().sum().item())
+        expect = float(threads) * reds * (2 + reps)
+        out[name] = {"per_s": threads * reds / (best / 1e3), "ms": best, "sum_ok": abs(total - expect) <= 1e-6 * expect}
+    return out
+
+
 def bench_ablations(substeps=100):
     """The paper's single-GPU ablations (Sec. 6), on the snow-blocks scene
     with the particles added in a shuffled order: free-zone rebuilds with a
@@ -725,7 +754,7 @@ WORKLOADS = (("batched", bench_batched), ("fountain", bench_fountain),
              ("nacc_snow", bench_nacc_snow),
              ("small_elastic", bench_small_elastic), ("adjoint", bench_adjoint),
              ("ablations", bench_ablations), ("cta_warps", bench_cta_warps), ("layout", bench_layout_ablations),
-             ("fast_math", bench_fast_math))
+             ("fast_math", bench_fast_math), ("ceilings", bench_ceilings))
 
 
 def main():

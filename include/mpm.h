@@ -475,6 +475,24 @@ mpm_status mpm_debug_plasticity(const mpm_material* mat, float* F, float* Jp, in
  * nothing faults, nothing is left in flight.  Synchronous. */
 mpm_status mpm_debug_wait_timeout(int max_iter);
 
+/* Measurement of a second ceiling of P2G (not part of the substep): the rate
+ * at which L2 applies float4 reductions, the operation P2G's scatter ends in
+ * (Sec. 4.2.2 aggregates per warp to issue fewer of them).  Launches `threads`
+ * threads (a multiple of 32) on `stream`; each applies `reds_per_thread`
+ * reductions of (1, 1, 1, 1) to the device array `grid` of `nodes` float4
+ * (caller-owned, 16-byte aligned, nodes a multiple of 32; a few MB keeps it
+ * resident in L2 like the P2G grid).  Each step picks spans of 32 consecutive
+ * nodes by a pseudo-random sequence: pattern 0 gives each lane of a warp its
+ * own node of one span (32 distinct nodes in 4 lines), pattern 1 four lanes per
+ * node of one span, pattern 2 each lane node 0 of its own span (32 lines per
+ * warp instruction), pattern 3 one node for the whole warp.  The caller times
+ * it (events on `stream`) and may check that the
+ * fourth components sum to threads * reds_per_thread.  Asynchronous.
+ * MPM_EINVAL for a null or misaligned grid or sizes out of range (1 to 4096
+ * reductions per thread), MPM_ECUDA if the launch fails. */
+mpm_status mpm_debug_red_rate(void* grid, int64_t nodes, int64_t threads, int32_t reds_per_thread, int32_t pattern,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

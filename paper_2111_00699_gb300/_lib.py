@@ -94,6 +94,7 @@ _PROTOS = {
     "mpm_set_g2p2g": (I, [P, I]),
     "mpm_use_graphs": (I, [P, I]),
     "mpm_debug_wait_timeout": (I, [I]),
+    "mpm_debug_red_rate": (I, [P, I64, I64, I, I, P]),
     "mpm_graph_launches": (I64, [P]),
     "mpm_profile_enable": (I, [P, I]),
     "mpm_profile_read": (I, [P, P, P, I]),

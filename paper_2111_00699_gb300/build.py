@@ -22,7 +22,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 # exp and log), built on request only, for the fast-math ablation of Sec. 6
 LIB_IEEE = os.path.join(HERE, "libmpm_ieee.so")
 BUILD_DIR_IEEE = os.path.join(HERE, "_build_ieee")
-SOURCES = ["sort.cu", "rebuild.cu", "p2g.cu", "g2p.cu", "g2p2g.cu", "api.cu", "batch.cu", "adjoint.cu"]
+SOURCES = ["sort.cu", "rebuild.cu", "p2g.cu", "g2p.cu", "g2p2g.cu", "api.cu", "batch.cu", "adjoint.cu",
+           "ceilings.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-use_fast_math", "-std=c++17", "-Xcompiler", "-fPIC",
          "-I" + INCLUDE, "-I" + CSRC]

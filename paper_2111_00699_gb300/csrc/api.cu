@@ -1395,6 +1395,19 @@ mpm_status mpm_debug_plasticity(const mpm_material* mat, float* F, float* Jp, in
     return cudaDeviceSynchronize() == cudaSuccess && cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ECUDA;
 }
 
+mpm_status mpm_debug_red_rate(void* grid, int64_t nodes, int64_t threads, int32_t reds_per_thread, int32_t pattern,
+                              void* stream)
+{
+    if (!grid || nodes < 32 || nodes % 32 != 0 || threads < 32 || threads % 32 != 0 || threads > (int64_t)1 << 31 ||
+        reds_per_thread < 1 || reds_per_thread > 4096 || pattern < 0 || pattern > 3 ||
+        ((uintptr_t)grid & 15u) != 0)
+        return MPM_EINVAL;
+    return launch_debug_red_rate(static_cast<float4*>(grid), nodes, threads, reds_per_thread, pattern,
+                                 static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? MPM_OK
+               : MPM_ECUDA;
+}
+
 mpm_status mpm_debug_wait_timeout(int max_iter)
 {
     if (max_iter < 1 || max_iter > (1 << 16))

@@ -481,3 +481,16 @@ def radix_sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, key_bits: i
                                             ctypes.c_void_p(kout.data_ptr()), ctypes.c_void_p(vout.data_ptr()),
                                             n, key_bits, ctypes.c_void_p(s.cuda_stream)))
     return kout.view(keys.dtype), vout
+
+
+def debug_red_rate(grid: torch.Tensor, threads: int, reds_per_thread: int, pattern: int = 0,
+                   stream: torch.cuda.Stream | None = None) -> None:
+    """Launch the L2 float4-reduction rate probe (mpm_debug_red_rate) on
+    `grid`, a float32 CUDA tensor of shape (nodes, 4); asynchronous on
+    `stream` (default: the current stream)."""
+    if grid.dtype != torch.float32 or not grid.is_cuda or grid.dim() != 2 or grid.shape[1] != 4 \
+            or not grid.is_contiguous():
+        raise ValueError("grid must be a contiguous float32 CUDA tensor of shape (nodes, 4)")
+    s = stream if stream is not None else torch.cuda.current_stream(grid.device)
+    _check(load().mpm_debug_red_rate(ctypes.c_void_p(grid.data_ptr()), int(grid.shape[0]), int(threads),
+                                     int(reds_per_thread), int(pattern), ctypes.c_void_p(s.cuda_stream)), None)

@@ -190,3 +190,15 @@ int main(void) {
                      ctypes.sizeof(_lib.SceneDesc)]
     assert offs == [_lib.Config.max_particles.offset, _lib.Config.transfer.offset, _lib.Config.flip_beta_max.offset,
                     _lib.Config.flip_compress_margin.offset, _lib.Material.alpha0.offset]
+
+
+def test_red_rate_probe_rejects_bad_arguments_without_touching_the_gpu(lib):
+    from paper_2111_00699_gb300 import _lib
+    V = ctypes.c_void_p
+    assert lib.mpm_debug_red_rate(None, 64, 64, 1, 0, None) == _lib.MPM_EINVAL
+    assert lib.mpm_debug_red_rate(V(256), 33, 64, 1, 0, None) == _lib.MPM_EINVAL       # nodes not a multiple of 32
+    assert lib.mpm_debug_red_rate(V(256), 64, 48, 1, 0, None) == _lib.MPM_EINVAL       # threads not whole warps
+    assert lib.mpm_debug_red_rate(V(256), 64, 64, 0, 0, None) == _lib.MPM_EINVAL       # no reductions
+    assert lib.mpm_debug_red_rate(V(256), 64, 64, 5000, 0, None) == _lib.MPM_EINVAL
+    assert lib.mpm_debug_red_rate(V(256), 64, 64, 1, 4, None) == _lib.MPM_EINVAL       # unknown pattern
+    assert lib.mpm_debug_red_rate(V(264), 64, 64, 1, 0, None) == _lib.MPM_EINVAL       # not 16-byte aligned

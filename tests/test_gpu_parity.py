@@ -996,6 +996,30 @@ def test_window_resort_matches_oracle(M, graphs):
     assert stats["rebuilds"] >= 2
 
 
+@pytest.mark.parametrize("pattern", [0, 1, 2, 3])
+def test_red_rate_probe_applies_every_reduction(M, pattern):
+    """The L2 reduction-rate probe: every one of threads x reductions float4
+    additions of (1, 1, 1, 1) lands in the grid (all four components sum to
+    the count), spread over the spans its sequence picks; four lanes per node
+    touch nodes 0-7 of a span, one node per lane or per warp only node 0."""
+    nodes, threads, reds = 32 * 1024, 32 * 300, 7
+    grid = torch.zeros((nodes, 4), dtype=torch.float32, device="cuda")
+    M.debug_red_rate(grid, threads, reds, pattern)
+    torch.cuda.synchronize()
+    g = grid.double().cpu().numpy()
+    for c in range(4):
+        assert g[:, c].sum() == threads * reds
+    assert np.all(g[:, 0] == g[:, 3])
+    touched = (g[:, 3] > 0).reshape(-1, 32)
+    if pattern == 1:
+        assert not touched[:, 8:].any()          # lanes l / 4: nodes 0-7 of a span
+    if pattern >= 2:
+        assert not touched[:, 1:].any()          # node 0 of a span only
+    assert touched.any(axis=1).sum() > 100       # many spans
+    with pytest.raises(ValueError):
+        M.debug_red_rate(grid[:, :3], threads, reds, pattern)
+
+
 def test_bounded_wait_times_out_and_device_stays_usable(M):
     """Failure detection without a fault: a device wait on an mbarrier that no
     copy completes gives up after its iteration limit and reports
