@@ -30,6 +30,10 @@
 using namespace mpm;
 
 namespace mpm {
+
+// ceilings.cu: the L2 reduction-rate probe (not part of the substep)
+cudaError_t launch_debug_red_rate(float4* grid, int64_t nodes, int64_t threads, int reds, int pattern,
+                                  cudaStream_t s);
 // rebuild.cu: one warp polls an mbarrier no copy completes, with the bounded
 // wait of the staged transfer kernels, and sets ST_TIMEOUT when it gives up.
 void launch_debug_wait_timeout(int max_iter, uint32_t* err, cudaStream_t s);

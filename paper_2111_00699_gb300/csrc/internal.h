@@ -161,10 +161,6 @@ cudaError_t radix_sort_pairs(const uint32_t* kin, const int32_t* vin, uint32_t* 
 cudaError_t exclusive_scan(const int32_t* in, int32_t* out, int64_t n, void* scratch, cudaStream_t s,
                            int64_t* launches);
 
-// ceilings.cu
-cudaError_t launch_debug_red_rate(float4* grid, int64_t nodes, int64_t threads, int reds, int pattern,
-                                  cudaStream_t s);
-
 // rebuild.cu
 void launch_keys(const SimParams& sp, const PartView& pv, int64_t n, uint32_t* keys, int32_t* vals,
                  uint32_t* err, cudaStream_t s);
