@@ -57,9 +57,9 @@ BYTES_GRID_NODE = 48
 # substep moves 260 B (P2G 100 + G2P reads x, F, Jp 52 and writes x, v, C, F, Jp 100 + the
 # grid's ~8 B per particle at 8 particles per cell); the fused G2P2G moves 112 B (reads and
 # writes x, F, Jp 52 B each + ~8 B of grid).
-SURVEY_BYTES_P2G = 100
-SURVEY_BYTES_SUBSTEP = 260
-SURVEY_BYTES_SUBSTEP_FUSED = 112
+LAYOUT_FREE_BYTES_P2G = 100
+LAYOUT_FREE_BYTES_SUBSTEP = 260
+LAYOUT_FREE_BYTES_SUBSTEP_FUSED = 112
 
 
 def workload_config(n, world=1):
@@ -976,17 +976,17 @@ def main():
                            else g2p_kernel_name(_variant_name("G2P", g2p_final), aosoa, tuned_l["cta_warps"])),
                    "grid": "k_grid"}[dom]
     # the same kernel on the layout-free byte count (P2G: x, v, C, F, Jp = 100 B per particle)
-    survey_bytes = {"p2g": SURVEY_BYTES_P2G * n_now}.get(dom)
+    survey_bytes = {"p2g": LAYOUT_FREE_BYTES_P2G * n_now}.get(dom)
     achieved_survey = survey_bytes / (avg[dom] / 1e3) / 1e9 if (survey_bytes and avg[dom] > 0) else None
     # the whole substep (timed region): own layout and the layout-free count
     sub_own = (algo["p2g"] if not use_fused else 0) + algo["g2p"] + algo["grid"]
-    sub_survey = (SURVEY_BYTES_SUBSTEP_FUSED if use_fused else SURVEY_BYTES_SUBSTEP) * n
+    sub_survey = (LAYOUT_FREE_BYTES_SUBSTEP_FUSED if use_fused else LAYOUT_FREE_BYTES_SUBSTEP) * n
     substep = {"ms": ms_per_step, "bytes_own": sub_own, "bytes_survey": sub_survey,
                "achieved_own_gbs": sub_own / (ms_per_step / 1e3) / 1e9,
                "achieved_survey_gbs": sub_survey / (ms_per_step / 1e3) / 1e9,
                "frac_own": sub_own / (ms_per_step / 1e3) / 1e9 / hbm,
                "frac_survey": sub_survey / (ms_per_step / 1e3) / 1e9 / hbm,
-               "survey_bytes_per_particle": SURVEY_BYTES_SUBSTEP_FUSED if use_fused else SURVEY_BYTES_SUBSTEP,
+               "survey_bytes_per_particle": LAYOUT_FREE_BYTES_SUBSTEP_FUSED if use_fused else LAYOUT_FREE_BYTES_SUBSTEP,
                "ms_per_frame_at_frac_0p5_survey": sub_survey / (0.5 * hbm * 1e9) * 1e3 * SUBSTEPS_PER_FRAME}
     roofline = {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": peak_note,
