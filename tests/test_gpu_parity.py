@@ -510,10 +510,14 @@ def test_mixed_materials_match_oracle(M, g2p):
     assert linf(g["Jp"], s.Jp) <= 1e-4
 
 
-def test_ten_substeps_snow_full_size_bench_configuration(M):
-    """The 1.34M-particle snow scene in the launch configuration bench.py
-    times (register-run P2G, 64-register G2P, CUDA-graph replay on a side
-    stream): x and v after 10 substeps within 1e-4 of the FP64 oracle."""
+@pytest.mark.parametrize("p2g,g2p,aosoa,warps,resort", [(3, 4, False, 4, 0), (15, 7, True, 4, 0), (4, 7, True, 2, 4)])
+def test_ten_substeps_snow_full_size_bench_configuration(M, p2g, g2p, aosoa, warps, resort):
+    """The 1.34M-particle snow scene in the launch configurations bench.py's
+    autotuner ends on (register runs in storage or base-cell order, the
+    64-register G2P with the weights in registers or shared memory, SoA or
+    AoSoA store, 2 or 4 warps per CTA, window re-sorts or none; CUDA-graph
+    replay on a side stream): x and v after 10 substeps within 1e-4 of the
+    FP64 oracle."""
     x, _ = scenes.snow_blocks()
     vol = (1 / 256) ** 3 / 8
     gm, om = mats_pair(M, M.SNOW, E=1.4e5, nu=0.2, rho=400.0)
@@ -521,8 +525,10 @@ def test_ten_substeps_snow_full_size_bench_configuration(M):
     rng = np.random.default_rng(9)
     v = (0.2 * rng.normal(size=(len(x), 3))).astype(np.float32)
     stream = torch.cuda.Stream()
-    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP, stream=stream, p2g_variant=3, g2p_variant=4,
-                     graphs=True) as sim:
+    with M.Simulator(256, 1 / 256, [gm], boundary=M.SLIP, stream=stream, p2g_variant=p2g, g2p_variant=g2p,
+                     graphs=True, resort_interval=resort) as sim:
+        sim.set_cta_warps(warps)
+        sim.set_layout(aosoa)
         sim.add_particles(torch.from_numpy(x).cuda(), v=torch.from_numpy(v).cuda())
         s = orc.State(x.astype(np.float64), v.astype(np.float64), vol=vol)
         g = _run_both(M, sim, [om], s, 10, 5e-5, cfg)
